@@ -1,0 +1,264 @@
+"""ctypes front end of the plain FP64 CPU oracle.
+
+TEST INFRASTRUCTURE ONLY: imported by tests/, by the package smoke check and
+by the benchmark's CPU-baseline leg, never by the product path.  Arrays are
+numpy complex128 in the canonical layouts:
+    full spinor  [V][4][3], even/odd spinor [V/2][4][3] (rank among the sites
+    of that parity, lexicographic order), links [V][4][3][3].
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build_oracle
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = build_oracle.build()
+        L = C.CDLL(path)
+        P = C.c_void_p
+        D = C.c_double
+        I = C.c_int
+        LG = C.c_long
+        IP = C.POINTER(C.c_int)
+        DP = C.POINTER(C.c_double)
+        sig = {
+            "or_create": (P, [I, I, I, I, I]),
+            "or_destroy": (None, [P]),
+            "or_set_gauge": (None, [P, P]),
+            "or_set_params": (I, [P, D, D]),
+            "or_gamma": (None, [I, P]),
+            "or_fhat_site": (None, [P, LG, I, I, P]),
+            "or_clover_site": (None, [P, LG, P]),
+            "or_clover_inv_site": (None, [P, LG, P]),
+            "or_logdet": (D, [P, I]),
+            "or_hop": (None, [P, P, P]),
+            "or_apply_clover": (None, [P, I, P, P]),
+            "or_apply_D": (None, [P, P, P]),
+            "or_apply_Dhat": (None, [P, P, P]),
+            "or_apply_Dhat_dag": (None, [P, P, P]),
+            "or_apply_gamma5": (None, [LG, P, P]),
+            "or_dhat_site": (None, [P, P, LG, P]),
+            "or_d_site": (None, [P, P, LG, P]),
+            "or_even_rank_to_site": (LG, [P, I, LG]),
+            "or_cgnr": (I, [P, P, P, D, I, IP]),
+            "or_sap": (None, [P, IP, I, I, P, P]),
+            "or_sap_block_solve": (None, [P, IP, LG, I, P, P]),
+            "or_gcr": (I, [P, I, IP, I, I, I, I, D, P, P, IP, DP]),
+            "or_dfl_build": (I, [P, IP, I, I, I, I, P]),
+            "or_dfl_project": (None, [P, P, P]),
+            "or_dfl_expand": (None, [P, P, P]),
+            "or_dfl_little": (None, [P, P]),
+            "or_dfl_little_apply": (None, [P, P, P]),
+            "or_dfl_coarse_solve": (I, [P, P, P, D, I, I, IP]),
+            "or_dfl_precond": (None, [P, IP, I, I, D, P, P]),
+            "or_dfl_subspace": (None, [P, P]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _p(a: np.ndarray):
+    assert a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def _c(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.complex128)
+
+
+def gamma(mu: int) -> np.ndarray:
+    """gamma_mu (mu = 0..3) or gamma5 (mu = 4) of the oracle's chiral basis."""
+    g = np.zeros((4, 4), dtype=np.complex128)
+    lib().or_gamma(mu, _p(g))
+    return g
+
+
+def gamma5(x: np.ndarray) -> np.ndarray:
+    x = _c(x)
+    out = np.empty_like(x)
+    lib().or_apply_gamma5(x.size // 12, _p(x), _p(out))
+    return out
+
+
+class Oracle:
+    """One lattice with its gauge field and clover term (all FP64)."""
+
+    def __init__(self, dims, U: np.ndarray, kappa: float, csw: float, antiperiodic_t: bool = True):
+        self.dims = tuple(int(d) for d in dims)
+        T, L1, L2, L3 = self.dims
+        self.V = T * L1 * L2 * L3
+        self.Vh = self.V // 2
+        self._o = lib().or_create(T, L1, L2, L3, 1 if antiperiodic_t else 0)
+        if not self._o:
+            raise ValueError(f"bad lattice {dims}")
+        self._U = _c(U).reshape(self.V, 4, 3, 3)
+        lib().or_set_gauge(self._o, _p(self._U))
+        self.status = lib().or_set_params(self._o, float(kappa), float(csw))
+        self.kappa, self.csw = kappa, csw
+
+    def __del__(self):
+        if getattr(self, "_o", None):
+            lib().or_destroy(self._o)
+            self._o = None
+
+    # ---- geometry
+    def even_sites(self) -> np.ndarray:
+        return np.array([lib().or_even_rank_to_site(self._o, 0, r) for r in range(self.Vh)])
+
+    def odd_sites(self) -> np.ndarray:
+        return np.array([lib().or_even_rank_to_site(self._o, 1, r) for r in range(self.Vh)])
+
+    # ---- operators
+    def _apply(self, fn, x, n):
+        x = _c(x).reshape(n, 4, 3)
+        out = np.empty_like(x)
+        fn(self._o, _p(x), _p(out))
+        return out
+
+    def hop(self, x):
+        return self._apply(lib().or_hop, x, self.V)
+
+    def D(self, x):
+        return self._apply(lib().or_apply_D, x, self.V)
+
+    def Dhat(self, x):
+        return self._apply(lib().or_apply_Dhat, x, self.Vh)
+
+    def Dhat_dag(self, x):
+        return self._apply(lib().or_apply_Dhat_dag, x, self.Vh)
+
+    def clover(self, x, inverse=False):
+        x = _c(x).reshape(self.V, 4, 3)
+        out = np.empty_like(x)
+        lib().or_apply_clover(self._o, 1 if inverse else 0, _p(x), _p(out))
+        return out
+
+    def clover_site(self, x: int, inverse=False) -> np.ndarray:
+        A = np.empty((12, 12), dtype=np.complex128)
+        (lib().or_clover_inv_site if inverse else lib().or_clover_site)(self._o, int(x), _p(A))
+        return A
+
+    def fhat_site(self, x: int, mu: int, nu: int) -> np.ndarray:
+        F = np.empty((3, 3), dtype=np.complex128)
+        lib().or_fhat_site(self._o, int(x), mu, nu, _p(F))
+        return F
+
+    def logdet(self, parity: int) -> float:
+        return lib().or_logdet(self._o, parity)
+
+    def dhat_site(self, x_e, re: int) -> np.ndarray:
+        x_e = _c(x_e).reshape(self.Vh, 4, 3)
+        out = np.empty((4, 3), dtype=np.complex128)
+        lib().or_dhat_site(self._o, _p(x_e), int(re), _p(out))
+        return out
+
+    def d_site(self, x, site: int) -> np.ndarray:
+        x = _c(x).reshape(self.V, 4, 3)
+        out = np.empty((4, 3), dtype=np.complex128)
+        lib().or_d_site(self._o, _p(x), int(site), _p(out))
+        return out
+
+    # ---- solvers
+    def cgnr(self, eta_e, tol=1e-10, maxit=10000):
+        eta_e = _c(eta_e).reshape(self.Vh, 4, 3)
+        psi = np.empty_like(eta_e)
+        it = C.c_int(0)
+        st = lib().or_cgnr(self._o, _p(eta_e), _p(psi), tol, maxit, C.byref(it))
+        return psi, st, it.value
+
+    @staticmethod
+    def _bs(bs):
+        return (C.c_int * 4)(*[int(b) for b in bs])
+
+    def sap(self, eta, bs=(4, 4, 4, 4), ncy=4, nmr=5):
+        eta = _c(eta).reshape(self.V, 4, 3)
+        psi = np.empty_like(eta)
+        lib().or_sap(self._o, self._bs(bs), ncy, nmr, _p(eta), _p(psi))
+        return psi
+
+    def sap_block_solve(self, r, blk, bs=(4, 4, 4, 4), nmr=5):
+        r = _c(r).reshape(self.V, 4, 3)
+        chi = np.zeros_like(r)
+        lib().or_sap_block_solve(self._o, self._bs(bs), int(blk), nmr, _p(r), _p(chi))
+        return chi
+
+    def gcr(self, eta, precond=1, bs=(4, 4, 4, 4), ncy=4, nmr=5, nkv=16, nmx=2048, tol=1e-10):
+        eta = _c(eta).reshape(self.V, 4, 3)
+        psi = np.empty_like(eta)
+        it = C.c_int(0)
+        rr = C.c_double(0)
+        st = lib().or_gcr(self._o, precond, self._bs(bs), ncy, nmr, nkv, nmx, tol, _p(eta), _p(psi),
+                          C.byref(it), C.byref(rr))
+        return psi, st, it.value, rr.value
+
+    # ---- deflation
+    def dfl_build(self, v0, bs=(4, 4, 4, 4), ninv=4, ncy=4, nmr=4):
+        v0 = _c(v0)
+        Ns = v0.size // (12 * self.V)
+        self.Ns = Ns
+        self.dfl_bs = tuple(bs)
+        nb = 1
+        for L, b in zip(self.dims, bs):
+            nb *= L // b
+        self.nblk = nb
+        return lib().or_dfl_build(self._o, self._bs(bs), Ns, ninv, ncy, nmr, _p(v0))
+
+    def dfl_subspace(self):
+        out = np.empty((self.Ns, self.V, 4, 3), dtype=np.complex128)
+        lib().or_dfl_subspace(self._o, _p(out))
+        return out
+
+    def dfl_project(self, x):
+        x = _c(x).reshape(self.V, 4, 3)
+        c = np.empty(self.nblk * self.Ns, dtype=np.complex128)
+        lib().or_dfl_project(self._o, _p(x), _p(c))
+        return c
+
+    def dfl_expand(self, c):
+        c = _c(c)
+        out = np.empty((self.V, 4, 3), dtype=np.complex128)
+        lib().or_dfl_expand(self._o, _p(c), _p(out))
+        return out
+
+    def dfl_little(self):
+        N = self.nblk * self.Ns
+        A = np.empty((N, N), dtype=np.complex128)
+        lib().or_dfl_little(self._o, _p(A))
+        return A
+
+    def dfl_little_apply(self, c):
+        c = _c(c)
+        out = np.empty_like(c)
+        lib().or_dfl_little_apply(self._o, _p(c), _p(out))
+        return out
+
+    def dfl_coarse_solve(self, b, tol=1e-8, nkv=16, nmx=4096):
+        b = _c(b)
+        x = np.empty_like(b)
+        it = C.c_int(0)
+        st = lib().or_dfl_coarse_solve(self._o, _p(b), _p(x), tol, nkv, nmx, C.byref(it))
+        return x, st, it.value
+
+    def dfl_precond(self, rho, bs=(4, 4, 4, 4), ncy=4, nmr=5, ctol=1e-8):
+        rho = _c(rho).reshape(self.V, 4, 3)
+        out = np.empty_like(rho)
+        lib().or_dfl_precond(self._o, self._bs(bs), ncy, nmr, ctol, _p(rho), _p(out))
+        return out
+
+
+def even_odd_split(o: Oracle, x: np.ndarray):
+    """(x_e, x_o) of a full field in the oracle's even/odd rank order."""
+    x = np.asarray(x).reshape(o.V, 4, 3)
+    return x[o.even_sites()], x[o.odd_sites()]
