@@ -1,0 +1,260 @@
+"""Benchmark of the Wilson-clover hot path on GB300.
+
+Workload: the 48x24^3 lattice of Sec. 3 (kappa = 0.13625, c_sw = 1.9,
+synthetic SU(3) links with plaquette 0.55, antiperiodic time), 12 Gaussian
+right-hand sides batched in one multi-RHS stencil.  One step = one application
+of the even-odd Schur complement Dhat (Eq. 2) in FP32 to the 12-field batch,
+on fields resident in HBM in the library's native layout.
+
+value    : Dhat GFLOP/s (3672 flop per even site per field)
+e2e      : the same through the public C ABI (lqcd_apply_Dhat on canonical
+           fields) with the step's sources copied host->device from pinned
+           memory and the result read back inside the timed region
+roofline : algorithmic HBM bytes of one Dhat application / its CUDA-event time
+cpu_baseline: the FP64 CPU oracle's Dhat on the same lattice (1 field)
+
+`--impl reference` times the CPU oracle alone (the comparison arm).
+Several GPUs (torchrun): independent replicas, one lattice batch per rank.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+FLOP_PER_SITE = 3672
+DIMS = (48, 24, 24, 24)
+KAPPA, CSW = 0.13625, 1.9
+WORKLOAD = "48x24^3 Wilson-clover Dhat_ee, kappa=0.13625, c_sw=1.9, 12 RHS"
+
+
+def dhat_bytes_per_site(prec: str, nrhs: int) -> int:
+    """Algorithmic HBM bytes of one Dhat application per even site, all fields.
+    Links: each of the two half-hops reads every link once (8 per site);
+    clover: A_ee and A_oo^-1 (2 x 72 reals); per field: psi_e read by both
+    kernels, chi_o written and read, out written (5 x 24 reals)."""
+    word = 8 if prec == "f64" else 4
+    link_words = 2 * 8 * (18 if prec == "f64" else 12)
+    return word * (link_words + 144 + 120 * nrhs)
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return d["hbm_gbs"], "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampler running during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.p = None
+        self.out = []
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}",
+                                       "--format=csv,noheader,nounits", "-lms", "100"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            txt, _ = self.p.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+            txt, _ = self.p.communicate()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in txt.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(steps: int = 2):
+    """The FP64 oracle's Dhat on the same 48x24^3 lattice (one field): a bounded
+    sample of the workload, scaled to GFLOP/s."""
+    import oracle as orc
+    from paper_1011_0911_gb300 import synth
+    U = synth.su3_links(DIMS, 0)
+    o = orc.Oracle(DIMS, U, KAPPA, CSW)
+    pe = synth.gaussian_spinor(o.Vh, 1)
+    o.Dhat(pe)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        o.Dhat(pe)
+    dt = (time.perf_counter() - t0) / steps
+    return {"value": round(FLOP_PER_SITE * o.Vh / dt / 1e9, 4), "unit": "GFLOP/s", "cores": orc.num_threads(),
+            "kind": "oracle",
+            "sample": f"{steps} FP64 Dhat applications on one 48x24^3 field (one-field sample of the 12-field step)",
+            "seconds_per_application": round(dt, 4)}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    cb = cpu_baseline(steps=max(1, min(args.steps, 3)))
+    line = {"impl": "reference", "metric": "Dhat GFLOP/s", "value": cb["value"], "unit": "GFLOP/s",
+            "n_gpus": args.gpus, "steps": max(1, min(args.steps, 3)), "warmup": args.warmup,
+            "higher_is_better": True, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD + " (oracle: 1 field)", "lattice": "48x24x24x24"},
+            "cpu_baseline": {k: cb[k] for k in ("kind", "cores", "sample")} | {"value": cb["value"], "unit": "GFLOP/s"},
+            "e2e": {"value": cb["value"], "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--nrhs", type=int, default=12)
+    ap.add_argument("--prec", default="f32", choices=["f32", "f64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    from paper_1011_0911_gb300 import lqcd, synth
+    prec = lqcd.F32 if args.prec == "f32" else lqcd.F64
+    nrhs = args.nrhs
+    U = synth.su3_links(DIMS, 0)
+    ctx = lqcd.Context(DIMS)
+    ctx.set_gauge(torch.from_numpy(U).cuda())
+    ctx.clover_invert(KAPPA, CSW)
+    Vh = ctx.Vh
+    eta = synth.gaussian_spinor(nrhs * Vh, 1 + rank).reshape(nrhs, Vh, 4, 3)
+    cdt = torch.complex64 if prec == lqcd.F32 else torch.complex128
+    eta_host = torch.from_numpy(eta).to(cdt).pin_memory()
+    eta_dev = eta_host.cuda()
+    nin = ctx.pack(eta_dev, prec, 1)
+    nout = ctx.native_empty(prec, 1, nrhs)
+    stream = ctx.stream
+    flops_step = FLOP_PER_SITE * Vh * nrhs
+
+    # ---- device-resident timing (value, roofline)
+    for _ in range(args.warmup):
+        ctx.apply_Dhat_native(nin, nout, prec, nrhs)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = Clocks(local)
+    clocks.start()
+    time.sleep(0.3)
+    launches0 = ctx.kernel_launches
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    torch.cuda.synchronize()
+    evs[0].record(stream)
+    for i in range(args.steps):
+        ctx.apply_Dhat_native(nin, nout, prec, nrhs)
+        evs[i + 1].record(stream)
+    torch.cuda.synchronize()
+    launches = ctx.kernel_launches - launches0
+    clk = clocks.stop()
+    per = [evs[i].elapsed_time(evs[i + 1]) for i in range(args.steps)]
+    total_ms = evs[0].elapsed_time(evs[-1])
+    t_tensor = torch.tensor([total_ms], device="cuda")
+    if dist:
+        dist.all_reduce(t_tensor, op=dist.ReduceOp.MAX)
+    total_ms = t_tensor.item()
+    ms_step = total_ms / args.steps
+    value = flops_step * args.steps * world / (total_ms * 1e-3) / 1e9
+    avg_launch_ms = statistics.mean(per)
+    bytes_app = dhat_bytes_per_site(args.prec, nrhs) * Vh
+    peak, peak_kind = load_peaks()
+    achieved = bytes_app / (avg_launch_ms * 1e-3) / 1e9
+
+    # ---- end-to-end through the public ABI, host buffers, copies inside the timed region
+    out_host = torch.empty_like(eta_host).pin_memory()
+    e2e_steps = max(3, min(args.steps // 10, 40))
+    for _ in range(2):
+        d = eta_host.to("cuda", non_blocking=True)
+        o = ctx.apply_Dhat(d, prec)
+        out_host.copy_(o, non_blocking=True)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        d = eta_host.to("cuda", non_blocking=True)
+        o = ctx.apply_Dhat(d, prec)
+        out_host.copy_(o, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / e2e_steps
+    e2e_val = flops_step * world / (e2e_ms * 1e-3) / 1e9
+    nbytes = eta_host.numel() * eta_host.element_size()
+
+    if rank == 0:
+        cb = None
+        if not args.no_cpu_baseline:
+            cb = cpu_baseline()
+        line = {
+            "metric": "Dhat GFLOP/s", "value": round(value, 2), "unit": "GFLOP/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 5),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": args.prec, "data": "synthetic",
+            "config": {"workload": WORKLOAD, "lattice": "48x24x24x24", "nrhs": nrhs, "precision": args.prec,
+                       "links": "2-row SU(3)" if prec == lqcd.F32 else "full SU(3)",
+                       "l2": "inputs larger than L2 (links+clover+12 fields = %.2f GB)" % (
+                           (dhat_bytes_per_site(args.prec, nrhs) * Vh) / 1e9),
+                       "parallelism": f"replicas x{world}"},
+            "e2e": {"value": round(e2e_val, 2), "unit": "GFLOP/s", "ms_per_step": round(e2e_ms, 4),
+                    "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
+                    "path": "lqcd_apply_Dhat (canonical fields) + pinned host copies"},
+            "roofline": {"kernel": "Dhat = k_hop<DHAT1> + k_hop<DHAT2>", "bound": "hbm",
+                         "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                         "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
+                         "traffic": None, "algorithmic_bytes_per_launch": bytes_app},
+            "gpu_launches": launches,
+            "clocks": clk,
+            "cpu_baseline": cb,
+        }
+        print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

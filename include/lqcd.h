@@ -1,0 +1,239 @@
+/*
+ * lqcd.h -- C ABI of the GB300 (sm_103a) Wilson-clover solver library.
+ *
+ * The library implements the solver hot path of Marinkovic & Schaefer,
+ * "Comparison of the mass preconditioned HMC and the DD-HMC algorithm for
+ * two-flavour QCD" (Lattice 2010):
+ *   - the O(a)-improved Wilson-clover operator D(m) of Eq. 1,
+ *   - its even-odd Schur complement Dhat = D_ee - D_eo D_oo^-1 D_oe (Eq. 2),
+ *   - the clover term, its inverse and log det (Eq. 1, Eq. 4),
+ *   - the Schwarz (SAP) preconditioner and the locally deflated GCR solver
+ *     named in Sec. 3-4 (Table 1), and the solution of Dhat psi = eta through
+ *     a full-lattice solve (Eq. 5).
+ *
+ * Conventions (shared by every entry point):
+ *   Lattice   T x L1 x L2 x L3, every extent even; x0 is time and the slowest
+ *             coordinate: site = x3 + L3*(x2 + L2*(x1 + L1*x0)).
+ *   Parity    a site is even when x0+x1+x2+x3 is even.  A half-lattice
+ *             ("even" or "odd") field lists the sites of that parity in
+ *             increasing site order (rank r holds site 2r or 2r+1).
+ *   Spinor    canonical layout [site][spin 4][colour 3][re,im]; LQCD_F64
+ *             uses double, LQCD_F32 float.  nrhs fields are stored one after
+ *             the other ([rhs][site]...).
+ *   Links     [site][mu 0..3][row 3][col 3][re,im] double, forward links
+ *             U_mu(x), SU(3); the gauge field is periodic.
+ *   Gamma     chiral basis, gamma5 = g0 g1 g2 g3 = diag(1,1,-1,-1),
+ *             g0 = [[0,-1],[-1,0]], gk = [[0,-i s_k],[i s_k,0]] (2x2 blocks).
+ *   Operator  D = (4+m0) + c_sw sum_{mu,nu} (i/4) sigma_{mu nu} Fhat_{mu nu}
+ *                 - 1/2 sum_mu [(1-g_mu) U_mu(x) psi(x+mu)
+ *                               + (1+g_mu) U_mu(x-mu)^dag psi(x-mu)],
+ *             m0 = 1/(2 kappa) - 4, sigma = (i/2)[g_mu, g_nu],
+ *             Fhat = (Q - Q^dag)/8 with Q the four plaquette leaves at x.
+ *             The fermion field is antiperiodic in time when
+ *             geom.antiperiodic_t != 0: hops across x0 = T-1 <-> 0 carry -1.
+ *   Pointers  every field pointer is a caller-owned DEVICE buffer (e.g. a
+ *             torch tensor); the library copies what it keeps.  All work is
+ *             enqueued on the context's stream; calls that return host
+ *             scalars synchronise that stream.
+ *   Errors    every entry point returns an lqcd_status; nothing aborts, traps
+ *             or throws.  lqcd_last_error() gives a one-line reason.
+ */
+#ifndef LQCD_H
+#define LQCD_H
+
+#include <stddef.h>
+
+#if defined(__GNUC__)
+#define LQCD_API __attribute__((visibility("default")))
+#else
+#define LQCD_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lqcd_ctx lqcd_ctx;
+
+typedef enum {
+    LQCD_OK = 0,
+    LQCD_ERR_ARG = 1,              /* invalid argument, size or pointer */
+    LQCD_ERR_CUDA = 2,             /* a CUDA call failed */
+    LQCD_ERR_NOMEM = 3,            /* device allocation failed */
+    LQCD_ERR_SINGULAR_CLOVER = 4,  /* |pivot| < 1e-12 max|A| in a 6x6 clover block */
+    LQCD_ERR_NOT_CONVERGED = 5,    /* iteration limit reached; best iterate returned */
+    LQCD_ERR_BREAKDOWN = 6,        /* zero norm in Gram-Schmidt / MinRes / CG */
+    LQCD_ERR_NAN = 7,              /* non-finite residual */
+    LQCD_ERR_TIMEOUT = 8,          /* a bounded device-side wait expired */
+    LQCD_ERR_STATE = 9             /* call out of order (no gauge field, no clover, no subspace) */
+} lqcd_status;
+
+typedef enum {
+    LQCD_F64 = 0,   /* double storage and arithmetic */
+    LQCD_F32 = 1,   /* float storage and arithmetic, SU(3) links stored as 2 rows */
+    LQCD_F16S = 2   /* half storage with one float scale per site and field, float arithmetic */
+} lqcd_prec;
+
+typedef struct {
+    int T, L1, L2, L3;
+    int antiperiodic_t;
+} lqcd_geom;
+
+/* ------------------------------------------------------------------ context */
+
+/* Create a context for one lattice.  stream: a cudaStream_t (NULL = legacy
+ * default stream) on which all work of this context is enqueued.
+ * Errors: LQCD_ERR_ARG for odd or non-positive extents or V > 2^31 / 4. */
+LQCD_API lqcd_status lqcd_create(const lqcd_geom *geom, void *stream, lqcd_ctx **out);
+LQCD_API lqcd_status lqcd_destroy(lqcd_ctx *ctx);
+LQCD_API const char *lqcd_last_error(const lqcd_ctx *ctx);
+/* Number of kernels this context has launched so far (instrumentation). */
+LQCD_API long lqcd_kernel_launches(const lqcd_ctx *ctx);
+/* Change the stream used by later calls. */
+LQCD_API lqcd_status lqcd_set_stream(lqcd_ctx *ctx, void *stream);
+
+/* Copy the gauge field (canonical layout, FP64, device) into the context and
+ * derive its FP32 / FP16 copies.  Invalidates the clover term and any
+ * deflation subspace.  (Eq. 1: U enters D through the hops and Fhat.) */
+LQCD_API lqcd_status lqcd_set_gauge(lqcd_ctx *ctx, const double *U_dev);
+
+/* Build Fhat from the clover leaves, A(x) = (4+m0) + c_sw (i/4) sum sigma Fhat
+ * as two 6x6 Hermitian blocks per site, and invert every block in FP64 by LU
+ * with partial pivoting (Eq. 1; the log det enters S_eff in Eq. 4).
+ * logdet_ee / logdet_oo (host pointers, may be NULL) receive
+ * sum over even / odd sites of log|det A(x)|.
+ * Errors: LQCD_ERR_STATE without gauge field, LQCD_ERR_SINGULAR_CLOVER. */
+LQCD_API lqcd_status lqcd_clover_invert(lqcd_ctx *ctx, double kappa, double csw, double *logdet_ee,
+                               double *logdet_oo);
+
+/* out = A(x) in (inverse = 0) or A(x)^-1 in (inverse = 1) on the sites of one
+ * parity; in, out: canonical FP64 half-lattice spinors (Eq. 1 / Eq. 2). */
+LQCD_API lqcd_status lqcd_apply_clover(lqcd_ctx *ctx, int parity, int inverse, const double *in_dev,
+                              double *out_dev);
+
+/* -------------------------------------------------------------- operators */
+
+/* out = D in on the full lattice (Eq. 1).  in, out: nrhs canonical full
+ * spinor fields of precision prec (F64: double, F32: float).  in != out. */
+LQCD_API lqcd_status lqcd_apply_D(lqcd_ctx *ctx, lqcd_prec prec, const void *in_dev, void *out_dev,
+                         int nrhs);
+
+/* out_e = Dhat in_e = A_ee in_e - H_eo A_oo^-1 H_oe in_e (Eq. 2) on even
+ * fields; in, out: nrhs canonical even spinor fields of precision prec. */
+LQCD_API lqcd_status lqcd_apply_Dhat(lqcd_ctx *ctx, lqcd_prec prec, const void *in_dev, void *out_dev,
+                            int nrhs);
+
+/* Native (device-private, resident) layout for repeated applications.
+ * A native half-lattice field of precision prec and nrhs right-hand sides is
+ * lqcd_native_bytes(ctx, prec, 1, nrhs) bytes (a full field: nsub = 2, the
+ * even half first).  Layout, for sites s of one parity, rhs k:
+ *   F64:  double2 at [(k*12 + c) * Vh + s], c = 3*spin+colour
+ *   F32:  float4  at [(k*6 + q) * Vh + s],  q-th group of 4 reals of the site
+ *   F16S: uint4 (8 halves) at [(k*3 + q) * Vh + s], then one float scale per
+ *         (k, s) after all nrhs*3*Vh uint4 (value = half * scale).
+ * Pack / unpack convert between canonical and native fields. */
+LQCD_API size_t lqcd_native_bytes(const lqcd_ctx *ctx, lqcd_prec prec, int nsub, int nrhs);
+LQCD_API lqcd_status lqcd_pack(lqcd_ctx *ctx, lqcd_prec prec, int nsub, const void *canon_dev,
+                      void *native_dev, int nrhs);
+LQCD_API lqcd_status lqcd_unpack(lqcd_ctx *ctx, lqcd_prec prec, int nsub, const void *native_dev,
+                        void *canon_dev, int nrhs);
+/* Dhat / D on native fields: the benchmarked kernels, no layout conversion. */
+LQCD_API lqcd_status lqcd_apply_Dhat_native(lqcd_ctx *ctx, lqcd_prec prec, const void *in_dev,
+                                   void *out_dev, int nrhs);
+LQCD_API lqcd_status lqcd_apply_D_native(lqcd_ctx *ctx, lqcd_prec prec, const void *in_dev, void *out_dev,
+                                int nrhs);
+
+/* -------------------------------------------------------------------- SAP */
+
+typedef struct {
+    int bs[4];       /* block extents (even, dividing the lattice); 4,4,4,4 */
+    int ncy;         /* Schwarz cycles (each: both block colours) */
+    int nmr;         /* MinRes steps per block visit */
+    lqcd_prec prec;  /* block-solve precision */
+} lqcd_sap_params;
+
+/* psi = M_sap eta: Schwarz alternating procedure on the block colours with
+ * even-odd block MinRes (the Schwarz preconditioner of Sec. 3-4).
+ * eta, psi: canonical FP64 full spinors.  Errors: LQCD_ERR_ARG for a block
+ * shape that does not tile the lattice. */
+LQCD_API lqcd_status lqcd_sap(lqcd_ctx *ctx, const lqcd_sap_params *p, const double *eta_dev,
+                     double *psi_dev);
+
+/* -------------------------------------------------------------- deflation */
+
+typedef struct {
+    int bs[4];        /* deflation block extents; 4,4,4,4 */
+    int Ns;           /* subspace vectors per block (<= 32) */
+    int ninv;         /* SAP inverse-iteration passes */
+    int ncy, nmr;     /* SAP parameters used in the passes */
+    lqcd_prec prec;   /* SAP precision used in the passes */
+    double coarse_tol;/* relative residual of the little-Dirac solve */
+    int coarse_nkv;   /* GCR Krylov length of the little-Dirac solve */
+    int coarse_nmx;   /* iteration limit of the little-Dirac solve */
+} lqcd_dfl_params;
+
+/* Build the deflation subspace ("locally deflated" solver, Sec. 3-4,
+ * Table 1): v_l <- M_sap v_l, normalised, ninv times; block Gram-Schmidt on
+ * every block; little Dirac operator A_{(L k),(L' l)} = <phi^L_k, D phi^L'_l>.
+ * v0_dev: Ns canonical FP64 full fields (the random start vectors; the
+ * caller draws them).  Requires lqcd_clover_invert. */
+LQCD_API lqcd_status lqcd_dfl_build(lqcd_ctx *ctx, const lqcd_dfl_params *p, const double *v0_dev);
+/* Export: the block-orthonormal fields (Ns canonical FP64 full fields) and
+ * the little operator as [nblk][9][Ns][Ns] complex (entry j of block b couples
+ * to the neighbour reached by direction j: 0 self, 1+2mu: +mu, 2+2mu: -mu;
+ * hops that stay in the block are part of entry 0). */
+LQCD_API lqcd_status lqcd_dfl_export(lqcd_ctx *ctx, double *phi_dev, double *A_dev);
+/* c = Pi^dag in (in: canonical FP64 full field; c: nblk*Ns complex),
+ * out = Pi c, out = A c, and the coarse solve A c = b (plain FP64 GCR). */
+LQCD_API lqcd_status lqcd_dfl_project(lqcd_ctx *ctx, const double *in_dev, double *c_dev);
+LQCD_API lqcd_status lqcd_dfl_expand(lqcd_ctx *ctx, const double *c_dev, double *out_dev);
+LQCD_API lqcd_status lqcd_dfl_little_apply(lqcd_ctx *ctx, const double *c_dev, double *out_dev);
+LQCD_API lqcd_status lqcd_dfl_coarse_solve(lqcd_ctx *ctx, const double *b_dev, double *c_dev, int *iters);
+/* phi = M_dfl rho = M_sap(rho - D Pi A^-1 Pi^dag rho) + Pi A^-1 Pi^dag rho. */
+LQCD_API lqcd_status lqcd_dfl_precond(lqcd_ctx *ctx, const lqcd_sap_params *sap, const double *rho_dev,
+                             double *phi_dev);
+
+/* ----------------------------------------------------------------- solvers */
+
+typedef enum {
+    LQCD_SOLVER_CGNR = 0,     /* even-odd CG on Dhat^dag Dhat (FP64) */
+    LQCD_SOLVER_SAP_GCR = 1,  /* flexible GCR, SAP preconditioner */
+    LQCD_SOLVER_DFL_SAP_GCR = 2 /* flexible GCR, deflated SAP preconditioner */
+} lqcd_solver;
+
+typedef struct {
+    lqcd_solver solver;
+    int nkv;                 /* GCR Krylov length before restart (<= 64) */
+    int nmx;                 /* iteration limit */
+    double tol;              /* target true relative residual */
+    lqcd_sap_params sap;     /* preconditioner */
+    lqcd_prec inner;         /* precision of the preconditioner output and of D phi_k */
+} lqcd_solver_params;
+
+typedef struct {
+    int iters;               /* preconditioned GCR steps (or CG iterations) */
+    int restarts;            /* FP64 true-residual recomputations */
+    double true_relres;      /* |eta - D psi| / |eta| in FP64 (full system) */
+    double relres_dhat;      /* |eta_e - Dhat psi_e| / |eta_e| in FP64 */
+    double seconds;          /* wall time of the solve */
+    lqcd_status status;
+} lqcd_solve_info;
+
+/* Solve Dhat psi_e = eta_e (Eq. 2) for nrhs even fields to a true relative
+ * residual <= tol.  CGNR works on Dhat directly; the GCR solvers solve the
+ * full system D chi = (eta_e, 0) and return psi_e = chi_e (Eq. 5), then
+ * check the Dhat residual in FP64 and tighten the tolerance when needed.
+ * eta_e, psi_e: nrhs canonical FP64 even fields.  info: host array of nrhs
+ * entries (may be NULL).  Returns the worst per-RHS status. */
+LQCD_API lqcd_status lqcd_solve_dhat(lqcd_ctx *ctx, const lqcd_solver_params *p, const double *eta_dev,
+                            double *psi_dev, int nrhs, lqcd_solve_info *info);
+
+/* Solve D psi = eta on the full lattice (GCR solvers only); canonical FP64. */
+LQCD_API lqcd_status lqcd_solve_D(lqcd_ctx *ctx, const lqcd_solver_params *p, const double *eta_dev,
+                         double *psi_dev, int nrhs, lqcd_solve_info *info);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif

@@ -60,6 +60,7 @@ def lib():
             "or_dfl_coarse_solve": (I, [P, P, P, D, I, I, IP]),
             "or_dfl_precond": (None, [P, IP, I, I, D, P, P]),
             "or_dfl_subspace": (None, [P, P]),
+            "or_num_threads": (I, []),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -76,6 +77,11 @@ def _p(a: np.ndarray):
 
 def _c(a) -> np.ndarray:
     return np.ascontiguousarray(a, dtype=np.complex128)
+
+
+def num_threads() -> int:
+    """OpenMP threads used by the oracle's site loops."""
+    return lib().or_num_threads()
 
 
 def gamma(mu: int) -> np.ndarray:

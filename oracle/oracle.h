@@ -82,6 +82,7 @@ void or_apply_gamma5(long n, const double *in, double *out);
 void or_dhat_site(const oracle *o, const double *in_e, long xe, double *out12);
 void or_d_site(const oracle *o, const double *in, long x, double *out12);
 long or_even_rank_to_site(const oracle *o, int parity, long r);
+int or_num_threads(void);
 
 /* --- solvers (oracle_solvers.c) --- */
 int or_cgnr(const oracle *o, const double *eta_e, double *psi_e, double tol, int maxit,

@@ -548,3 +548,16 @@ void or_dhat_site(const oracle *o, const double *in_e_, long re, double *out12)
         }
     for (int i = 0; i < 12; i++) ((ocplx *)out12)[i] = acc[i];
 }
+
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+/* threads the oracle's site loops use (reported with CPU timings) */
+int or_num_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}

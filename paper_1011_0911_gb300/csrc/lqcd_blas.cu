@@ -1,0 +1,229 @@
+// FP64 BLAS-1 on complex vectors (arrays of re,im doubles) for the outer
+// solvers: batched dot products with a fixed reduction order (results are
+// bitwise reproducible run to run), axpy forms, gamma5.
+#include <algorithm>
+
+#include "lqcd_internal.cuh"
+
+namespace {
+
+constexpr int RED_BLOCKS = 304;   // 2 x 152 SMs
+constexpr int RED_THREADS = 256;
+constexpr int DOT_CHUNK = 8;
+
+// partial[b][i] (complex) = sum over this block's slice of conj(a_i) b
+__global__ void __launch_bounds__(RED_THREADS) k_dot_partial(long n, const double2 *__restrict__ A, long sa,
+                                                             const double2 *__restrict__ B, int k0, int kn,
+                                                             double2 *partial)
+{
+    double re[DOT_CHUNK], im[DOT_CHUNK];
+#pragma unroll
+    for (int i = 0; i < DOT_CHUNK; i++) re[i] = im[i] = 0;
+    for (long j = blockIdx.x * (long)blockDim.x + threadIdx.x; j < n; j += (long)gridDim.x * blockDim.x) {
+        double2 b = B[j];
+#pragma unroll
+        for (int i = 0; i < DOT_CHUNK; i++)
+            if (i < kn) {
+                double2 a = A[(k0 + i) * sa + j];
+                re[i] += a.x * b.x + a.y * b.y;
+                im[i] += a.x * b.y - a.y * b.x;
+            }
+    }
+    __shared__ double sh[RED_THREADS / 32][DOT_CHUNK][2];
+    int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int i = 0; i < DOT_CHUNK; i++) {
+        double r = re[i], m = im[i];
+        for (int o = 16; o > 0; o >>= 1) {
+            r += __shfl_down_sync(0xffffffffu, r, o);
+            m += __shfl_down_sync(0xffffffffu, m, o);
+        }
+        if (lane == 0) {
+            sh[warp][i][0] = r;
+            sh[warp][i][1] = m;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < kn) {
+        double r = 0, m = 0;
+        for (int w = 0; w < RED_THREADS / 32; w++) {
+            r += sh[w][threadIdx.x][0];
+            m += sh[w][threadIdx.x][1];
+        }
+        partial[(long)blockIdx.x * 64 + k0 + threadIdx.x] = make_double2(r, m);
+    }
+}
+
+__global__ void k_dot_final(int nblk, int k, const double2 *partial, double2 *out)
+{
+    int i = threadIdx.x;
+    if (i >= k) return;
+    double r = 0, m = 0;
+    for (int b = 0; b < nblk; b++) {
+        double2 v = partial[(long)b * 64 + i];
+        r += v.x;
+        m += v.y;
+    }
+    out[i] = make_double2(r, m);
+}
+
+__global__ void k_axpy(long n, double ar, double ai, const double2 *__restrict__ x, double2 *y)
+{
+    for (long j = blockIdx.x * (long)blockDim.x + threadIdx.x; j < n; j += (long)gridDim.x * blockDim.x) {
+        double2 a = x[j], b = y[j];
+        b.x += ar * a.x - ai * a.y;
+        b.y += ar * a.y + ai * a.x;
+        y[j] = b;
+    }
+}
+__global__ void k_xpay(long n, const double2 *__restrict__ x, double ar, double2 *y)
+{
+    for (long j = blockIdx.x * (long)blockDim.x + threadIdx.x; j < n; j += (long)gridDim.x * blockDim.x) {
+        double2 a = x[j], b = y[j];
+        y[j] = make_double2(a.x + ar * b.x, a.y + ar * b.y);
+    }
+}
+__global__ void k_scal(long n, double ar, double ai, double2 *y)
+{
+    for (long j = blockIdx.x * (long)blockDim.x + threadIdx.x; j < n; j += (long)gridDim.x * blockDim.x) {
+        double2 b = y[j];
+        y[j] = make_double2(ar * b.x - ai * b.y, ar * b.y + ai * b.x);
+    }
+}
+__global__ void k_sub(long n, const double2 *__restrict__ x, const double2 *__restrict__ y, double2 *z)
+{
+    for (long j = blockIdx.x * (long)blockDim.x + threadIdx.x; j < n; j += (long)gridDim.x * blockDim.x) {
+        double2 a = x[j], b = y[j];
+        z[j] = make_double2(a.x - b.x, a.y - b.y);
+    }
+}
+// y += sign * sum_i c_i X_i  (c complex, up to 64 terms)
+struct Coefs {
+    double c[2 * 64];
+};
+__global__ void k_multi_axpy(long n, int k, Coefs cf, const double2 *__restrict__ X, long stride, double2 *y,
+                             double sign)
+{
+    for (long j = blockIdx.x * (long)blockDim.x + threadIdx.x; j < n; j += (long)gridDim.x * blockDim.x) {
+        double2 b = y[j];
+        double sr = 0, si = 0;
+        for (int i = 0; i < k; i++) {
+            double2 a = X[i * stride + j];
+            sr += cf.c[2 * i] * a.x - cf.c[2 * i + 1] * a.y;
+            si += cf.c[2 * i] * a.y + cf.c[2 * i + 1] * a.x;
+        }
+        y[j] = make_double2(b.x + sign * sr, b.y + sign * si);
+    }
+}
+// gamma5 = diag(1,1,-1,-1): negate spins 2,3 = complex components 6..11
+__global__ void k_gamma5_64(long Vh, long nhalf, const double2 *__restrict__ in, double2 *out)
+{
+    long r = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    long h = blockIdx.y;
+    if (r >= Vh || h >= nhalf) return;
+    const double2 *i = in + h * 12 * Vh + r;
+    double2 *o = out + h * 12 * Vh + r;
+    for (int c = 0; c < 12; c++) {
+        double2 v = i[c * Vh];
+        o[c * Vh] = c < 6 ? v : make_double2(-v.x, -v.y);
+    }
+}
+
+inline int grid_for(long n) { return (int)std::min<long>(4 * 152, (n + 255) / 256); }
+
+}  // namespace
+
+lqcd_status blas_dot(lqcd_ctx *c, long n2, const double *A, const double *B, int k, long stride_a,
+                     double *host_out)
+{
+    if (k < 1 || k > 64) return set_err(c, LQCD_ERR_ARG, "blas_dot: k=%d", k);
+    long n = n2 / 2;
+    double2 *partial = (double2 *)c->red;
+    for (int k0 = 0; k0 < k; k0 += DOT_CHUNK) {
+        int kn = std::min(DOT_CHUNK, k - k0);
+        k_dot_partial<<<RED_BLOCKS, RED_THREADS, 0, c->stream>>>(n, (const double2 *)A, stride_a / 2,
+                                                                 (const double2 *)B, k0, kn, partial);
+        c->n_kernel_launches++;
+    }
+    k_dot_final<<<1, 64, 0, c->stream>>>(RED_BLOCKS, k, partial, (double2 *)c->red_out);
+    c->n_kernel_launches++;
+    LQCD_LAUNCH_CHECK(c);
+    LQCD_CUDA_CHECK(c, cudaMemcpyAsync(c->red_host, c->red_out, 2 * k * sizeof(double), cudaMemcpyDeviceToHost,
+                                       c->stream));
+    LQCD_CUDA_CHECK(c, cudaStreamSynchronize(c->stream));
+    for (int i = 0; i < 2 * k; i++) host_out[i] = c->red_host[i];
+    return LQCD_OK;
+}
+
+lqcd_status blas_norm2(lqcd_ctx *c, long n2, const double *a, double *host_out)
+{
+    double t[2];
+    LQCD_TRY(blas_dot(c, n2, a, a, 1, 0, t));
+    *host_out = t[0];
+    return LQCD_OK;
+}
+
+lqcd_status blas_axpy(lqcd_ctx *c, long n2, double ar, double ai, const double *x, double *y)
+{
+    long n = n2 / 2;
+    k_axpy<<<grid_for(n), 256, 0, c->stream>>>(n, ar, ai, (const double2 *)x, (double2 *)y);
+    c->n_kernel_launches++;
+    LQCD_LAUNCH_CHECK(c);
+    return LQCD_OK;
+}
+lqcd_status blas_xpay(lqcd_ctx *c, long n2, const double *x, double ar, double *y)
+{
+    long n = n2 / 2;
+    k_xpay<<<grid_for(n), 256, 0, c->stream>>>(n, (const double2 *)x, ar, (double2 *)y);
+    c->n_kernel_launches++;
+    LQCD_LAUNCH_CHECK(c);
+    return LQCD_OK;
+}
+lqcd_status blas_scal(lqcd_ctx *c, long n2, double ar, double ai, double *y)
+{
+    long n = n2 / 2;
+    k_scal<<<grid_for(n), 256, 0, c->stream>>>(n, ar, ai, (double2 *)y);
+    c->n_kernel_launches++;
+    LQCD_LAUNCH_CHECK(c);
+    return LQCD_OK;
+}
+lqcd_status blas_sub(lqcd_ctx *c, long n2, const double *x, const double *y, double *z)
+{
+    long n = n2 / 2;
+    k_sub<<<grid_for(n), 256, 0, c->stream>>>(n, (const double2 *)x, (const double2 *)y, (double2 *)z);
+    c->n_kernel_launches++;
+    LQCD_LAUNCH_CHECK(c);
+    return LQCD_OK;
+}
+lqcd_status blas_copy(lqcd_ctx *c, long n2, const double *x, double *y)
+{
+    LQCD_CUDA_CHECK(c, cudaMemcpyAsync(y, x, n2 * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    return LQCD_OK;
+}
+lqcd_status blas_zero(lqcd_ctx *c, size_t bytes, void *p)
+{
+    LQCD_CUDA_CHECK(c, cudaMemsetAsync(p, 0, bytes, c->stream));
+    return LQCD_OK;
+}
+lqcd_status blas_multi_axpy(lqcd_ctx *c, long n2, int k, const double *coef_host, const double *X, long stride,
+                            double *y, double sign)
+{
+    if (k < 1) return LQCD_OK;
+    if (k > 64) return set_err(c, LQCD_ERR_ARG, "multi_axpy: k=%d", k);
+    Coefs cf;
+    for (int i = 0; i < 2 * k; i++) cf.c[i] = coef_host[i];
+    long n = n2 / 2;
+    k_multi_axpy<<<grid_for(n), 256, 0, c->stream>>>(n, k, cf, (const double2 *)X, stride / 2, (double2 *)y,
+                                                     sign);
+    c->n_kernel_launches++;
+    LQCD_LAUNCH_CHECK(c);
+    return LQCD_OK;
+}
+lqcd_status blas_gamma5_native64(lqcd_ctx *c, long nhalf, const double2 *in, double2 *out)
+{
+    dim3 grid(div_up(c->g.Vh, 256), (unsigned)nhalf);
+    k_gamma5_64<<<grid, 256, 0, c->stream>>>(c->g.Vh, nhalf, in, out);
+    c->n_kernel_launches++;
+    LQCD_LAUNCH_CHECK(c);
+    return LQCD_OK;
+}

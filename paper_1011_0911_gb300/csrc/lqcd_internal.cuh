@@ -1,0 +1,193 @@
+// Internal declarations of the sm_103a Wilson-clover library: context,
+// device-private ("native") layouts, geometry and the chiral-basis spin
+// algebra of the hopping term (Eq. 1).
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "lqcd.h"
+
+// ------------------------------------------------------------------ complex
+template <class R>
+struct cx {
+    R re, im;
+};
+template <class R>
+__host__ __device__ __forceinline__ cx<R> mk(R a, R b) { return cx<R>{a, b}; }
+template <class R>
+__device__ __forceinline__ cx<R> operator+(cx<R> a, cx<R> b) { return {a.re + b.re, a.im + b.im}; }
+template <class R>
+__device__ __forceinline__ cx<R> operator-(cx<R> a, cx<R> b) { return {a.re - b.re, a.im - b.im}; }
+template <class R>
+__device__ __forceinline__ cx<R> operator-(cx<R> a) { return {-a.re, -a.im}; }
+template <class R>
+__device__ __forceinline__ cx<R> operator*(cx<R> a, cx<R> b)
+{
+    return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
+}
+template <class R>
+__device__ __forceinline__ cx<R> operator*(R s, cx<R> a) { return {s * a.re, s * a.im}; }
+template <class R>
+__device__ __forceinline__ cx<R> conjx(cx<R> a) { return {a.re, -a.im}; }
+template <class R>
+__device__ __forceinline__ cx<R> timesI(cx<R> a) { return {-a.im, a.re}; }   // i a
+template <class R>
+__device__ __forceinline__ cx<R> timesmI(cx<R> a) { return {a.im, -a.re}; }  // -i a
+// a * b with a conjugated
+template <class R>
+__device__ __forceinline__ cx<R> cmulc(cx<R> a, cx<R> b)
+{
+    return {a.re * b.re + a.im * b.im, a.re * b.im - a.im * b.re};
+}
+
+// ------------------------------------------------------------------ geometry
+struct Geom {
+    int L[4];      // L[0] = T
+    int V, Vh;
+    int L3h;       // L3 / 2
+    int bc_t;      // -1 antiperiodic fermion field in time, +1 periodic
+};
+
+// coordinates of the site of parity p and rank r (site = 2r + b)
+__device__ __forceinline__ void rank_coords(const Geom &g, int p, int r, int x[4])
+{
+    int row = r / g.L3h;
+    int x3h = r - row * g.L3h;
+    int t = row / g.L[2];
+    x[2] = row - t * g.L[2];
+    x[0] = t / g.L[1];
+    x[1] = t - x[0] * g.L[1];
+    int b = (p + x[0] + x[1] + x[2]) & 1;
+    x[3] = 2 * x3h + b;
+}
+__device__ __forceinline__ int coords_rank(const Geom &g, const int x[4])
+{
+    return (x[3] + g.L[3] * (x[2] + g.L[2] * (x[1] + g.L[1] * x[0]))) >> 1;
+}
+// rank of the neighbour x + d*mu (d = +-1), periodic wrap
+__device__ __forceinline__ int nbr_rank(const Geom &g, const int x[4], int mu, int d)
+{
+    int y[4] = {x[0], x[1], x[2], x[3]};
+    int v = y[mu] + d;
+    y[mu] = v < 0 ? v + g.L[mu] : (v >= g.L[mu] ? v - g.L[mu] : v);
+    return coords_rank(g, y);
+}
+
+// ------------------------------------------------------------------ context
+struct Workspace {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+struct DflState;   // deflation subspace (lqcd_dfl.cu)
+
+struct lqcd_ctx {
+    lqcd_geom geom;
+    Geom g;
+    cudaStream_t stream = nullptr;
+    char err[512] = {0};
+    // gauge field, native layouts
+    double2 *U64 = nullptr;   // [p][mu][9][Vh]      full SU(3), FP64
+    float4 *U32 = nullptr;    // [p][mu][3][Vh]      two rows, FP32
+    uint2 *U16 = nullptr;     // [p][mu][3][Vh]      two rows, FP16 (4 halves per uint2)
+    bool have_gauge = false;
+    // clover term: A and A^-1 for both parities, packed Hermitian 6x6 pairs
+    double2 *A64[2] = {nullptr, nullptr}, *Ai64[2] = {nullptr, nullptr};  // [36][Vh]
+    float4 *A32[2] = {nullptr, nullptr}, *Ai32[2] = {nullptr, nullptr};   // [18][Vh]
+    bool have_clover = false;
+    double kappa = 0, csw = 0;
+    // device scratch for reductions
+    double *red = nullptr;        // partial sums
+    double *red_out = nullptr;    // final reduction results (device)
+    double *red_host = nullptr;   // pinned host mirror
+    // named temporary buffers, grown on demand
+    Workspace ws[24];
+    DflState *dfl = nullptr;
+    long n_kernel_launches = 0;
+};
+
+// error helpers
+lqcd_status set_err(lqcd_ctx *c, lqcd_status s, const char *fmt, ...);
+#define LQCD_CUDA_CHECK(ctx, call)                                                          \
+    do {                                                                                    \
+        cudaError_t e__ = (call);                                                           \
+        if (e__ != cudaSuccess)                                                             \
+            return set_err(ctx, LQCD_ERR_CUDA, "%s:%d %s: %s", __FILE__, __LINE__, #call,   \
+                           cudaGetErrorString(e__));                                        \
+    } while (0)
+#define LQCD_LAUNCH_CHECK(ctx) LQCD_CUDA_CHECK(ctx, cudaGetLastError())
+#define LQCD_TRY(expr)                         \
+    do {                                       \
+        lqcd_status s__ = (expr);              \
+        if (s__ != LQCD_OK) return s__;        \
+    } while (0)
+
+// workspace slots
+enum {
+    WS_PACK_IN = 0,
+    WS_PACK_OUT,
+    WS_TMP_O,       // odd temporaries of Dhat
+    WS_SAP_R,
+    WS_SAP_PSI,
+    WS_SAP_IN,
+    WS_SOLVER,      // solver vectors
+    WS_DFL,
+    WS_CGNR,
+    WS_MISC,
+    WS_MISC2,
+    WS_COARSE,
+    WS_SOLVE_IO,
+};
+lqcd_status ws_get(lqcd_ctx *c, int slot, size_t bytes, void **out);
+
+// native element counts per site
+inline int native_chunks(lqcd_prec p) { return p == LQCD_F64 ? 12 : (p == LQCD_F32 ? 6 : 3); }
+inline size_t native_chunk_bytes(lqcd_prec p) { return p == LQCD_F64 ? 16 : (p == LQCD_F32 ? 16 : 16); }
+size_t native_half_bytes(const lqcd_ctx *c, lqcd_prec p);   // one rhs, one parity
+
+// launch helpers
+inline int div_up(long a, long b) { return (int)((a + b - 1) / b); }
+
+// --------------------------------------------------------------- internals
+// dirac
+lqcd_status dirac_dhat(lqcd_ctx *c, lqcd_prec p, const void *in, void *out, void *tmp_o, int nrhs);
+lqcd_status dirac_D(lqcd_ctx *c, lqcd_prec p, const void *in, void *out, int nrhs);
+lqcd_status dirac_hop_parity(lqcd_ctx *c, lqcd_prec p, int p_out, const void *in_other,
+                             void *out, long in_rstride, long out_rstride, int nrhs);
+lqcd_status convert_native(lqcd_ctx *c, lqcd_prec from, lqcd_prec to, const void *in, void *out,
+                           long nhalf);
+lqcd_status pack_field(lqcd_ctx *c, lqcd_prec p, int nsub, const void *canon, void *native,
+                       int nrhs, bool unpack);
+lqcd_status clover_build(lqcd_ctx *c, double kappa, double csw, double *ld_e, double *ld_o);
+lqcd_status clover_apply_native64(lqcd_ctx *c, int parity, int inverse, const double2 *in,
+                                  double2 *out);
+
+// blas (FP64 native vectors viewed as arrays of double; complex pairs)
+lqcd_status blas_dot(lqcd_ctx *c, long n2, const double *a, const double *b, int k, long stride_a,
+                     double *host_out);  // k dots <a_i, b>, host_out: 2k doubles
+lqcd_status blas_norm2(lqcd_ctx *c, long n2, const double *a, double *host_out);
+lqcd_status blas_axpy(lqcd_ctx *c, long n2, double ar, double ai, const double *x, double *y);
+lqcd_status blas_xpay(lqcd_ctx *c, long n2, const double *x, double ar, double *y);  // y = x + a y
+lqcd_status blas_scal(lqcd_ctx *c, long n2, double ar, double ai, double *y);
+lqcd_status blas_copy(lqcd_ctx *c, long n2, const double *x, double *y);
+lqcd_status blas_sub(lqcd_ctx *c, long n2, const double *x, const double *y, double *z);  // z = x - y
+lqcd_status blas_multi_axpy(lqcd_ctx *c, long n2, int k, const double *coef_host, const double *X,
+                            long stride, double *y, double sign);
+lqcd_status blas_gamma5_native64(lqcd_ctx *c, long nhalf, const double2 *in, double2 *out);
+lqcd_status blas_zero(lqcd_ctx *c, size_t bytes, void *p);
+
+// sap
+lqcd_status sap_axpby_native(lqcd_ctx *c, lqcd_prec p, const void *eta, void *r);
+void sap_free_plans(lqcd_ctx *c);
+lqcd_status sap_apply(lqcd_ctx *c, const lqcd_sap_params *sp, const void *eta_native,
+                      void *psi_native);
+// deflation
+void dfl_free(lqcd_ctx *c);
+lqcd_status dfl_precond_native(lqcd_ctx *c, const lqcd_sap_params *sp, const double2 *rho,
+                               double2 *phi);

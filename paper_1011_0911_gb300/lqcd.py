@@ -1,0 +1,309 @@
+"""Thin ctypes binding of liblqcd.so (include/lqcd.h).
+
+Argument marshalling only: every step of the computation runs in the
+library's CUDA kernels.  Fields are torch tensors on the GPU in the canonical
+layouts of lqcd.h (complex128 for FP64, complex64 for FP32):
+    full field  (V, 4, 3), even/odd field (V/2, 4, 3), nrhs fields stacked
+    in front; links (V, 4, 3, 3) complex128.
+There is no CPU path: if the library or a GPU is missing the first call
+raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import torch
+
+from . import build_lib
+
+F64, F32, F16S = 0, 1, 2
+SOLVER_CGNR, SOLVER_SAP_GCR, SOLVER_DFL_SAP_GCR = 0, 1, 2
+
+STATUS = {
+    0: "OK", 1: "ERR_ARG", 2: "ERR_CUDA", 3: "ERR_NOMEM", 4: "ERR_SINGULAR_CLOVER",
+    5: "ERR_NOT_CONVERGED", 6: "ERR_BREAKDOWN", 7: "ERR_NAN", 8: "ERR_TIMEOUT", 9: "ERR_STATE",
+}
+
+
+class LqcdError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Geom(C.Structure):
+    _fields_ = [("T", C.c_int), ("L1", C.c_int), ("L2", C.c_int), ("L3", C.c_int), ("antiperiodic_t", C.c_int)]
+
+
+class SapParams(C.Structure):
+    _fields_ = [("bs", C.c_int * 4), ("ncy", C.c_int), ("nmr", C.c_int), ("prec", C.c_int)]
+
+
+class DflParams(C.Structure):
+    _fields_ = [("bs", C.c_int * 4), ("Ns", C.c_int), ("ninv", C.c_int), ("ncy", C.c_int), ("nmr", C.c_int),
+                ("prec", C.c_int), ("coarse_tol", C.c_double), ("coarse_nkv", C.c_int), ("coarse_nmx", C.c_int)]
+
+
+class SolverParams(C.Structure):
+    _fields_ = [("solver", C.c_int), ("nkv", C.c_int), ("nmx", C.c_int), ("tol", C.c_double),
+                ("sap", SapParams), ("inner", C.c_int)]
+
+
+class SolveInfo(C.Structure):
+    _fields_ = [("iters", C.c_int), ("restarts", C.c_int), ("true_relres", C.c_double),
+                ("relres_dhat", C.c_double), ("seconds", C.c_double), ("status", C.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+
+def lib_path() -> str:
+    return build_lib.LIB
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        if build_lib.needs_build():
+            build_lib.build()
+        if not os.path.exists(build_lib.LIB):
+            raise RuntimeError("liblqcd.so is missing: run __graft_entry__.build()")
+        L = C.CDLL(build_lib.LIB)
+        P, I, D, S = C.c_void_p, C.c_int, C.c_double, C.c_size_t
+        sig = {
+            "lqcd_create": [C.POINTER(Geom), P, C.POINTER(P)],
+            "lqcd_destroy": [P],
+            "lqcd_set_stream": [P, P],
+            "lqcd_set_gauge": [P, P],
+            "lqcd_clover_invert": [P, D, D, C.POINTER(D), C.POINTER(D)],
+            "lqcd_apply_clover": [P, I, I, P, P],
+            "lqcd_apply_D": [P, I, P, P, I],
+            "lqcd_apply_Dhat": [P, I, P, P, I],
+            "lqcd_pack": [P, I, I, P, P, I],
+            "lqcd_unpack": [P, I, I, P, P, I],
+            "lqcd_apply_Dhat_native": [P, I, P, P, I],
+            "lqcd_apply_D_native": [P, I, P, P, I],
+            "lqcd_sap": [P, C.POINTER(SapParams), P, P],
+            "lqcd_dfl_build": [P, C.POINTER(DflParams), P],
+            "lqcd_dfl_export": [P, P, P],
+            "lqcd_dfl_project": [P, P, P],
+            "lqcd_dfl_expand": [P, P, P],
+            "lqcd_dfl_little_apply": [P, P, P],
+            "lqcd_dfl_coarse_solve": [P, P, P, C.POINTER(I)],
+            "lqcd_dfl_precond": [P, C.POINTER(SapParams), P, P],
+            "lqcd_solve_dhat": [P, C.POINTER(SolverParams), P, P, I, C.POINTER(SolveInfo)],
+            "lqcd_solve_D": [P, C.POINTER(SolverParams), P, P, I, C.POINTER(SolveInfo)],
+        }
+        for name, args in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = C.c_int
+        L.lqcd_last_error.argtypes = [P]
+        L.lqcd_last_error.restype = C.c_char_p
+        L.lqcd_native_bytes.argtypes = [P, I, I, I]
+        L.lqcd_native_bytes.restype = S
+        L.lqcd_kernel_launches.argtypes = [P]
+        L.lqcd_kernel_launches.restype = C.c_long
+        _lib = L
+    return _lib
+
+
+def _ptr(t: torch.Tensor):
+    if not t.is_cuda:
+        raise ValueError("liblqcd takes device tensors only")
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return C.c_void_p(t.data_ptr())
+
+
+def _dtype(prec):
+    return {F64: torch.complex128, F32: torch.complex64}[prec]
+
+
+def sap_params(bs=(4, 4, 4, 4), ncy=4, nmr=5, prec=F64) -> SapParams:
+    return SapParams((C.c_int * 4)(*bs), ncy, nmr, prec)
+
+
+class Context:
+    """One lattice on the current CUDA device; all work on the given stream
+    (default: torch's current stream at creation)."""
+
+    def __init__(self, dims, antiperiodic_t: bool = True, stream=None):
+        self.dims = tuple(int(d) for d in dims)
+        T, L1, L2, L3 = self.dims
+        self.V = T * L1 * L2 * L3
+        self.Vh = self.V // 2
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        h = C.c_void_p()
+        g = Geom(T, L1, L2, L3, 1 if antiperiodic_t else 0)
+        st = lib().lqcd_create(C.byref(g), C.c_void_p(stream.cuda_stream), C.byref(h))
+        if st != 0:
+            raise LqcdError(st, f"lqcd_create{self.dims}")
+        self._h = h
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.lqcd_destroy(self._h)
+            self._h = None
+
+    def _check(self, st, what):
+        if st != 0:
+            msg = lib().lqcd_last_error(self._h)
+            raise LqcdError(st, f"{what}: {msg.decode() if msg else ''}")
+
+    @property
+    def kernel_launches(self) -> int:
+        return lib().lqcd_kernel_launches(self._h)
+
+    # ---------------------------------------------------------------- setup
+    def set_gauge(self, U: torch.Tensor):
+        U = U.to(torch.complex128).contiguous()
+        assert U.numel() == self.V * 36
+        self._U = U
+        self._check(lib().lqcd_set_gauge(self._h, _ptr(U)), "lqcd_set_gauge")
+
+    def clover_invert(self, kappa: float, csw: float):
+        le, lo = C.c_double(), C.c_double()
+        st = lib().lqcd_clover_invert(self._h, float(kappa), float(csw), C.byref(le), C.byref(lo))
+        self._check(st, "lqcd_clover_invert")
+        return le.value, lo.value
+
+    def apply_clover(self, parity: int, inverse: bool, x: torch.Tensor) -> torch.Tensor:
+        x = x.to(torch.complex128).contiguous()
+        out = torch.empty_like(x)
+        self._check(lib().lqcd_apply_clover(self._h, parity, int(inverse), _ptr(x), _ptr(out)), "apply_clover")
+        return out
+
+    # ------------------------------------------------------------ operators
+    def _nrhs(self, x, nsites):
+        n = x.numel() // (12 * nsites)
+        assert n * 12 * nsites == x.numel(), "field size mismatch"
+        return n
+
+    def apply_D(self, x: torch.Tensor, prec=F64) -> torch.Tensor:
+        x = x.to(_dtype(prec)).contiguous()
+        out = torch.empty_like(x)
+        self._check(lib().lqcd_apply_D(self._h, prec, _ptr(x), _ptr(out), self._nrhs(x, self.V)), "apply_D")
+        return out
+
+    def apply_Dhat(self, x: torch.Tensor, prec=F64) -> torch.Tensor:
+        x = x.to(_dtype(prec)).contiguous()
+        out = torch.empty_like(x)
+        self._check(lib().lqcd_apply_Dhat(self._h, prec, _ptr(x), _ptr(out), self._nrhs(x, self.Vh)),
+                    "apply_Dhat")
+        return out
+
+    def native_bytes(self, prec, nsub, nrhs) -> int:
+        return lib().lqcd_native_bytes(self._h, prec, nsub, nrhs)
+
+    def native_empty(self, prec, nsub, nrhs) -> torch.Tensor:
+        n = self.native_bytes(prec, nsub, nrhs)
+        return torch.empty(n, dtype=torch.uint8, device="cuda")
+
+    def pack(self, x: torch.Tensor, prec, nsub) -> torch.Tensor:
+        x = x.to(_dtype(prec)).contiguous()
+        nrhs = self._nrhs(x, nsub * self.Vh)
+        out = self.native_empty(prec, nsub, nrhs)
+        self._check(lib().lqcd_pack(self._h, prec, nsub, _ptr(x), _ptr(out), nrhs), "pack")
+        return out
+
+    def unpack(self, n: torch.Tensor, prec, nsub, nrhs) -> torch.Tensor:
+        out = torch.empty((nrhs, nsub * self.Vh, 4, 3), dtype=_dtype(prec), device="cuda")
+        self._check(lib().lqcd_unpack(self._h, prec, nsub, _ptr(n), _ptr(out), nrhs), "unpack")
+        return out
+
+    def apply_Dhat_native(self, x_native, out_native, prec, nrhs):
+        self._check(lib().lqcd_apply_Dhat_native(self._h, prec, _ptr(x_native), _ptr(out_native), nrhs),
+                    "apply_Dhat_native")
+
+    def apply_D_native(self, x_native, out_native, prec, nrhs):
+        self._check(lib().lqcd_apply_D_native(self._h, prec, _ptr(x_native), _ptr(out_native), nrhs),
+                    "apply_D_native")
+
+    # ------------------------------------------------------------------ SAP
+    def sap(self, eta: torch.Tensor, bs=(4, 4, 4, 4), ncy=4, nmr=5, prec=F64) -> torch.Tensor:
+        eta = eta.to(torch.complex128).contiguous()
+        out = torch.empty_like(eta)
+        p = sap_params(bs, ncy, nmr, prec)
+        self._check(lib().lqcd_sap(self._h, C.byref(p), _ptr(eta), _ptr(out)), "lqcd_sap")
+        return out
+
+    # ------------------------------------------------------------ deflation
+    def dfl_build(self, v0: torch.Tensor, bs=(4, 4, 4, 4), ninv=4, ncy=4, nmr=4, prec=F32, coarse_tol=1e-8,
+                  coarse_nkv=16, coarse_nmx=4096):
+        v0 = v0.to(torch.complex128).contiguous()
+        Ns = v0.numel() // (12 * self.V)
+        self.Ns = Ns
+        nb = 1
+        for L, b in zip(self.dims, bs):
+            nb *= L // b
+        self.nblk = nb
+        p = DflParams((C.c_int * 4)(*bs), Ns, ninv, ncy, nmr, prec, coarse_tol, coarse_nkv, coarse_nmx)
+        self._check(lib().lqcd_dfl_build(self._h, C.byref(p), _ptr(v0)), "lqcd_dfl_build")
+
+    def dfl_export(self):
+        phi = torch.empty((self.Ns, self.V, 4, 3), dtype=torch.complex128, device="cuda")
+        A = torch.empty((self.nblk, 9, self.Ns, self.Ns), dtype=torch.complex128, device="cuda")
+        self._check(lib().lqcd_dfl_export(self._h, _ptr(phi), _ptr(A)), "lqcd_dfl_export")
+        return phi, A
+
+    def dfl_project(self, x):
+        x = x.to(torch.complex128).contiguous()
+        c = torch.empty(self.nblk * self.Ns, dtype=torch.complex128, device="cuda")
+        self._check(lib().lqcd_dfl_project(self._h, _ptr(x), _ptr(c)), "dfl_project")
+        return c
+
+    def dfl_expand(self, c):
+        c = c.to(torch.complex128).contiguous()
+        out = torch.empty((self.V, 4, 3), dtype=torch.complex128, device="cuda")
+        self._check(lib().lqcd_dfl_expand(self._h, _ptr(c), _ptr(out)), "dfl_expand")
+        return out
+
+    def dfl_little_apply(self, c):
+        c = c.to(torch.complex128).contiguous()
+        out = torch.empty_like(c)
+        self._check(lib().lqcd_dfl_little_apply(self._h, _ptr(c), _ptr(out)), "dfl_little_apply")
+        return out
+
+    def dfl_coarse_solve(self, b):
+        b = b.to(torch.complex128).contiguous()
+        out = torch.empty_like(b)
+        it = C.c_int(0)
+        self._check(lib().lqcd_dfl_coarse_solve(self._h, _ptr(b), _ptr(out), C.byref(it)), "dfl_coarse_solve")
+        return out, it.value
+
+    def dfl_precond(self, rho, bs=(4, 4, 4, 4), ncy=4, nmr=5, prec=F64):
+        rho = rho.to(torch.complex128).contiguous()
+        out = torch.empty_like(rho)
+        p = sap_params(bs, ncy, nmr, prec)
+        self._check(lib().lqcd_dfl_precond(self._h, C.byref(p), _ptr(rho), _ptr(out)), "dfl_precond")
+        return out
+
+    # -------------------------------------------------------------- solvers
+    def _solve(self, fn, eta, nsites, solver, tol, nkv, nmx, bs, ncy, nmr, sap_prec, inner, check):
+        eta = eta.to(torch.complex128).contiguous()
+        nrhs = self._nrhs(eta, nsites)
+        psi = torch.empty_like(eta)
+        p = SolverParams(solver, nkv, nmx, tol, sap_params(bs, ncy, nmr, sap_prec), inner)
+        info = (SolveInfo * nrhs)()
+        st = fn(self._h, C.byref(p), _ptr(eta), _ptr(psi), nrhs, info)
+        infos = [i.as_dict() for i in info]
+        if check:
+            self._check(st, "solve")
+        return psi, infos, st
+
+    def solve_dhat(self, eta, solver=SOLVER_SAP_GCR, tol=1e-10, nkv=16, nmx=4096, bs=(4, 4, 4, 4), ncy=4, nmr=5,
+                   sap_prec=F64, inner=F64, check=True):
+        return self._solve(lib().lqcd_solve_dhat, eta, self.Vh, solver, tol, nkv, nmx, bs, ncy, nmr, sap_prec,
+                           inner, check)
+
+    def solve_D(self, eta, solver=SOLVER_SAP_GCR, tol=1e-10, nkv=16, nmx=4096, bs=(4, 4, 4, 4), ncy=4, nmr=5,
+                sap_prec=F64, inner=F64, check=True):
+        return self._solve(lib().lqcd_solve_D, eta, self.V, solver, tol, nkv, nmx, bs, ncy, nmr, sap_prec, inner,
+                           check)

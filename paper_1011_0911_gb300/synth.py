@@ -20,6 +20,7 @@ that c^4 = 0.55, the normalised average plaquette <U_P>/3 ~ 1.651/3 of Table 2.
 from __future__ import annotations
 
 import functools
+import os
 
 import numpy as np
 
@@ -102,21 +103,27 @@ def _hermitian_from_normals(h: np.ndarray) -> np.ndarray:
 
 
 def _expi(H: np.ndarray, eps: float) -> np.ndarray:
-    """exp(i eps H) for Hermitian H (N,3,3): scaling and squaring of a Taylor series."""
+    """exp(i eps H) for Hermitian traceless H (N,3,3): scaling and squaring of a
+    Taylor series, then the rows are re-orthonormalised and the third row set to
+    the conjugate cross product of the first two (exact SU(3) structure)."""
     X = 1j * eps * H
-    nrm = np.abs(X).sum(axis=2).max(axis=1).max() if X.shape[0] else 0.0
-    s = max(0, int(np.ceil(np.log2(max(nrm, 1e-300)))) + 2)
+    nrm = np.abs(X).sum(axis=2).max() if X.shape[0] else 0.0
+    s = max(0, int(np.ceil(np.log2(max(nrm, 1e-300) / 0.25))))
     X = X / (2.0**s)
     out = np.broadcast_to(np.eye(3, dtype=np.complex128), X.shape).copy()
     term = out.copy()
-    for k in range(1, 19):
+    for k in range(1, 13):
         term = term @ X / k
-        out = out + term
+        out += term
     for _ in range(s):
         out = out @ out
-    # remove the O(1e-16) drift from unitarity: one polar (Newton) step
-    out = 0.5 * (out + np.linalg.inv(out).conj().transpose(0, 2, 1))
-    return out
+    r0 = out[:, 0]
+    r0 = r0 / np.sqrt((np.abs(r0) ** 2).sum(axis=1))[:, None]
+    r1 = out[:, 1]
+    r1 = r1 - (r0.conj() * r1).sum(axis=1)[:, None] * r0
+    r1 = r1 / np.sqrt((np.abs(r1) ** 2).sum(axis=1))[:, None]
+    r2 = np.conj(np.cross(r0, r1))
+    return np.stack([r0, r1, r2], axis=1)
 
 
 @functools.lru_cache(maxsize=None)
@@ -140,12 +147,26 @@ def tuned_eps(target_plaquette: float = 0.55, nsample: int = 1 << 16) -> float:
     return 0.5 * (lo + hi)
 
 
-def su3_links(dims, seed: int, eps: float | None = None) -> np.ndarray:
-    """Gauge field U[site][mu][3][3] (complex128), site = x3 + L3*(x2 + L2*(x1 + L1*x0))."""
+def su3_links(dims, seed: int, eps: float | None = None, cache: bool = True) -> np.ndarray:
+    """Gauge field U[site][mu][3][3] (complex128), site = x3 + L3*(x2 + L2*(x1 + L1*x0)).
+
+    Deterministic in (dims, seed, eps); large fields are cached on disk under
+    $LQCD_SYNTH_CACHE (default /tmp/lqcd_synth_cache) to skip regeneration."""
     T, L1, L2, L3 = dims
     V = T * L1 * L2 * L3
     if eps is None:
         eps = tuned_eps()
+    path = None
+    if cache and V >= 1 << 16:
+        d = os.environ.get("LQCD_SYNTH_CACHE", "/tmp/lqcd_synth_cache")
+        path = os.path.join(d, f"links_{T}x{L1}x{L2}x{L3}_s{seed}_e{eps:.17g}.npy")
+        if os.path.exists(path):
+            try:
+                U = np.load(path)
+                if U.shape == (V, 4, 3, 3):
+                    return U
+            except (OSError, ValueError):
+                pass
     n = 4 * V
     out = np.empty((n, 3, 3), dtype=np.complex128)
     chunk = 1 << 18
@@ -154,7 +175,16 @@ def su3_links(dims, seed: int, eps: float | None = None) -> np.ndarray:
         # each link owns 8 normals: counters for link j start at 4*j (2 normals per counter)
         h = _gaussians_range(seed, STREAM_LINKS, 8 * s, 8 * e).reshape(e - s, 8)
         out[s:e] = _expi(_hermitian_from_normals(h), eps)
-    return out.reshape(V, 4, 3, 3)
+    U = out.reshape(V, 4, 3, 3)
+    if path is not None:
+        try:
+            os.makedirs(os.path.dirname(path), exist_ok=True)
+            tmp = path + f".{os.getpid()}.tmp.npy"
+            np.save(tmp, U)
+            os.replace(tmp, path)
+        except OSError:
+            pass
+    return U
 
 
 def _gaussians_range(seed: int, stream: int, start: int, stop: int) -> np.ndarray:
