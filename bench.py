@@ -143,7 +143,11 @@ def main():
     ap.add_argument("--nrhs", type=int, default=12)
     ap.add_argument("--prec", default="f32", choices=["f32", "f64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
+    ap.add_argument("--lattice", default="48x24x24x24", help="TxL1xL2xL3 (profiling runs use smaller ones)")
     args = ap.parse_args()
+    global DIMS
+    DIMS = tuple(int(v) for v in args.lattice.split("x"))
     if args.impl == "reference":
         return run_reference(args)
 
@@ -207,24 +211,27 @@ def main():
     achieved = bytes_app / (avg_launch_ms * 1e-3) / 1e9
 
     # ---- end-to-end through the public ABI, host buffers, copies inside the timed region
-    out_host = torch.empty_like(eta_host).pin_memory()
-    e2e_steps = max(3, min(args.steps // 10, 40))
-    for _ in range(2):
-        d = eta_host.to("cuda", non_blocking=True)
-        o = ctx.apply_Dhat(d, prec)
-        out_host.copy_(o, non_blocking=True)
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(e2e_steps):
-        d = eta_host.to("cuda", non_blocking=True)
-        o = ctx.apply_Dhat(d, prec)
-        out_host.copy_(o, non_blocking=True)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    e2e_ms = e0.elapsed_time(e1) / e2e_steps
-    e2e_val = flops_step * world / (e2e_ms * 1e-3) / 1e9
     nbytes = eta_host.numel() * eta_host.element_size()
+    e2e_ms, e2e_val = None, None
+    if not args.no_e2e:
+        out_host = torch.empty_like(eta_host).pin_memory()
+        e2e_steps = max(3, min(args.steps // 10, 40))
+        for _ in range(2):
+            d = eta_host.to("cuda", non_blocking=True)
+            o = ctx.apply_Dhat(d, prec)
+            out_host.copy_(o, non_blocking=True)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(e2e_steps):
+            d = eta_host.to("cuda", non_blocking=True)
+            o = ctx.apply_Dhat(d, prec)
+            out_host.copy_(o, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms = e0.elapsed_time(e1) / e2e_steps
+        e2e_val = round(flops_step * world / (e2e_ms * 1e-3) / 1e9, 2)
+        e2e_ms = round(e2e_ms, 4)
 
     if rank == 0:
         cb = None
@@ -235,12 +242,12 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 5),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": args.prec, "data": "synthetic",
-            "config": {"workload": WORKLOAD, "lattice": "48x24x24x24", "nrhs": nrhs, "precision": args.prec,
+            "config": {"workload": WORKLOAD, "lattice": args.lattice, "nrhs": nrhs, "precision": args.prec,
                        "links": "2-row SU(3)" if prec == lqcd.F32 else "full SU(3)",
                        "l2": "inputs larger than L2 (links+clover+12 fields = %.2f GB)" % (
                            (dhat_bytes_per_site(args.prec, nrhs) * Vh) / 1e9),
                        "parallelism": f"replicas x{world}"},
-            "e2e": {"value": round(e2e_val, 2), "unit": "GFLOP/s", "ms_per_step": round(e2e_ms, 4),
+            "e2e": {"value": e2e_val, "unit": "GFLOP/s", "ms_per_step": e2e_ms,
                     "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
                     "path": "lqcd_apply_Dhat (canonical fields) + pinned host copies"},
             "roofline": {"kernel": "Dhat = k_hop<DHAT1> + k_hop<DHAT2>", "bound": "hbm",

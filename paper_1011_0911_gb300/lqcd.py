@@ -121,7 +121,8 @@ def _ptr(t: torch.Tensor):
 
 
 def _dtype(prec):
-    return {F64: torch.complex128, F32: torch.complex64}[prec]
+    # F16S has no canonical form: such calls pass through and the library rejects them
+    return {F64: torch.complex128, F32: torch.complex64}.get(prec, torch.complex128)
 
 
 def sap_params(bs=(4, 4, 4, 4), ncy=4, nmr=5, prec=F64) -> SapParams:

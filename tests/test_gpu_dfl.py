@@ -1,0 +1,110 @@
+"""GPU deflation against the oracle: subspace build (inverse iteration with
+SAP + block Gram-Schmidt), Pi^dag, Pi, the little Dirac operator, the coarse
+solve and the deflated preconditioner; the deflated GCR solve judged by the
+FP64 true residual."""
+import numpy as np
+import pytest
+import torch
+
+from paper_1011_0911_gb300 import lqcd, synth
+from tests import util
+from tests.gpu_util import Pair, relerr, to_gpu
+
+pytestmark = pytest.mark.gpu
+
+NS = 4
+
+
+def _v0(P, Ns, seed=100):
+    return synth.gaussian_spinor(Ns * P.V, seed, synth.STREAM_SUBSPACE).reshape(Ns, P.V, 4, 3)
+
+
+@pytest.fixture(scope="module", params=[(8, 8, 8, 8), (12, 8, 4, 8)], ids=["8x8x8x8", "12x8x4x8"])
+def built(request):
+    """FP64 subspace on the GPU and in the oracle from the same start vectors.
+    12x8x4x8: 3 blocks in time (odd), 1 block along L2 (the block wraps)."""
+    P = Pair(request.param, kappa=0.1355)
+    v0 = _v0(P, NS)
+    P.ctx.dfl_build(to_gpu(v0), bs=(4, 4, 4, 4), ninv=2, ncy=2, nmr=4, prec=lqcd.F64, coarse_tol=1e-12)
+    assert P.o.dfl_build(v0, bs=(4, 4, 4, 4), ninv=2, ncy=2, nmr=4) == 0
+    return P
+
+
+def test_subspace_parity(built):
+    P = built
+    phi, A = P.ctx.dfl_export()
+    ref = P.o.dfl_subspace()
+    assert relerr(phi, ref) < 1e-11
+
+
+def test_little_operator_parity(built):
+    P = built
+    phi, A = P.ctx.dfl_export()
+    nblk, Ns = P.ctx.nblk, P.ctx.Ns
+    # dense from the block-row form: entry j of block b couples to the neighbour reached by j
+    Ad = np.zeros((nblk * Ns, nblk * Ns), dtype=np.complex128)
+    Ah = A.cpu().numpy()
+    nb = [L // 4 for L in P.dims]
+
+    def step(b, mu, d):
+        c = [0] * 4
+        u = b
+        for i in (3, 2, 1, 0):
+            c[i] = u % nb[i]
+            u //= nb[i]
+        c[mu] = (c[mu] + d) % nb[mu]
+        return c[3] + nb[3] * (c[2] + nb[2] * (c[1] + nb[1] * c[0]))
+
+    for b in range(nblk):
+        for j in range(9):
+            n = b if j == 0 else step(b, (j - 1) // 2, 1 if j % 2 == 1 else -1)
+            Ad[b * Ns:(b + 1) * Ns, n * Ns:(n + 1) * Ns] += Ah[b, j]
+    assert util.relerr(Ad, P.o.dfl_little()) < 1e-11
+
+
+def test_project_expand_apply_solve(built):
+    P = built
+    rho = synth.gaussian_spinor(P.V, 31)
+    c = P.ctx.dfl_project(to_gpu(rho))
+    assert relerr(c, P.o.dfl_project(rho)) < 1e-11
+    cc = synth.gaussian_spinor(P.ctx.nblk * P.ctx.Ns, 32).reshape(-1)[: P.ctx.nblk * P.ctx.Ns]
+    cc = np.ascontiguousarray(cc)
+    assert relerr(P.ctx.dfl_expand(to_gpu(cc)), P.o.dfl_expand(cc)) < 1e-11
+    assert relerr(P.ctx.dfl_little_apply(to_gpu(cc)), P.o.dfl_little_apply(cc)) < 1e-11
+    x, it = P.ctx.dfl_coarse_solve(to_gpu(cc))
+    xr = np.linalg.solve(P.o.dfl_little(), cc)
+    assert relerr(x, xr) < 1e-9
+
+
+def test_deflated_precond_parity(built):
+    P = built
+    rho = synth.gaussian_spinor(P.V, 33)
+    out = P.ctx.dfl_precond(to_gpu(rho), ncy=4, nmr=5, prec=lqcd.F64)
+    ref = P.o.dfl_precond(rho, ncy=4, nmr=5, ctol=1e-12)
+    assert relerr(out, ref) < 1e-8
+
+
+def test_deflated_gcr_solve_8x4():
+    """FP32 subspace (Ns = 8) and FP32 SAP, FP64 outer GCR: true residual 1e-10,
+    fewer GCR iterations than plain SAP-GCR (the shape of Table 1)."""
+    P = Pair((8, 8, 8, 8), kappa=0.1355)
+    v0 = _v0(P, 8, seed=200)
+    P.ctx.dfl_build(to_gpu(v0), bs=(4, 4, 4, 4), ninv=3, ncy=4, nmr=4, prec=lqcd.F32, coarse_tol=1e-8)
+    eta = synth.gaussian_spinor(P.Vh, 7)
+    psi, info, st = P.ctx.solve_dhat(to_gpu(eta), solver=lqcd.SOLVER_DFL_SAP_GCR, tol=1e-10, sap_prec=lqcd.F32,
+                                     inner=lqcd.F32)
+    assert st == 0
+    assert util.relerr(P.o.Dhat(psi.cpu().numpy()), eta) <= 1e-10
+    psi2, info2, st2 = P.ctx.solve_dhat(to_gpu(eta), solver=lqcd.SOLVER_SAP_GCR, tol=1e-10, sap_prec=lqcd.F32,
+                                        inner=lqcd.F32)
+    assert st2 == 0
+    assert info[0]["iters"] <= info2[0]["iters"]
+
+
+def test_dfl_requires_subspace_and_clover():
+    P = Pair((8, 8, 8, 8))
+    eta = synth.gaussian_spinor(P.Vh, 8)
+    psi, info, st = P.ctx.solve_dhat(to_gpu(eta), solver=lqcd.SOLVER_DFL_SAP_GCR, check=False)
+    assert st == 9
+    with pytest.raises(lqcd.LqcdError):
+        P.ctx.dfl_build(to_gpu(_v0(P, 2)), bs=(3, 4, 4, 4))
