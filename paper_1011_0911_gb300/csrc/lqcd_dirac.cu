@@ -15,6 +15,7 @@
 // half is -+ e_mu^dag h.  Each hop therefore multiplies only two colour
 // vectors by the link (spin projection), 1320 flops per output site.
 #include "lqcd_internal.cuh"
+#include "lqcd_tune.h"
 
 namespace {
 
@@ -306,8 +307,30 @@ struct HopArgs {
 //   MODE_DHAT2: out = A in_same + 1/2 S        (A_ee psi_e - H_eo chi_o)
 //   MODE_D    : out = A in_same - 1/2 S        (D psi on one parity)
 // with S = sum of the 8 projected hops of in_other.
-template <class R, class SP, class LK, class CL, int MODE>
-__global__ void __launch_bounds__(256) k_hop(HopArgs<SP, LK, CL> a)
+// occupancy variants: (max threads per CTA, min CTAs per SM)
+template <int VAR>
+struct Var;
+template <>
+struct Var<0> {
+    static constexpr int T = 384, B = 1;
+};
+template <>
+struct Var<1> {
+    static constexpr int T = 384, B = 2;
+};
+template <>
+struct Var<2> {
+    static constexpr int T = 256, B = 3;
+};
+template <>
+struct Var<3> {
+    static constexpr int T = 256, B = 4;
+};
+constexpr int NVAR = 4;
+inline int var_max_threads(int v) { return v < 2 ? 384 : 256; }
+
+template <class R, class SP, class LK, class CL, int MODE, int VAR>
+__global__ void __launch_bounds__(Var<VAR>::T, Var<VAR>::B) k_hop(HopArgs<SP, LK, CL> a)
 {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     const int k = blockIdx.y * blockDim.y + threadIdx.y;
@@ -317,42 +340,75 @@ __global__ void __launch_bounds__(256) k_hop(HopArgs<SP, LK, CL> a)
     rank_coords(a.g, a.p_out, r, x);
     const SP *in = a.in_other + k * a.in_rs;
     Spinor<R> acc;
-#pragma unroll
-    for (int s = 0; s < 4; s++)
-#pragma unroll
-        for (int c = 0; c < 3; c++) acc.s[s][c] = mk(R(0), R(0));
-    hop_dir<R, SP, LK, 0>(a.g, a.p_out, r, x, in, Vh, a.U, acc);
-    hop_dir<R, SP, LK, 1>(a.g, a.p_out, r, x, in, Vh, a.U, acc);
-    hop_dir<R, SP, LK, 2>(a.g, a.p_out, r, x, in, Vh, a.U, acc);
-    hop_dir<R, SP, LK, 3>(a.g, a.p_out, r, x, in, Vh, a.U, acc);
-    Spinor<R> res;
     if (MODE == MODE_HOP || MODE == MODE_DHAT1) {
 #pragma unroll
         for (int s = 0; s < 4; s++)
 #pragma unroll
-            for (int c = 0; c < 3; c++) acc.s[s][c] = R(-0.5) * acc.s[s][c];
-        if (MODE == MODE_HOP)
-            res = acc;
-        else
-            clover_apply<R, CL>(a.clov, Vh, r, acc, res);
+            for (int c = 0; c < 3; c++) acc.s[s][c] = mk(R(0), R(0));
     } else {
+        // start from (1/f) A in_same, f = +-1/2 (exact power-of-two scaling), so the
+        // hops accumulate into the same registers: out = f (A in / f + S)
         Spinor<R> self;
         load_spinor(a.in_same + k * a.same_rs, Vh, r, self);
-        clover_apply<R, CL>(a.clov, Vh, r, self, res);
-        const R f = MODE == MODE_DHAT2 ? R(0.5) : R(-0.5);
+        clover_apply<R, CL>(a.clov, Vh, r, self, acc);
+        const R inv_f = MODE == MODE_DHAT2 ? R(2) : R(-2);
 #pragma unroll
         for (int s = 0; s < 4; s++)
 #pragma unroll
-            for (int c = 0; c < 3; c++) res.s[s][c] = res.s[s][c] + f * acc.s[s][c];
+            for (int c = 0; c < 3; c++) acc.s[s][c] = inv_f * acc.s[s][c];
     }
-    store_spinor(a.out + k * a.out_rs, Vh, r, res);
+    hop_dir<R, SP, LK, 0>(a.g, a.p_out, r, x, in, Vh, a.U, acc);
+    hop_dir<R, SP, LK, 1>(a.g, a.p_out, r, x, in, Vh, a.U, acc);
+    hop_dir<R, SP, LK, 2>(a.g, a.p_out, r, x, in, Vh, a.U, acc);
+    hop_dir<R, SP, LK, 3>(a.g, a.p_out, r, x, in, Vh, a.U, acc);
+    const R f = MODE == MODE_DHAT2 ? R(0.5) : R(-0.5);
+#pragma unroll
+    for (int s = 0; s < 4; s++)
+#pragma unroll
+        for (int c = 0; c < 3; c++) acc.s[s][c] = f * acc.s[s][c];
+    if (MODE == MODE_DHAT1) {
+        Spinor<R> res;
+        clover_apply<R, CL>(a.clov, Vh, r, acc, res);
+        store_spinor(a.out + k * a.out_rs, Vh, r, res);
+    } else {
+        store_spinor(a.out + k * a.out_rs, Vh, r, acc);
+    }
 }
 
-inline dim3 hop_block(int nrhs)
+template <class R, class SP, class LK, class CL, int MODE>
+lqcd_status launch_var(lqcd_ctx *c, int var, dim3 b, const HopArgs<SP, LK, CL> &a)
 {
-    if (nrhs <= 1) return dim3(128, 1);
-    int ty = nrhs < 8 ? nrhs : 8;
-    return dim3(32, ty);
+    dim3 grid(div_up(c->g.Vh, b.x), div_up(a.nrhs, b.y));
+    switch (var) {
+        case 0: k_hop<R, SP, LK, CL, MODE, 0><<<grid, b, 0, c->stream>>>(a); break;
+        case 1: k_hop<R, SP, LK, CL, MODE, 1><<<grid, b, 0, c->stream>>>(a); break;
+        case 2: k_hop<R, SP, LK, CL, MODE, 2><<<grid, b, 0, c->stream>>>(a); break;
+        default: k_hop<R, SP, LK, CL, MODE, 3><<<grid, b, 0, c->stream>>>(a); break;
+    }
+    c->n_kernel_launches++;
+    LQCD_LAUNCH_CHECK(c);
+    return LQCD_OK;
+}
+
+// candidate launch shapes: tx sites x ty fields per CTA
+std::vector<TuneChoice> hop_candidates(int nrhs)
+{
+    std::vector<TuneChoice> v;
+    std::vector<int> tys;
+    for (int t : {nrhs, (nrhs + 1) / 2, (nrhs + 2) / 3, 4, 2, 1})
+        if (t >= 1 && t <= nrhs && std::find(tys.begin(), tys.end(), t) == tys.end()) tys.push_back(t);
+    for (int var = 0; var < NVAR; var++)
+        for (int ty : tys)
+            for (int tx : {16, 32, 64, 128, 256}) {
+                int n = tx * ty;
+                if (n > var_max_threads(var) || n < 64) continue;
+                TuneChoice t;
+                t.variant = var;
+                t.tx = tx;
+                t.ty = ty;
+                v.push_back(t);
+            }
+    return v;
 }
 
 template <class R, class SP, class LK, class CL, int MODE>
@@ -371,12 +427,31 @@ lqcd_status launch_hop(lqcd_ctx *c, int p_out, const SP *in_other, long in_rs, c
     a.out_rs = out_rs;
     a.U = U;
     a.clov = clov;
-    dim3 b = hop_block(nrhs);
-    dim3 grid(div_up(c->g.Vh, b.x), div_up(nrhs, b.y));
-    k_hop<R, SP, LK, CL, MODE><<<grid, b, 0, c->stream>>>(a);
-    c->n_kernel_launches++;
-    LQCD_LAUNCH_CHECK(c);
-    return LQCD_OK;
+    const int prec = sizeof(R) == 8 ? 0 : 1;
+    std::string key = tune_key(c, "k_hop", MODE, prec, nrhs);
+    TuneChoice tc;
+    if (!tune_lookup(key, &tc)) {
+        tc = TuneChoice();
+        tc.tx = nrhs == 1 ? 128 : 32;
+        tc.ty = nrhs == 1 ? 1 : std::min(nrhs, 8);
+        if (tune_enabled()) {
+            float best = 1e30f;
+            for (const TuneChoice &cand : hop_candidates(nrhs)) {
+                float us;
+                lqcd_status s = tune_time(
+                    c, [&]() { return launch_var<R, SP, LK, CL, MODE>(c, cand.variant, dim3(cand.tx, cand.ty), a); },
+                    3, &us);
+                if (s != LQCD_OK) return s;
+                if (us < best) {
+                    best = us;
+                    tc = cand;
+                    tc.us = us;
+                }
+            }
+            tune_store(key, tc);
+        }
+    }
+    return launch_var<R, SP, LK, CL, MODE>(c, tc.variant, dim3(tc.tx, tc.ty), a);
 }
 
 }  // namespace
