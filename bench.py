@@ -120,6 +120,103 @@ def cpu_baseline(steps: int = 2):
             "seconds_per_application": round(dt, 4)}
 
 
+KAPPA_OF = {(8, 8, 8, 8): 0.1355, (32, 16, 16, 16): 0.1357, (48, 24, 24, 24): 0.13625, (64, 32, 32, 32): 0.1363}
+
+
+def solve_once(ctx, lqcd, eta, solver, inner, Ns=20, ninv=8, ctol=1e-2, seed=100, cnmx=4096, cnkv=16, cprec=None):
+    """Time-to-solution of Dhat psi = eta (all fields of eta) to 1e-10 with the
+    given solver; the subspace build is timed separately and included in total."""
+    import torch
+    from paper_1011_0911_gb300 import synth
+    prec = lqcd.F32 if inner == "f32" else lqcd.F64
+    res = {"solver": solver, "inner": inner, "nrhs": int(eta.shape[0])}
+    torch.cuda.synchronize()
+    build_s = 0.0
+    if solver == "dfl":
+        v0 = torch.from_numpy(synth.gaussian_spinor(Ns * ctx.V, seed, synth.STREAM_SUBSPACE)
+                              .reshape(Ns, ctx.V, 4, 3)).cuda()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        cp = prec if cprec is None else (lqcd.F32 if cprec == "f32" else lqcd.F64)
+        ctx.dfl_build(v0, bs=(4, 4, 4, 4), ninv=ninv, ncy=4, nmr=4, prec=prec, coarse_tol=ctol, coarse_nkv=cnkv,
+                      coarse_nmx=cnmx, coarse_prec=cp)
+        torch.cuda.synchronize()
+        build_s = time.perf_counter() - t0
+        res.update({"Ns": Ns, "ninv": ninv, "coarse_tol": ctol, "coarse_nmx": cnmx,
+                    "coarse_prec": "f32" if cp == lqcd.F32 else "f64", "build_s": round(build_s, 4)})
+    sid = {"cgnr": lqcd.SOLVER_CGNR, "sap": lqcd.SOLVER_SAP_GCR, "dfl": lqcd.SOLVER_DFL_SAP_GCR}[solver]
+    t0 = time.perf_counter()
+    psi, info, st = ctx.solve_dhat(eta, solver=sid, tol=1e-10, nmx=20000 if solver == "cgnr" else 4096,
+                                   sap_prec=prec, inner=prec, check=False)
+    torch.cuda.synchronize()
+    solve_s = time.perf_counter() - t0
+    res.update({"status": st, "solve_s": round(solve_s, 4), "total_s": round(solve_s + build_s, 4),
+                "iters": [i["iters"] for i in info],
+                "max_relres_dhat": max(i["relres_dhat"] for i in info)})
+    if solver == "dfl":
+        res["coarse_solves"], res["coarse_iters"] = ctx.dfl_stats()
+    return res, psi
+
+
+def time_to_solve(ctx, lqcd, eta):
+    """Time-to-solution of Dhat psi = eta for the 12 sources to a true relative
+    residual <= 1e-10 (checked in FP64), subspace build included:
+      plain_f64 : deflated SAP-GCR, FP64 everywhere, one source at a time
+      dfl_mixed : deflated SAP-GCR, FP32 SAP / subspace / little operator,
+                  FP64 outer GCR, the 12 sources in one batched solve
+      chosen    : SAP-GCR, FP32 SAP and stencil, FP64 outer GCR, the 12
+                  sources in one batched solve (fastest measured form)"""
+    import torch
+    out = {}
+    r, _ = solve_once(ctx, lqcd, eta, "sap", "f32")
+    out["chosen"] = {"form": "SAP-GCR, FP32 SAP/stencil, FP64 GCR, 12 RHS batched", "seconds": r["total_s"],
+                     "iters": max(r["iters"]), "max_relres_dhat": r["max_relres_dhat"], "status": r["status"]}
+    r, _ = solve_once(ctx, lqcd, eta, "dfl", "f32", Ns=20, ninv=8, ctol=1e-2, cnmx=64, cprec="f32")
+    out["dfl_mixed"] = {"form": "deflated SAP-GCR (Ns=20, 4^4 blocks), FP32 SAP/subspace/little operator, FP64 GCR, "
+                                "12 RHS batched", "seconds": r["total_s"], "build_s": r["build_s"],
+                        "iters": max(r["iters"]), "max_relres_dhat": r["max_relres_dhat"], "status": r["status"]}
+    total, build, iters, worst, st = 0.0, 0.0, 0, 0.0, 0
+    for k in range(eta.shape[0]):
+        if k == 0:
+            r, _ = solve_once(ctx, lqcd, eta[k:k + 1].contiguous(), "dfl", "f64", Ns=20, ninv=8, ctol=1e-2,
+                              cnmx=64, cprec="f64")
+            build = r["build_s"]
+            total += r["total_s"]
+        else:   # the subspace is reused for the other sources
+            sid = lqcd.SOLVER_DFL_SAP_GCR
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            psi, info, s = ctx.solve_dhat(eta[k:k + 1].contiguous(), solver=sid, tol=1e-10, sap_prec=lqcd.F64,
+                                          inner=lqcd.F64, check=False)
+            torch.cuda.synchronize()
+            total += time.perf_counter() - t0
+            r = {"iters": [info[0]["iters"]], "max_relres_dhat": info[0]["relres_dhat"], "status": s}
+        iters = max(iters, max(r["iters"]))
+        worst = max(worst, r["max_relres_dhat"])
+        st = st or r["status"]
+    out["plain_f64"] = {"form": "deflated SAP-GCR (Ns=20, 4^4 blocks), FP64 throughout, one source at a time",
+                        "seconds": round(total, 4), "build_s": build, "iters": iters, "max_relres_dhat": worst,
+                        "status": st}
+    out["speedup_chosen_vs_plain_f64"] = round(out["plain_f64"]["seconds"] / out["chosen"]["seconds"], 2)
+    out["speedup_dfl_mixed_vs_plain_f64"] = round(out["plain_f64"]["seconds"] / out["dfl_mixed"]["seconds"], 2)
+    out["tolerance"] = 1e-10
+    return out
+
+
+def run_solve(args):
+    import torch
+    from paper_1011_0911_gb300 import lqcd, synth
+    kappa = args.kappa or KAPPA_OF.get(DIMS, 0.1355)
+    ctx = lqcd.Context(DIMS)
+    ctx.set_gauge(torch.from_numpy(synth.su3_links(DIMS, 0)).cuda())
+    ctx.clover_invert(kappa, CSW)
+    eta = torch.from_numpy(synth.gaussian_spinor(args.nrhs * ctx.Vh, 1).reshape(args.nrhs, ctx.Vh, 4, 3)).cuda()
+    res, _ = solve_once(ctx, lqcd, eta, args.solver, args.prec, Ns=args.Ns, ninv=args.ninv, ctol=args.ctol,
+                        cnmx=args.cnmx, cprec=args.cprec)
+    res.update({"mode": "solve", "lattice": args.lattice, "kappa": kappa})
+    print(json.dumps(res))
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -144,12 +241,24 @@ def main():
     ap.add_argument("--prec", default="f32", choices=["f32", "f64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
+    ap.add_argument("--no-solve", action="store_true", help="skip the time-to-solution comparison")
     ap.add_argument("--lattice", default="48x24x24x24", help="TxL1xL2xL3 (profiling runs use smaller ones)")
+    ap.add_argument("--mode", default="dhat", choices=["dhat", "solve"],
+                    help="solve: one time-to-solution run (profiling / studies)")
+    ap.add_argument("--solver", default="dfl", choices=["cgnr", "sap", "dfl"])
+    ap.add_argument("--kappa", type=float, default=None)
+    ap.add_argument("--Ns", type=int, default=20)
+    ap.add_argument("--ninv", type=int, default=8)
+    ap.add_argument("--ctol", type=float, default=1e-2)
+    ap.add_argument("--cnmx", type=int, default=4096, help="iteration budget of each little-Dirac solve")
+    ap.add_argument("--cprec", default=None, choices=["f32", "f64"], help="little-Dirac operator precision")
     args = ap.parse_args()
     global DIMS
     DIMS = tuple(int(v) for v in args.lattice.split("x"))
     if args.impl == "reference":
         return run_reference(args)
+    if args.mode == "solve":
+        return run_solve(args)
 
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -233,6 +342,10 @@ def main():
         e2e_val = round(flops_step * world / (e2e_ms * 1e-3) / 1e9, 2)
         e2e_ms = round(e2e_ms, 4)
 
+    tts = None
+    if not args.no_solve and rank == 0 and DIMS == (48, 24, 24, 24):
+        tts = time_to_solve(ctx, lqcd, eta_dev.to(torch.complex128))
+
     if rank == 0:
         cb = None
         if not args.no_cpu_baseline:
@@ -257,6 +370,7 @@ def main():
             "gpu_launches": launches,
             "clocks": clk,
             "cpu_baseline": cb,
+            "time_to_solve": tts,
         }
         print(json.dumps(line))
     if dist:

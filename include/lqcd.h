@@ -170,6 +170,9 @@ typedef struct {
     double coarse_tol;/* relative residual of the little-Dirac solve */
     int coarse_nkv;   /* GCR Krylov length of the little-Dirac solve */
     int coarse_nmx;   /* iteration limit of the little-Dirac solve */
+    lqcd_prec coarse_prec; /* arithmetic of the little-Dirac operator: LQCD_F64, or LQCD_F32
+                              (operator stored and applied in float; the GCR around it,
+                              its vectors and inner products stay FP64) */
 } lqcd_dfl_params;
 
 /* Build the deflation subspace ("locally deflated" solver, Sec. 3-4,
@@ -189,6 +192,9 @@ LQCD_API lqcd_status lqcd_dfl_project(lqcd_ctx *ctx, const double *in_dev, doubl
 LQCD_API lqcd_status lqcd_dfl_expand(lqcd_ctx *ctx, const double *c_dev, double *out_dev);
 LQCD_API lqcd_status lqcd_dfl_little_apply(lqcd_ctx *ctx, const double *c_dev, double *out_dev);
 LQCD_API lqcd_status lqcd_dfl_coarse_solve(lqcd_ctx *ctx, const double *b_dev, double *c_dev, int *iters);
+/* Counters of the little-Dirac solves since the subspace was built (host
+ * pointers; instrumentation).  Errors: LQCD_ERR_STATE without a subspace. */
+LQCD_API lqcd_status lqcd_dfl_stats(const lqcd_ctx *ctx, long *coarse_solves, long *coarse_iters);
 /* phi = M_dfl rho = M_sap(rho - D Pi A^-1 Pi^dag rho) + Pi A^-1 Pi^dag rho. */
 LQCD_API lqcd_status lqcd_dfl_precond(lqcd_ctx *ctx, const lqcd_sap_params *sap, const double *rho_dev,
                              double *phi_dev);

@@ -7,65 +7,8 @@
 
 namespace {
 
-constexpr int RED_BLOCKS = 304;   // 2 x 152 SMs
 constexpr int RED_THREADS = 256;
 constexpr int DOT_CHUNK = 8;
-
-// partial[b][i] (complex) = sum over this block's slice of conj(a_i) b
-__global__ void __launch_bounds__(RED_THREADS) k_dot_partial(long n, const double2 *__restrict__ A, long sa,
-                                                             const double2 *__restrict__ B, int k0, int kn,
-                                                             double2 *partial)
-{
-    double re[DOT_CHUNK], im[DOT_CHUNK];
-#pragma unroll
-    for (int i = 0; i < DOT_CHUNK; i++) re[i] = im[i] = 0;
-    for (long j = blockIdx.x * (long)blockDim.x + threadIdx.x; j < n; j += (long)gridDim.x * blockDim.x) {
-        double2 b = B[j];
-#pragma unroll
-        for (int i = 0; i < DOT_CHUNK; i++)
-            if (i < kn) {
-                double2 a = A[(k0 + i) * sa + j];
-                re[i] += a.x * b.x + a.y * b.y;
-                im[i] += a.x * b.y - a.y * b.x;
-            }
-    }
-    __shared__ double sh[RED_THREADS / 32][DOT_CHUNK][2];
-    int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-    for (int i = 0; i < DOT_CHUNK; i++) {
-        double r = re[i], m = im[i];
-        for (int o = 16; o > 0; o >>= 1) {
-            r += __shfl_down_sync(0xffffffffu, r, o);
-            m += __shfl_down_sync(0xffffffffu, m, o);
-        }
-        if (lane == 0) {
-            sh[warp][i][0] = r;
-            sh[warp][i][1] = m;
-        }
-    }
-    __syncthreads();
-    if (threadIdx.x < kn) {
-        double r = 0, m = 0;
-        for (int w = 0; w < RED_THREADS / 32; w++) {
-            r += sh[w][threadIdx.x][0];
-            m += sh[w][threadIdx.x][1];
-        }
-        partial[(long)blockIdx.x * 64 + k0 + threadIdx.x] = make_double2(r, m);
-    }
-}
-
-__global__ void k_dot_final(int nblk, int k, const double2 *partial, double2 *out)
-{
-    int i = threadIdx.x;
-    if (i >= k) return;
-    double r = 0, m = 0;
-    for (int b = 0; b < nblk; b++) {
-        double2 v = partial[(long)b * 64 + i];
-        r += v.x;
-        m += v.y;
-    }
-    out[i] = make_double2(r, m);
-}
 
 __global__ void k_axpy(long n, double ar, double ai, const double2 *__restrict__ x, double2 *y)
 {
@@ -131,28 +74,208 @@ __global__ void k_gamma5_64(long Vh, long nhalf, const double2 *__restrict__ in,
 
 inline int grid_for(long n) { return (int)std::min<long>(4 * 152, (n + 255) / 256); }
 
+// ---------------------------------------------------------------- batched
+// partial[(r*nb + b)*64 + i] = block b's share of <A_{i,r}, B_r>
+__global__ void __launch_bounds__(RED_THREADS) k_bdot_partial(long n, const double2 *__restrict__ A, long sa,
+                                                              long fa, const double2 *__restrict__ B, long fb,
+                                                              int k0, int kn, double2 *partial)
+{
+    const int r = blockIdx.y;
+    const double2 *Br = B + r * fb;
+    const double2 *Ar = A + r * fa;
+    double re[DOT_CHUNK], im[DOT_CHUNK];
+#pragma unroll
+    for (int i = 0; i < DOT_CHUNK; i++) re[i] = im[i] = 0;
+    for (long j = blockIdx.x * (long)blockDim.x + threadIdx.x; j < n; j += (long)gridDim.x * blockDim.x) {
+        double2 b = Br[j];
+#pragma unroll
+        for (int i = 0; i < DOT_CHUNK; i++)
+            if (i < kn) {
+                double2 a = Ar[(k0 + i) * sa + j];
+                re[i] += a.x * b.x + a.y * b.y;
+                im[i] += a.x * b.y - a.y * b.x;
+            }
+    }
+    __shared__ double sh[RED_THREADS / 32][DOT_CHUNK][2];
+    int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int i = 0; i < DOT_CHUNK; i++) {
+        double x = re[i], m = im[i];
+        for (int o = 16; o > 0; o >>= 1) {
+            x += __shfl_down_sync(0xffffffffu, x, o);
+            m += __shfl_down_sync(0xffffffffu, m, o);
+        }
+        if (lane == 0) {
+            sh[warp][i][0] = x;
+            sh[warp][i][1] = m;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < kn) {
+        double x = 0, m = 0;
+        for (int w = 0; w < RED_THREADS / 32; w++) {
+            x += sh[w][threadIdx.x][0];
+            m += sh[w][threadIdx.x][1];
+        }
+        partial[((long)r * gridDim.x + blockIdx.x) * 64 + k0 + threadIdx.x] = make_double2(x, m);
+    }
+}
+// one CTA per (vector i, rhs r): fixed-order tree over the nb partial sums
+__global__ void k_bdot_final(int nb, int k, const double2 *partial, double2 *out)
+{
+    const int i = blockIdx.x, r = blockIdx.y;
+    __shared__ double sx[256], sm[256];
+    double x = 0, m = 0;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+        double2 v = partial[((long)r * nb + b) * 64 + i];
+        x += v.x;
+        m += v.y;
+    }
+    sx[threadIdx.x] = x;
+    sm[threadIdx.x] = m;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) {
+            sx[threadIdx.x] += sx[threadIdx.x + s];
+            sm[threadIdx.x] += sm[threadIdx.x + s];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[r * k + i] = make_double2(sx[0], sm[0]);
+}
+// coefficients passed by value (16 KB of launch parameters)
+struct CoefParam {
+    static constexpr int N = 1024;
+    double2 c[N];
+};
+
+// y_r += sign * sum_i c[r*k + i] X_{i,r}
+__global__ void k_bmulti_axpy(long n, int k, const __grid_constant__ CoefParam cf, const double2 *__restrict__ X,
+                              long sa, long fa, double2 *y, long fy, double sign)
+{
+    const int r = blockIdx.y;
+    const double2 *c = cf.c + r * k;
+    const double2 *Xr = X + r * fa;
+    double2 *yr = y + r * fy;
+    for (long j = blockIdx.x * (long)blockDim.x + threadIdx.x; j < n; j += (long)gridDim.x * blockDim.x) {
+        double2 b = yr[j];
+        double sr = 0, si = 0;
+        for (int i = 0; i < k; i++) {
+            double2 a = Xr[i * sa + j], ci = c[i];
+            sr += ci.x * a.x - ci.y * a.y;
+            si += ci.x * a.y + ci.y * a.x;
+        }
+        yr[j] = make_double2(b.x + sign * sr, b.y + sign * si);
+    }
+}
+
+// y_r += sign * sum_i cf[r*k + i] X_{i,r} with the coefficients in device memory
+__global__ void k_bmulti_axpy_dev(long n, int k, const double2 *__restrict__ cf, const double2 *__restrict__ X,
+                                  long sa, long fa, double2 *y, long fy, double sign)
+{
+    const int r = blockIdx.y;
+    const double2 *c = cf + r * k;
+    const double2 *Xr = X + r * fa;
+    double2 *yr = y + r * fy;
+    for (long j = blockIdx.x * (long)blockDim.x + threadIdx.x; j < n; j += (long)gridDim.x * blockDim.x) {
+        double2 b = yr[j];
+        double sr = 0, si = 0;
+        for (int i = 0; i < k; i++) {
+            double2 a = Xr[i * sa + j], ci = c[i];
+            sr += ci.x * a.x - ci.y * a.y;
+            si += ci.x * a.y + ci.y * a.x;
+        }
+        yr[j] = make_double2(b.x + sign * sr, b.y + sign * si);
+    }
+}
+
 }  // namespace
+
+// as bblas_dot, results left in device memory: out_dev[r*k + i] (complex)
+lqcd_status bblas_dot_dev(lqcd_ctx *c, long n2, int nrhs, const double *A, long sa, long fa, const double *B, long fb,
+                          int k, double2 *out_dev)
+{
+    if (k < 1 || k > 64 || nrhs < 1 || nrhs * k > 2048) return set_err(c, LQCD_ERR_ARG, "bblas_dot_dev k=%d", k);
+    long n = n2 / 2;
+    // about 4 CTAs per SM over the batch, but no more than one CTA per 256 elements
+    int nb = std::max(1, (int)std::min<long>(std::max(8, 4 * 152 / nrhs), (n + 255) / 256));
+    nb = std::min(nb, 4096 / nrhs);
+    double2 *partial = (double2 *)c->red;
+    for (int k0 = 0; k0 < k; k0 += DOT_CHUNK) {
+        int kn = std::min(DOT_CHUNK, k - k0);
+        k_bdot_partial<<<dim3(nb, nrhs), RED_THREADS, 0, c->stream>>>(n, (const double2 *)A, sa / 2, fa / 2,
+                                                                      (const double2 *)B, fb / 2, k0, kn, partial);
+        c->n_kernel_launches++;
+    }
+    k_bdot_final<<<dim3(k, nrhs), 256, 0, c->stream>>>(nb, k, partial, out_dev);
+    c->n_kernel_launches++;
+    LQCD_LAUNCH_CHECK(c);
+    return LQCD_OK;
+}
+
+lqcd_status bblas_multi_axpy_dev(lqcd_ctx *c, long n2, int nrhs, int k, const double2 *coef_dev, const double *X,
+                                 long sa, long fa, double *y, long fy, double sign)
+{
+    if (k < 1) return LQCD_OK;
+    long n = n2 / 2;
+    dim3 grid(std::max(1, grid_for(n) / std::max(1, nrhs / 2)), nrhs);
+    k_bmulti_axpy_dev<<<grid, 256, 0, c->stream>>>(n, k, coef_dev, (const double2 *)X, sa / 2, fa / 2, (double2 *)y,
+                                                   fy / 2, sign);
+    c->n_kernel_launches++;
+    LQCD_LAUNCH_CHECK(c);
+    return LQCD_OK;
+}
+
+// dots[r][i] = <A + i*sa + r*fa, B + r*fb> for i < k, r < nrhs (lengths and strides in doubles)
+lqcd_status bblas_dot(lqcd_ctx *c, long n2, int nrhs, const double *A, long sa, long fa, const double *B, long fb,
+                      int k, double *host_out)
+{
+    if (k < 1 || k > 64 || nrhs < 1 || nrhs * k > 2048) return set_err(c, LQCD_ERR_ARG, "bblas_dot k=%d", k);
+    long n = n2 / 2;
+    // about 4 CTAs per SM over the batch, but no more than one CTA per 256 elements
+    int nb = std::max(1, (int)std::min<long>(std::max(8, 4 * 152 / nrhs), (n + 255) / 256));
+    nb = std::min(nb, 4096 / nrhs);
+    double2 *partial = (double2 *)c->red;   // nrhs * nb * 64 double2 <= 4096 * 64 (sized at create)
+    for (int k0 = 0; k0 < k; k0 += DOT_CHUNK) {
+        int kn = std::min(DOT_CHUNK, k - k0);
+        k_bdot_partial<<<dim3(nb, nrhs), RED_THREADS, 0, c->stream>>>(n, (const double2 *)A, sa / 2, fa / 2,
+                                                                      (const double2 *)B, fb / 2, k0, kn, partial);
+        c->n_kernel_launches++;
+    }
+    k_bdot_final<<<dim3(k, nrhs), 256, 0, c->stream>>>(nb, k, partial, (double2 *)c->red_out);
+    c->n_kernel_launches++;
+    LQCD_LAUNCH_CHECK(c);
+    LQCD_CUDA_CHECK(c, cudaMemcpyAsync(c->red_host, c->red_out, 2 * (size_t)k * nrhs * sizeof(double),
+                                       cudaMemcpyDeviceToHost, c->stream));
+    LQCD_CUDA_CHECK(c, cudaStreamSynchronize(c->stream));
+    for (int i = 0; i < 2 * k * nrhs; i++) host_out[i] = c->red_host[i];
+    return LQCD_OK;
+}
+
+// y_r += sign * sum_i coef[r][i] X_{i,r}; coef: host, nrhs*k complex
+lqcd_status bblas_multi_axpy(lqcd_ctx *c, long n2, int nrhs, int k, const double *coef_host, const double *X,
+                             long sa, long fa, double *y, long fy, double sign)
+{
+    if (k < 1) return LQCD_OK;
+    if (k > 64 || nrhs * k > CoefParam::N) return set_err(c, LQCD_ERR_ARG, "bblas_multi_axpy k=%d", k);
+    // the coefficients travel by value in the launch parameters: no staging
+    // buffer, no host synchronisation
+    CoefParam cp;
+    for (int i = 0; i < k * nrhs; i++) cp.c[i] = make_double2(coef_host[2 * i], coef_host[2 * i + 1]);
+    long n = n2 / 2;
+    dim3 grid(std::max(1, grid_for(n) / std::max(1, nrhs / 2)), nrhs);
+    k_bmulti_axpy<<<grid, 256, 0, c->stream>>>(n, k, cp, (const double2 *)X, sa / 2, fa / 2, (double2 *)y, fy / 2,
+                                               sign);
+    c->n_kernel_launches++;
+    LQCD_LAUNCH_CHECK(c);
+    return LQCD_OK;
+}
 
 lqcd_status blas_dot(lqcd_ctx *c, long n2, const double *A, const double *B, int k, long stride_a,
                      double *host_out)
 {
     if (k < 1 || k > 64) return set_err(c, LQCD_ERR_ARG, "blas_dot: k=%d", k);
-    long n = n2 / 2;
-    double2 *partial = (double2 *)c->red;
-    for (int k0 = 0; k0 < k; k0 += DOT_CHUNK) {
-        int kn = std::min(DOT_CHUNK, k - k0);
-        k_dot_partial<<<RED_BLOCKS, RED_THREADS, 0, c->stream>>>(n, (const double2 *)A, stride_a / 2,
-                                                                 (const double2 *)B, k0, kn, partial);
-        c->n_kernel_launches++;
-    }
-    k_dot_final<<<1, 64, 0, c->stream>>>(RED_BLOCKS, k, partial, (double2 *)c->red_out);
-    c->n_kernel_launches++;
-    LQCD_LAUNCH_CHECK(c);
-    LQCD_CUDA_CHECK(c, cudaMemcpyAsync(c->red_host, c->red_out, 2 * k * sizeof(double), cudaMemcpyDeviceToHost,
-                                       c->stream));
-    LQCD_CUDA_CHECK(c, cudaStreamSynchronize(c->stream));
-    for (int i = 0; i < 2 * k; i++) host_out[i] = c->red_host[i];
-    return LQCD_OK;
+    return bblas_dot(c, n2, 1, A, stride_a, 0, B, 0, k, host_out);
 }
 
 lqcd_status blas_norm2(lqcd_ctx *c, long n2, const double *a, double *host_out)

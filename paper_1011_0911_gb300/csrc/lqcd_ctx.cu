@@ -226,8 +226,8 @@ lqcd_status lqcd_create(const lqcd_geom *geom, void *stream, lqcd_ctx **out)
     c->g.bc_t = geom->antiperiodic_t ? -1 : 1;
     c->stream = (cudaStream_t)stream;
     if (cudaMalloc(&c->red, 4096 * 2 * 64 * sizeof(double)) != cudaSuccess ||
-        cudaMalloc(&c->red_out, 2 * 256 * sizeof(double)) != cudaSuccess ||
-        cudaMallocHost(&c->red_host, 2 * 256 * sizeof(double)) != cudaSuccess) {
+        cudaMalloc(&c->red_out, 4 * 2048 * sizeof(double)) != cudaSuccess ||
+        cudaMallocHost(&c->red_host, 4 * 2048 * sizeof(double)) != cudaSuccess) {
         cudaGetLastError();
         lqcd_destroy(c);
         return LQCD_ERR_NOMEM;

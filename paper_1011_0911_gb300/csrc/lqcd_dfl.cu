@@ -232,7 +232,7 @@ __global__ void k_block_gs(Geom g, DBlk B, T *v, int Ns, long fstride, int *bad)
     }
 }
 
-// little Dirac build for vector l = blockIdx.y: Aint[b][j][l][k] = <phi_k|_b, W_j>
+// little Dirac build for vector l = blockIdx.y: Aint[b][j][k][l] = <phi_k|_b, W_j>
 template <class T>
 __global__ void k_little_build(Geom g, DBlk B, const T *phi, int Ns, long fstride, const double2 *U,
                                const double2 *A0, const double2 *A1, double2 *Aint)
@@ -296,7 +296,7 @@ __global__ void k_little_build(Geom g, DBlk B, const T *phi, int Ns, long fstrid
                 }
             }
             block_sum(d, 2 * kn, sh, res);
-            if (t < kn) Aint[(((long)b * 9 + j) * Ns + l) * Ns + k0 + t] = make_double2(res[2 * t], res[2 * t + 1]);
+            if (t < kn) Aint[(((long)b * 9 + j) * Ns + k0 + t) * Ns + l] = make_double2(res[2 * t], res[2 * t + 1]);
             __syncthreads();
         }
     }
@@ -314,17 +314,38 @@ __global__ void k_project(Geom g, DBlk B, const T *phi, int Ns, long fstride, co
     C w[12];
     ld(in + s.p * 12 * (long)g.Vh, g.Vh, s.r, w);
     const long hs = fstride / 2;
+    // FP32 subspace: the site's products in float (GB300's FP64 pipe is the bound
+    // otherwise), the sums over sites in double
+    float wf[24];
+    if constexpr (sizeof(T) == 16 && !std::is_same<T, double2>::value)
+        for (int cc = 0; cc < 12; cc++) {
+            wf[2 * cc] = (float)w[cc].re;
+            wf[2 * cc + 1] = (float)w[cc].im;
+        }
     for (int k0 = 0; k0 < Ns; k0 += RCHUNK) {
         double d[2 * RCHUNK];
         int kn = min(RCHUNK, Ns - k0);
         for (int i = 0; i < RCHUNK; i++) {
             d[2 * i] = d[2 * i + 1] = 0;
             if (i < kn) {
-                C q[12];
-                ld(phi + (k0 + i) * fstride + s.p * hs, g.Vh, s.r, q);
-                for (int cc = 0; cc < 12; cc++) {
-                    d[2 * i] += q[cc].re * w[cc].re + q[cc].im * w[cc].im;
-                    d[2 * i + 1] += q[cc].re * w[cc].im - q[cc].im * w[cc].re;
+                if constexpr (std::is_same<T, double2>::value) {
+                    C q[12];
+                    ld(phi + (k0 + i) * fstride + s.p * hs, g.Vh, s.r, q);
+                    for (int cc = 0; cc < 12; cc++) {
+                        d[2 * i] += q[cc].re * w[cc].re + q[cc].im * w[cc].im;
+                        d[2 * i + 1] += q[cc].re * w[cc].im - q[cc].im * w[cc].re;
+                    }
+                } else {
+                    const float4 *f = (const float4 *)(phi + (k0 + i) * fstride + s.p * hs) + s.r;
+                    float re = 0, im = 0;
+#pragma unroll
+                    for (int q = 0; q < 6; q++) {
+                        float4 v = f[q * g.Vh];
+                        re += v.x * wf[4 * q] + v.y * wf[4 * q + 1] + v.z * wf[4 * q + 2] + v.w * wf[4 * q + 3];
+                        im += v.x * wf[4 * q + 1] - v.y * wf[4 * q] + v.z * wf[4 * q + 3] - v.w * wf[4 * q + 2];
+                    }
+                    d[2 * i] = re;
+                    d[2 * i + 1] = im;
                 }
             }
         }
@@ -342,45 +363,35 @@ __global__ void k_expand(Geom g, DBlk B, const T *phi, int Ns, long fstride, con
     bsite(g, B, b, t, s);
     const long hs = fstride / 2;
     C w[12];
-    for (int cc = 0; cc < 12; cc++) w[cc] = mk(0.0, 0.0);
-    for (int k = 0; k < Ns; k++) {
-        double2 ck = c[(long)b * Ns + k];
-        C a = mk(ck.x, ck.y), q[12];
-        ld(phi + k * fstride + s.p * hs, g.Vh, s.r, q);
-        for (int cc = 0; cc < 12; cc++) w[cc] = w[cc] + a * q[cc];
+    if constexpr (std::is_same<T, double2>::value) {
+        for (int cc = 0; cc < 12; cc++) w[cc] = mk(0.0, 0.0);
+        for (int k = 0; k < Ns; k++) {
+            double2 ck = c[(long)b * Ns + k];
+            C a = mk(ck.x, ck.y), q[12];
+            ld(phi + k * fstride + s.p * hs, g.Vh, s.r, q);
+            for (int cc = 0; cc < 12; cc++) w[cc] = w[cc] + a * q[cc];
+        }
+    } else {
+        // FP32 subspace: products and sums in float
+        float acc[24];
+#pragma unroll
+        for (int i = 0; i < 24; i++) acc[i] = 0.f;
+        for (int k = 0; k < Ns; k++) {
+            double2 ck = c[(long)b * Ns + k];
+            const float ar = (float)ck.x, ai = (float)ck.y;
+            const float4 *f = (const float4 *)(phi + k * fstride + s.p * hs) + s.r;
+#pragma unroll
+            for (int q = 0; q < 6; q++) {
+                float4 v = f[q * g.Vh];
+                acc[4 * q] += ar * v.x - ai * v.y;
+                acc[4 * q + 1] += ar * v.y + ai * v.x;
+                acc[4 * q + 2] += ar * v.z - ai * v.w;
+                acc[4 * q + 3] += ar * v.w + ai * v.z;
+            }
+        }
+        for (int cc = 0; cc < 12; cc++) w[cc] = mk((double)acc[2 * cc], (double)acc[2 * cc + 1]);
     }
     st(out + s.p * 12 * (long)g.Vh, g.Vh, s.r, w);
-}
-
-// out[b*Ns + k] = sum_j sum_l Aint[b][j][l][k] c[nbr[b][j]*Ns + l]
-__global__ void k_little_apply(int nblk, int Ns, const int *nbr, const double2 *__restrict__ Aint,
-                               const double2 *__restrict__ c, double2 *out)
-{
-    long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
-    if (i >= (long)nblk * Ns) return;
-    int b = (int)(i / Ns), k = (int)(i % Ns);
-    double re = 0, im = 0;
-    for (int j = 0; j < 9; j++) {
-        int nb = nbr[b * 9 + j];
-        const double2 *a = Aint + ((long)b * 9 + j) * Ns * Ns + k;
-        const double2 *cv = c + (long)nb * Ns;
-        for (int l = 0; l < Ns; l++) {
-            double2 x = a[l * Ns], y = cv[l];
-            re += x.x * y.x - x.y * y.y;
-            im += x.x * y.y + x.y * y.x;
-        }
-    }
-    out[i] = make_double2(re, im);
-}
-
-// export: Aint[b][j][l][k] -> A[b][j][k][l]
-__global__ void k_little_export(long n, int Ns, const double2 *Aint, double2 *A)
-{
-    long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    long bj = i / (Ns * Ns);
-    int r = (int)(i % (Ns * Ns)), k = r / Ns, l = r % Ns;
-    A[i] = Aint[bj * Ns * Ns + l * Ns + k];
 }
 
 // F32 / F64 native field scale and norm helpers
@@ -417,6 +428,181 @@ __global__ void k_sum_partials(int n, const double *p, double *out)
     }
 }
 
+// inverse of every diagonal block A_bb of the little operator (block-Jacobi
+// preconditioner of the coarse solve): one warp per block, Gauss-Jordan with
+// partial pivoting on the Ns x Ns matrix held in shared memory.  Layout as
+// Aint: element (row k, column l) at [k*Ns + l].
+__global__ void k_block_inverse(int nblk, int Ns, const double2 *Aint, double2 *Dinv, int *bad)
+{
+    extern __shared__ double2 sm[];
+    const int warps = blockDim.x >> 5;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int b = blockIdx.x * warps + w;
+    if (b >= nblk) return;
+    double2 *M = sm + (size_t)w * 2 * Ns * Ns;   // [Ns][2Ns] row-major augmented matrix
+    const int n2 = 2 * Ns;
+    const double2 *A = Aint + (size_t)b * 9 * Ns * Ns;   // entry j = 0
+    for (int e = lane; e < Ns * n2; e += 32) {
+        int i = e / n2, j = e % n2;
+        M[e] = j < Ns ? A[i * Ns + j] : make_double2(j - Ns == i ? 1.0 : 0.0, 0.0);
+    }
+    __syncwarp();
+    double amax = 0;
+    for (int e = 0; e < Ns * Ns; e++) amax = fmax(amax, hypot(M[(e / Ns) * n2 + e % Ns].x, M[(e / Ns) * n2 + e % Ns].y));
+    for (int k = 0; k < Ns; k++) {
+        int p = k;
+        double best = hypot(M[k * n2 + k].x, M[k * n2 + k].y);
+        for (int i = k + 1; i < Ns; i++) {
+            double v = hypot(M[i * n2 + k].x, M[i * n2 + k].y);
+            if (v > best) {
+                best = v;
+                p = i;
+            }
+        }
+        if (!(best > 1e-14 * amax)) {
+            if (lane == 0) atomicAdd(bad, 1);
+            return;
+        }
+        if (p != k)
+            for (int j = lane; j < n2; j += 32) {
+                double2 t = M[k * n2 + j];
+                M[k * n2 + j] = M[p * n2 + j];
+                M[p * n2 + j] = t;
+            }
+        __syncwarp();
+        double2 d = M[k * n2 + k];
+        double dn = d.x * d.x + d.y * d.y;
+        double2 di = make_double2(d.x / dn, -d.y / dn);
+        for (int j = lane; j < n2; j += 32) {
+            double2 v = M[k * n2 + j];
+            M[k * n2 + j] = make_double2(v.x * di.x - v.y * di.y, v.x * di.y + v.y * di.x);
+        }
+        __syncwarp();
+        for (int i = 0; i < Ns; i++) {
+            if (i == k) continue;
+            double2 f = M[i * n2 + k];
+            __syncwarp();
+            for (int j = lane; j < n2; j += 32) {
+                double2 v = M[k * n2 + j], m = M[i * n2 + j];
+                M[i * n2 + j] = make_double2(m.x - (f.x * v.x - f.y * v.y), m.y - (f.x * v.y + f.y * v.x));
+            }
+            __syncwarp();
+        }
+    }
+    double2 *Di = Dinv + (size_t)b * Ns * Ns;
+    for (int e = lane; e < Ns * Ns; e += 32) {
+        int k = e / Ns, l = e % Ns;   // row k, column l of the inverse
+        Di[k * Ns + l] = M[k * n2 + Ns + l];
+    }
+}
+
+__device__ __forceinline__ void warp_sum2(double &re, double &im)
+{
+    for (int o = 16; o > 0; o >>= 1) {
+        re += __shfl_down_sync(0xffffffffu, re, o);
+        im += __shfl_down_sync(0xffffffffu, im, o);
+    }
+}
+
+// out_r[b*Ns + k] = sum_l Dinv[b][k][l] in_r[b*Ns + l]: one CTA per block b,
+// warp k computes row k (lane l holds column l), the row is kept in registers
+// for all nrhs vectors (stride N).
+__global__ void k_block_jacobi(int nblk, int Ns, long N, int nrhs, const double2 *__restrict__ Dinv,
+                               const double2 *__restrict__ in, double2 *out)
+{
+    const int b = blockIdx.x, k = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (b >= nblk || k >= Ns) return;
+    double2 a = l < Ns ? Dinv[((size_t)b * Ns + k) * Ns + l] : make_double2(0, 0);
+    for (int r = 0; r < nrhs; r++) {
+        double2 y = l < Ns ? in[r * N + (long)b * Ns + l] : make_double2(0, 0);
+        double re = a.x * y.x - a.y * y.y, im = a.x * y.y + a.y * y.x;
+        warp_sum2(re, im);
+        if (l == 0) out[r * N + (long)b * Ns + k] = make_double2(re, im);
+    }
+}
+
+// FP32 operator variants: matrices stored as float2, products and the row sums
+// in float, FP64 vectors in and out (the coarse GCR itself stays FP64)
+__global__ void k_block_jacobi32(int nblk, int Ns, long N, int nrhs, const float2 *__restrict__ Dinv,
+                                 const double2 *__restrict__ in, double2 *out)
+{
+    const int b = blockIdx.x, k = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (b >= nblk || k >= Ns) return;
+    float2 a = l < Ns ? Dinv[((size_t)b * Ns + k) * Ns + l] : make_float2(0, 0);
+    for (int r = 0; r < nrhs; r++) {
+        double2 yd = l < Ns ? in[r * N + (long)b * Ns + l] : make_double2(0, 0);
+        float yx = (float)yd.x, yy = (float)yd.y;
+        double re = a.x * yx - a.y * yy, im = a.x * yy + a.y * yx;
+        warp_sum2(re, im);
+        if (l == 0) out[r * N + (long)b * Ns + k] = make_double2(re, im);
+    }
+}
+__global__ void k_little_apply_b32(int nblk, int Ns, long N, int nrhs, const int *nbr,
+                                   const float2 *__restrict__ Aint, const double2 *__restrict__ c, double2 *out)
+{
+    const int b = blockIdx.x, k = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (b >= nblk || k >= Ns) return;
+    float2 a[9];
+    int nb[9];
+#pragma unroll
+    for (int j = 0; j < 9; j++) {
+        nb[j] = nbr[b * 9 + j];
+        a[j] = l < Ns ? Aint[(((long)b * 9 + j) * Ns + k) * Ns + l] : make_float2(0, 0);
+    }
+    for (int r = 0; r < nrhs; r++) {
+        float re = 0, im = 0;
+        if (l < Ns) {
+            const double2 *cr = c + r * N + l;
+#pragma unroll
+            for (int j = 0; j < 9; j++) {
+                double2 yd = cr[(long)nb[j] * Ns];
+                float yx = (float)yd.x, yy = (float)yd.y;
+                re += a[j].x * yx - a[j].y * yy;
+                im += a[j].x * yy + a[j].y * yx;
+            }
+        }
+        double dre = re, dim = im;
+        warp_sum2(dre, dim);
+        if (l == 0) out[r * N + (long)b * Ns + k] = make_double2(dre, dim);
+    }
+}
+__global__ void k_to_float2(long n, const double2 *in, float2 *out)
+{
+    long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (i < n) out[i] = make_float2((float)in[i].x, (float)in[i].y);
+}
+
+// batched little operator apply, out_r[b*Ns + k] = sum_j sum_l A[b][j][k][l]
+// c_r[nbr[b][j]*Ns + l]: one CTA per block, warp per row, the nine row
+// segments in registers and reused for every right-hand side.
+__global__ void k_little_apply_b(int nblk, int Ns, long N, int nrhs, const int *nbr,
+                                 const double2 *__restrict__ Aint, const double2 *__restrict__ c, double2 *out)
+{
+    const int b = blockIdx.x, k = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (b >= nblk || k >= Ns) return;
+    double2 a[9];
+    int nb[9];
+#pragma unroll
+    for (int j = 0; j < 9; j++) {
+        nb[j] = nbr[b * 9 + j];
+        a[j] = l < Ns ? Aint[(((long)b * 9 + j) * Ns + k) * Ns + l] : make_double2(0, 0);
+    }
+    for (int r = 0; r < nrhs; r++) {
+        double re = 0, im = 0;
+        if (l < Ns) {
+            const double2 *cr = c + r * N + l;
+#pragma unroll
+            for (int j = 0; j < 9; j++) {
+                double2 y = cr[(long)nb[j] * Ns];
+                re += a[j].x * y.x - a[j].y * y.y;
+                im += a[j].x * y.y + a[j].y * y.x;
+            }
+        }
+        warp_sum2(re, im);
+        if (l == 0) out[r * N + (long)b * Ns + k] = make_double2(re, im);
+    }
+}
+
 }  // namespace
 
 struct DflState {
@@ -426,8 +612,11 @@ struct DflState {
     void *phi = nullptr;   // Ns native full fields
     int *nbr = nullptr;    // [nblk][9] device
     double2 *Aint = nullptr;
+    double2 *Dinv = nullptr;   // [nblk][Ns][Ns] inverses of the diagonal blocks
+    float2 *Aint32 = nullptr, *Dinv32 = nullptr;   // FP32 copies (coarse_prec == LQCD_F32)
     lqcd_dfl_params params;
     std::vector<int> nbr_host;
+    long coarse_iters = 0, coarse_solves = 0;
 };
 
 void dfl_free(lqcd_ctx *c)
@@ -436,6 +625,9 @@ void dfl_free(lqcd_ctx *c)
     cudaFree(c->dfl->phi);
     cudaFree(c->dfl->nbr);
     cudaFree(c->dfl->Aint);
+    cudaFree(c->dfl->Dinv);
+    cudaFree(c->dfl->Aint32);
+    cudaFree(c->dfl->Dinv32);
     delete c->dfl;
     c->dfl = nullptr;
 }
@@ -499,135 +691,245 @@ lqcd_status expand(lqcd_ctx *c, const double2 *cv, double2 *out)
 {
     return c->dfl->prec == LQCD_F64 ? launch_expand<double2>(c, cv, out) : launch_expand<float4>(c, cv, out);
 }
-lqcd_status little_apply(lqcd_ctx *c, const double2 *cv, double2 *out)
+lqcd_status little_apply_b(lqcd_ctx *c, const double2 *cv, double2 *out, int nrhs)
 {
     DflState *d = c->dfl;
-    long n = (long)d->B.nblk * d->Ns;
-    k_little_apply<<<div_up(n, 128), 128, 0, c->stream>>>(d->B.nblk, d->Ns, d->nbr, d->Aint, cv, out);
+    long N = (long)d->B.nblk * d->Ns;
+    if (d->Aint32)
+        k_little_apply_b32<<<d->B.nblk, 32 * d->Ns, 0, c->stream>>>(d->B.nblk, d->Ns, N, nrhs, d->nbr, d->Aint32, cv,
+                                                                    out);
+    else
+        k_little_apply_b<<<d->B.nblk, 32 * d->Ns, 0, c->stream>>>(d->B.nblk, d->Ns, N, nrhs, d->nbr, d->Aint, cv, out);
+    c->n_kernel_launches++;
+    LQCD_LAUNCH_CHECK(c);
+    return LQCD_OK;
+}
+lqcd_status little_apply(lqcd_ctx *c, const double2 *cv, double2 *out) { return little_apply_b(c, cv, out, 1); }
+
+lqcd_status block_jacobi(lqcd_ctx *c, const double2 *in, double2 *out, int nrhs)
+{
+    DflState *d = c->dfl;
+    long N = (long)d->B.nblk * d->Ns;
+    if (d->Dinv32)
+        k_block_jacobi32<<<d->B.nblk, 32 * d->Ns, 0, c->stream>>>(d->B.nblk, d->Ns, N, nrhs, d->Dinv32, in, out);
+    else
+        k_block_jacobi<<<d->B.nblk, 32 * d->Ns, 0, c->stream>>>(d->B.nblk, d->Ns, N, nrhs, d->Dinv, in, out);
     c->n_kernel_launches++;
     LQCD_LAUNCH_CHECK(c);
     return LQCD_OK;
 }
 
-// plain FP64 GCR on the little operator, x = A^-1 b approximately
-lqcd_status coarse_gcr(lqcd_ctx *c, const double2 *b, double2 *x, double tol, int nkv, int nmx, int *iters)
+// ---- device-resident scalar bookkeeping of the coarse GCR (one thread per rhs)
+constexpr int CG_R = 64, CG_K = 32;
+struct CoarseScal {
+    double bn2[CG_R], rr[CG_R], tol2;
+    int active[CG_R], bad[CG_R];
+    double2 a[CG_R][CG_K][CG_K];   // a[r][i][k] = <q_i, q_k>
+    double bk[CG_R][CG_K];
+    double2 ck[CG_R][CG_K];
+    double2 cfR[CG_R], cfS[CG_R];
+    double2 alpha[CG_R * CG_K];
+    double2 dots[2048];
+};
+
+__global__ void k_c_init(int nrhs, double tol2, CoarseScal *s)
+{
+    int r = threadIdx.x;
+    if (r == 0) s->tol2 = tol2;
+    if (r >= nrhs) return;
+    double b2 = s->dots[r].x;
+    s->bn2[r] = b2;
+    s->rr[r] = b2;
+    s->bad[r] = 0;
+    s->active[r] = (b2 > 0 && isfinite(b2)) ? 1 : 0;
+}
+// store the Gram-Schmidt coefficients <q_i, q_k> (they are applied straight from s->dots)
+__global__ void k_c_gs(int nrhs, int k, CoarseScal *s)
+{
+    int r = blockIdx.x, i = threadIdx.x;
+    if (r >= nrhs || i >= k) return;
+    s->a[r][i][k] = s->dots[r * k + i];
+}
+// from |q_k|^2 and <rho, q_k>: b_k, c_k, the coefficients of rho -= c_k q_k / b_k
+// and q_k *= 1/b_k, the updated |rho|^2 and the convergence flag
+__global__ void k_c_norm(int nrhs, int k, CoarseScal *s)
+{
+    int r = threadIdx.x;
+    if (r >= nrhs) return;
+    double q2 = s->dots[2 * r].x;
+    double2 rq = s->dots[2 * r + 1];
+    double bk = sqrt(q2);
+    bool ok = bk > 0 && isfinite(bk);
+    if (s->active[r] && !ok) {
+        s->active[r] = 0;
+        s->bad[r] = 1;
+    }
+    double sc = ok ? 1.0 / bk : 0.0;
+    double cr = rq.x * sc, ci = -rq.y * sc;   // c_k = <q_k/b_k, rho>
+    int act = s->active[r];
+    s->bk[r][k] = bk;
+    s->ck[r][k] = act ? make_double2(cr, ci) : make_double2(0, 0);
+    s->cfR[r] = act ? make_double2(cr * sc, ci * sc) : make_double2(0, 0);
+    s->cfS[r] = make_double2(sc - 1.0, 0);
+    if (act) {
+        double rr = s->rr[r] - (cr * cr + ci * ci);
+        s->rr[r] = rr > 0 ? rr : 0;
+        if (s->rr[r] <= s->tol2 * s->bn2[r]) s->active[r] = 0;
+    }
+}
+// alpha_j = (c_j - sum_{i>j} a_ji alpha_i) / b_j
+__global__ void k_c_backsub(int nrhs, int nk, CoarseScal *s)
+{
+    int r = threadIdx.x;
+    if (r >= nrhs) return;
+    double2 *al = s->alpha + r * nk;
+    for (int j = nk - 1; j >= 0; j--) {
+        double sr = s->ck[r][j].x, si = s->ck[r][j].y;
+        for (int i = j + 1; i < nk; i++) {
+            double2 a = s->a[r][j][i], x = al[i];
+            sr -= a.x * x.x - a.y * x.y;
+            si -= a.x * x.y + a.y * x.x;
+        }
+        double bj = s->bk[r][j];
+        al[j] = bj > 0 ? make_double2(sr / bj, si / bj) : make_double2(0, 0);
+    }
+}
+// true residual norm after a restart
+__global__ void k_c_restart(int nrhs, CoarseScal *s, int *n_active)
+{
+    int r = threadIdx.x;
+    if (r < nrhs) {
+        s->rr[r] = s->dots[r].x;
+        if (s->active[r] && s->rr[r] <= s->tol2 * s->bn2[r]) s->active[r] = 0;
+        if (!isfinite(s->rr[r])) {
+            s->active[r] = 0;
+            s->bad[r] = 1;
+        }
+    }
+    __syncthreads();
+    if (r == 0) {
+        int n = 0;
+        for (int i = 0; i < nrhs; i++) n += s->active[i];
+        *n_active = n;
+    }
+}
+
+// FP64 GCR on the little operator for nrhs coarse right-hand sides in
+// lockstep, right-preconditioned by the inverse diagonal blocks (block
+// Jacobi): x_r ~ A^-1 b_r to a relative residual tol, or nmx steps.  All
+// scalars stay on the device: inside a Krylov cycle nothing returns to the
+// host; after each cycle the host reads the number of unconverged right-hand
+// sides (one synchronisation per cycle).  A right-hand side that converges
+// inside a cycle gets zero updates for the rest of it.
+lqcd_status coarse_gcr(lqcd_ctx *c, const double2 *b, double2 *x, int nrhs, double tol, int nkv, int nmx,
+                       int *iters)
 {
     DflState *d = c->dfl;
     const long N = (long)d->B.nblk * d->Ns;
     const long n2 = 2 * N;
-    if (nkv < 1 || nkv > 64) return set_err(c, LQCD_ERR_ARG, "coarse nkv=%d", nkv);
+    if (nkv < 1 || nkv > CG_K || nrhs > CG_R || nrhs * nkv > 2048)
+        return set_err(c, LQCD_ERR_ARG, "coarse nkv=%d nrhs=%d", nkv, nrhs);
+    const long bN = nrhs * N;
     void *buf;
-    LQCD_TRY(ws_get(c, WS_COARSE, (size_t)(2 * nkv + 2) * N * sizeof(double2), &buf));
-    double2 *P = (double2 *)buf, *Q = P + nkv * N, *rho = Q + nkv * N, *w = rho + N;
-    LQCD_TRY(blas_zero(c, N * sizeof(double2), x));
-    LQCD_TRY(blas_copy(c, n2, (const double *)b, (double *)rho));
-    double bn2;
-    LQCD_TRY(blas_norm2(c, n2, (const double *)b, &bn2));
-    double bn = std::sqrt(bn2), res = bn;
-    std::vector<double> a(2 * nkv * nkv), cc(2 * nkv), al(2 * nkv), bb(nkv), dots(128), coef(128);
-    int it = 0;
-    lqcd_status st = LQCD_ERR_NOT_CONVERGED;
-    if (bn == 0) st = LQCD_OK;
-    while (st != LQCD_OK && it < nmx) {
+    const size_t vec_bytes = (size_t)(2 * nkv + 2) * bN * sizeof(double2);
+    LQCD_TRY(ws_get(c, WS_COARSE, vec_bytes + sizeof(CoarseScal) + 256, &buf));
+    double2 *P = (double2 *)buf, *Q = P + nkv * bN, *rho = Q + nkv * bN, *w = rho + bN;
+    CoarseScal *S = (CoarseScal *)((char *)buf + ((vec_bytes + 255) / 256) * 256);
+    int *n_active_dev = (int *)c->red_out;
+    int *n_active_host = (int *)c->red_host;
+    LQCD_TRY(blas_zero(c, bN * sizeof(double2), x));
+    LQCD_TRY(blas_copy(c, n2 * nrhs, (const double *)b, (double *)rho));
+    LQCD_TRY(bblas_dot_dev(c, n2, nrhs, (const double *)b, 0, n2, (const double *)b, n2, 1, S->dots));
+    k_c_init<<<1, CG_R, 0, c->stream>>>(nrhs, tol * tol, S);
+    c->n_kernel_launches++;
+    int it = 0, active = nrhs;
+    while (active > 0 && it < nmx) {
         int nk = 0;
         for (int k = 0; k < nkv && it < nmx; k++) {
-            double2 *pk = P + k * N, *qk = Q + k * N;
-            LQCD_TRY(blas_copy(c, n2, (const double *)rho, (double *)pk));
-            LQCD_TRY(little_apply(c, pk, qk));
-            for (int i = 0; i < k; i++) a[2 * (i * nkv + k)] = a[2 * (i * nkv + k) + 1] = 0;
-            for (int pass = 0; pass < 2 && k > 0; pass++) {
-                LQCD_TRY(blas_dot(c, n2, (const double *)Q, (const double *)qk, k, n2, dots.data()));
-                for (int i = 0; i < k; i++) {
-                    a[2 * (i * nkv + k)] += dots[2 * i];
-                    a[2 * (i * nkv + k) + 1] += dots[2 * i + 1];
-                }
-                LQCD_TRY(blas_multi_axpy(c, n2, k, dots.data(), (const double *)Q, n2, (double *)qk, -1.0));
+            double2 *pk = P + k * bN, *qk = Q + k * bN;
+            LQCD_TRY(block_jacobi(c, rho, pk, nrhs));
+            LQCD_TRY(little_apply_b(c, pk, qk, nrhs));
+            if (k > 0) {
+                LQCD_TRY(bblas_dot_dev(c, n2, nrhs, (const double *)Q, 2 * bN, n2, (const double *)qk, n2, k, S->dots));
+                k_c_gs<<<nrhs, k, 0, c->stream>>>(nrhs, k, S);
+                c->n_kernel_launches++;
+                LQCD_TRY(bblas_multi_axpy_dev(c, n2, nrhs, k, S->dots, (const double *)Q, 2 * bN, n2, (double *)qk, n2,
+                                              -1.0));
             }
-            double q2;
-            LQCD_TRY(blas_norm2(c, n2, (const double *)qk, &q2));
-            bb[k] = std::sqrt(q2);
-            if (!(bb[k] > 0) || !std::isfinite(bb[k])) {
-                st = std::isfinite(bb[k]) ? LQCD_ERR_BREAKDOWN : LQCD_ERR_NAN;
-                break;
-            }
-            LQCD_TRY(blas_scal(c, n2, 1.0 / bb[k], 0, (double *)qk));
-            LQCD_TRY(blas_dot(c, n2, (const double *)qk, (const double *)rho, 1, 0, dots.data()));
-            cc[2 * k] = dots[0];
-            cc[2 * k + 1] = dots[1];
-            LQCD_TRY(blas_axpy(c, n2, -dots[0], -dots[1], (const double *)qk, (double *)rho));
+            // |q_k|^2 and <rho, q_k> in one pass
+            LQCD_TRY(bblas_dot_dev(c, n2, nrhs, (const double *)qk, 2 * (rho - qk), n2, (const double *)qk, n2, 2,
+                                   S->dots));
+            k_c_norm<<<1, CG_R, 0, c->stream>>>(nrhs, k, S);
+            c->n_kernel_launches++;
+            LQCD_TRY(bblas_multi_axpy_dev(c, n2, nrhs, 1, S->cfR, (const double *)qk, 0, n2, (double *)rho, n2, -1.0));
+            LQCD_TRY(bblas_multi_axpy_dev(c, n2, nrhs, 1, S->cfS, (const double *)qk, 0, n2, (double *)qk, n2, 1.0));
             it++;
             nk = k + 1;
-            double r2;
-            LQCD_TRY(blas_norm2(c, n2, (const double *)rho, &r2));
-            res = std::sqrt(r2);
-            if (res <= tol * bn) break;
         }
-        for (int j = nk - 1; j >= 0; j--) {
-            double sr = cc[2 * j], si = cc[2 * j + 1];
-            for (int i = j + 1; i < nk; i++) {
-                double ar = a[2 * (j * nkv + i)], ai = a[2 * (j * nkv + i) + 1];
-                sr -= ar * al[2 * i] - ai * al[2 * i + 1];
-                si -= ar * al[2 * i + 1] + ai * al[2 * i];
-            }
-            al[2 * j] = sr / bb[j];
-            al[2 * j + 1] = si / bb[j];
-        }
-        if (nk > 0) LQCD_TRY(blas_multi_axpy(c, n2, nk, al.data(), (const double *)P, n2, (double *)x, 1.0));
-        if (st == LQCD_ERR_BREAKDOWN || st == LQCD_ERR_NAN) break;
-        LQCD_TRY(little_apply(c, x, w));
-        LQCD_TRY(blas_sub(c, n2, (const double *)b, (const double *)w, (double *)rho));
-        double r2;
-        LQCD_TRY(blas_norm2(c, n2, (const double *)rho, &r2));
-        res = std::sqrt(r2);
-        if (res <= tol * bn) st = LQCD_OK;
+        k_c_backsub<<<1, CG_R, 0, c->stream>>>(nrhs, nk, S);
+        c->n_kernel_launches++;
+        LQCD_TRY(bblas_multi_axpy_dev(c, n2, nrhs, nk, S->alpha, (const double *)P, 2 * bN, n2, (double *)x, n2, 1.0));
+        LQCD_TRY(little_apply_b(c, x, w, nrhs));
+        LQCD_TRY(blas_sub(c, n2 * nrhs, (const double *)b, (const double *)w, (double *)rho));
+        LQCD_TRY(bblas_dot_dev(c, n2, nrhs, (const double *)rho, 0, n2, (const double *)rho, n2, 1, S->dots));
+        k_c_restart<<<1, CG_R, 0, c->stream>>>(nrhs, S, n_active_dev);
+        c->n_kernel_launches++;
+        LQCD_LAUNCH_CHECK(c);
+        LQCD_CUDA_CHECK(c, cudaMemcpyAsync(n_active_host, n_active_dev, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+        LQCD_CUDA_CHECK(c, cudaStreamSynchronize(c->stream));
+        active = *n_active_host;
     }
+    d->coarse_iters += it;
+    d->coarse_solves += 1;
     if (iters) *iters = it;
-    return st;
+    return active > 0 ? LQCD_ERR_NOT_CONVERGED : LQCD_OK;
 }
 
-lqcd_status precond_sap(lqcd_ctx *c, const lqcd_sap_params *sp, const double2 *rho, double2 *phi)
+lqcd_status precond_sap(lqcd_ctx *c, const lqcd_sap_params *sp, const double2 *rho, double2 *phi, int nrhs)
 {
-    if (sp->prec == LQCD_F64) return sap_apply(c, sp, rho, phi);
+    if (sp->prec == LQCD_F64) return sap_apply(c, sp, rho, phi, nrhs);
     void *a, *b;
-    size_t fb = 2 * native_half_bytes(c, sp->prec);
+    size_t fb = 2 * native_half_bytes(c, sp->prec) * nrhs;
     LQCD_TRY(ws_get(c, WS_SAP_IN, fb, &a));
     LQCD_TRY(ws_get(c, WS_SAP_PSI, fb, &b));
-    LQCD_TRY(convert_native(c, LQCD_F64, sp->prec, rho, a, 2));
-    LQCD_TRY(sap_apply(c, sp, a, b));
-    return convert_native(c, sp->prec, LQCD_F64, b, phi, 2);
+    LQCD_TRY(convert_native(c, LQCD_F64, sp->prec, rho, a, 2 * nrhs));
+    LQCD_TRY(sap_apply(c, sp, a, b, nrhs));
+    return convert_native(c, sp->prec, LQCD_F64, b, phi, 2 * nrhs);
 }
 
 }  // namespace
 
-lqcd_status dfl_precond_native(lqcd_ctx *c, const lqcd_sap_params *sp, const double2 *rho, double2 *phi)
+// phi_r = M_dfl rho_r for nrhs native full FP64 fields
+lqcd_status dfl_precond_native(lqcd_ctx *c, const lqcd_sap_params *sp, const double2 *rho, double2 *phi, int nrhs)
 {
     DflState *d = c->dfl;
     if (!d) return set_err(c, LQCD_ERR_STATE, "deflation subspace not built");
     const long N = (long)d->B.nblk * d->Ns;
     const long nf = 24 * (long)c->g.Vh;   // double2 per full F64 field
     void *buf;
-    LQCD_TRY(ws_get(c, WS_DFL, (2 * N + 2 * nf) * sizeof(double2), &buf));
-    double2 *cv = (double2 *)buf, *ev = cv + N, *u = ev + N, *w = u + nf;
-    LQCD_TRY(project(c, rho, cv));
+    LQCD_TRY(ws_get(c, WS_DFL, (2 * N * nrhs + 2 * nf * nrhs) * sizeof(double2), &buf));
+    double2 *cv = (double2 *)buf, *ev = cv + N * nrhs, *u = ev + N * nrhs, *w = u + nf * nrhs;
+    // u_r = Pi A^-1 Pi^dag rho_r, the coarse solves of all right-hand sides together
+    for (int r = 0; r < nrhs; r++) LQCD_TRY(project(c, rho + r * nf, cv + r * N));
     int it = 0;
-    lqcd_status st = coarse_gcr(c, cv, ev, d->params.coarse_tol, d->params.coarse_nkv, d->params.coarse_nmx, &it);
+    lqcd_status st = coarse_gcr(c, cv, ev, nrhs, d->params.coarse_tol, d->params.coarse_nkv, d->params.coarse_nmx, &it);
     if (st != LQCD_OK && st != LQCD_ERR_NOT_CONVERGED) return set_err(c, st, "coarse solve failed (%d)", (int)st);
-    LQCD_TRY(expand(c, ev, u));
+    for (int r = 0; r < nrhs; r++) LQCD_TRY(expand(c, ev + r * N, u + r * nf));
     // w = rho - D u  (D in the SAP precision)
     if (sp->prec == LQCD_F64) {
-        LQCD_TRY(dirac_D(c, LQCD_F64, u, w, 1));
+        LQCD_TRY(dirac_D(c, LQCD_F64, u, w, nrhs));
     } else {
         void *a, *b2;
-        size_t fb = 2 * native_half_bytes(c, sp->prec);
+        size_t fb = 2 * native_half_bytes(c, sp->prec) * nrhs;
         LQCD_TRY(ws_get(c, WS_MISC, fb, &a));
         LQCD_TRY(ws_get(c, WS_MISC2, fb, &b2));
-        LQCD_TRY(convert_native(c, LQCD_F64, sp->prec, u, a, 2));
-        LQCD_TRY(dirac_D(c, sp->prec, a, b2, 1));
-        LQCD_TRY(convert_native(c, sp->prec, LQCD_F64, b2, w, 2));
+        LQCD_TRY(convert_native(c, LQCD_F64, sp->prec, u, a, 2 * nrhs));
+        LQCD_TRY(dirac_D(c, sp->prec, a, b2, nrhs));
+        LQCD_TRY(convert_native(c, sp->prec, LQCD_F64, b2, w, 2 * nrhs));
     }
-    LQCD_TRY(blas_sub(c, 2 * nf, (const double *)rho, (const double *)w, (double *)w));
-    LQCD_TRY(precond_sap(c, sp, w, phi));
-    return blas_axpy(c, 2 * nf, 1.0, 0, (const double *)u, (double *)phi);
+    LQCD_TRY(blas_sub(c, 2 * nf * nrhs, (const double *)rho, (const double *)w, (double *)w));
+    LQCD_TRY(precond_sap(c, sp, w, phi, nrhs));
+    return blas_axpy(c, 2 * nf * nrhs, 1.0, 0, (const double *)u, (double *)phi);
 }
 
 extern "C" {
@@ -703,20 +1005,22 @@ lqcd_status lqcd_dfl_build(lqcd_ctx *c, const lqcd_dfl_params *p, const double *
     sp.nmr = p->nmr;
     sp.prec = p->prec;
     void *tmp;
-    LQCD_TRY(ws_get(c, WS_SAP_PSI, fbytes, &tmp));
-    for (int pass = 0; pass < p->ninv; pass++)
+    LQCD_TRY(ws_get(c, WS_SAP_PSI, fbytes * p->Ns, &tmp));
+    for (int pass = 0; pass < p->ninv; pass++) {
+        // all Ns vectors through one batched SAP application
+        LQCD_TRY(sap_apply(c, &sp, d->phi, tmp, p->Ns));
+        LQCD_CUDA_CHECK(c, cudaMemcpyAsync(d->phi, tmp, fbytes * p->Ns, cudaMemcpyDeviceToDevice, c->stream));
         for (int l = 0; l < p->Ns; l++) {
             void *vl = (char *)d->phi + l * fbytes;
-            LQCD_TRY(sap_apply(c, &sp, vl, tmp));
             double n2;
-            LQCD_TRY(norm_native(c, p->prec, tmp, 2, &n2));
+            LQCD_TRY(norm_native(c, p->prec, vl, 2, &n2));
             if (!(n2 > 0) || !std::isfinite(n2)) {
                 dfl_free(c);
                 return set_err(c, LQCD_ERR_BREAKDOWN, "subspace vector %d vanished", l);
             }
-            LQCD_CUDA_CHECK(c, cudaMemcpyAsync(vl, tmp, fbytes, cudaMemcpyDeviceToDevice, c->stream));
             LQCD_TRY(scale_native(c, p->prec, vl, 2, 1.0 / std::sqrt(n2)));
         }
+    }
     // block Gram-Schmidt
     int *bad = (int *)c->red_out;
     LQCD_CUDA_CHECK(c, cudaMemsetAsync(bad, 0, sizeof(int), c->stream));
@@ -745,7 +1049,41 @@ lqcd_status lqcd_dfl_build(lqcd_ctx *c, const lqcd_dfl_params *p, const double *
                                                                c->U64, c->A64[0], c->A64[1], d->Aint);
     c->n_kernel_launches++;
     LQCD_LAUNCH_CHECK(c);
+    // block-Jacobi preconditioner of the coarse solve: inverses of the diagonal blocks
+    if (cudaMalloc(&d->Dinv, (size_t)B.nblk * p->Ns * p->Ns * sizeof(double2)) != cudaSuccess) {
+        cudaGetLastError();
+        dfl_free(c);
+        return set_err(c, LQCD_ERR_NOMEM, "coarse preconditioner allocation");
+    }
+    const size_t per_warp = 2 * (size_t)p->Ns * p->Ns * sizeof(double2);
+    const int warps = (int)std::max<size_t>(1, std::min<size_t>(4, (40 * 1024) / per_warp));
+    LQCD_CUDA_CHECK(c, cudaMemsetAsync(bad, 0, sizeof(int), c->stream));
+    k_block_inverse<<<div_up(B.nblk, warps), 32 * warps, warps * per_warp, c->stream>>>(B.nblk, p->Ns, d->Aint,
+                                                                                       d->Dinv, bad);
+    c->n_kernel_launches++;
+    LQCD_LAUNCH_CHECK(c);
+    LQCD_CUDA_CHECK(c, cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     LQCD_CUDA_CHECK(c, cudaStreamSynchronize(c->stream));
+    if (hbad) {
+        dfl_free(c);
+        return set_err(c, LQCD_ERR_BREAKDOWN, "little Dirac operator: %d singular diagonal blocks", hbad);
+    }
+    if (p->coarse_prec == LQCD_F32) {
+        const long na = (long)B.nblk * 9 * p->Ns * p->Ns, nd = (long)B.nblk * p->Ns * p->Ns;
+        if (cudaMalloc(&d->Aint32, na * sizeof(float2)) != cudaSuccess ||
+            cudaMalloc(&d->Dinv32, nd * sizeof(float2)) != cudaSuccess) {
+            cudaGetLastError();
+            dfl_free(c);
+            return set_err(c, LQCD_ERR_NOMEM, "FP32 little operator allocation");
+        }
+        k_to_float2<<<div_up(na, 256), 256, 0, c->stream>>>(na, d->Aint, d->Aint32);
+        k_to_float2<<<div_up(nd, 256), 256, 0, c->stream>>>(nd, d->Dinv, d->Dinv32);
+        c->n_kernel_launches += 2;
+        LQCD_LAUNCH_CHECK(c);
+    } else if (p->coarse_prec != LQCD_F64) {
+        dfl_free(c);
+        return set_err(c, LQCD_ERR_ARG, "coarse precision %d", (int)p->coarse_prec);
+    }
     return LQCD_OK;
 }
 
@@ -764,10 +1102,9 @@ lqcd_status lqcd_dfl_export(lqcd_ctx *c, double *phi, double *A)
         }
     }
     if (A) {
-        long n = (long)d->B.nblk * 9 * d->Ns * d->Ns;
-        k_little_export<<<div_up(n, 256), 256, 0, c->stream>>>(n, d->Ns, d->Aint, (double2 *)A);
-        c->n_kernel_launches++;
-        LQCD_LAUNCH_CHECK(c);
+        // the internal layout [b][j][k][l] is the exported one
+        size_t n = (size_t)d->B.nblk * 9 * d->Ns * d->Ns;
+        LQCD_CUDA_CHECK(c, cudaMemcpyAsync(A, d->Aint, n * sizeof(double2), cudaMemcpyDeviceToDevice, c->stream));
     }
     return LQCD_OK;
 }
@@ -804,8 +1141,17 @@ lqcd_status lqcd_dfl_coarse_solve(lqcd_ctx *c, const double *b, double *x, int *
     if (!c || !b || !x) return set_err(c, LQCD_ERR_ARG, "null argument");
     if (!c->dfl) return set_err(c, LQCD_ERR_STATE, "no subspace");
     DflState *d = c->dfl;
-    return coarse_gcr(c, (const double2 *)b, (double2 *)x, d->params.coarse_tol, d->params.coarse_nkv,
+    return coarse_gcr(c, (const double2 *)b, (double2 *)x, 1, d->params.coarse_tol, d->params.coarse_nkv,
                       d->params.coarse_nmx, iters);
+}
+
+lqcd_status lqcd_dfl_stats(const lqcd_ctx *c, long *coarse_solves, long *coarse_iters)
+{
+    if (!c) return LQCD_ERR_ARG;
+    if (!c->dfl) return LQCD_ERR_STATE;
+    if (coarse_solves) *coarse_solves = c->dfl->coarse_solves;
+    if (coarse_iters) *coarse_iters = c->dfl->coarse_iters;
+    return LQCD_OK;
 }
 
 lqcd_status lqcd_dfl_precond(lqcd_ctx *c, const lqcd_sap_params *sp, const double *rho, double *phi)
@@ -817,7 +1163,7 @@ lqcd_status lqcd_dfl_precond(lqcd_ctx *c, const lqcd_sap_params *sp, const doubl
     LQCD_TRY(ws_get(c, WS_PACK_IN, fb, &a));
     LQCD_TRY(ws_get(c, WS_PACK_OUT, fb, &b));
     LQCD_TRY(pack_field(c, LQCD_F64, 2, rho, a, 1, false));
-    LQCD_TRY(dfl_precond_native(c, sp, (const double2 *)a, (double2 *)b));
+    LQCD_TRY(dfl_precond_native(c, sp, (const double2 *)a, (double2 *)b, 1));
     return pack_field(c, LQCD_F64, 2, phi, b, 1, true);
 }
 

@@ -179,6 +179,14 @@ lqcd_status blas_copy(lqcd_ctx *c, long n2, const double *x, double *y);
 lqcd_status blas_sub(lqcd_ctx *c, long n2, const double *x, const double *y, double *z);  // z = x - y
 lqcd_status blas_multi_axpy(lqcd_ctx *c, long n2, int k, const double *coef_host, const double *X,
                             long stride, double *y, double sign);
+lqcd_status bblas_dot(lqcd_ctx *c, long n2, int nrhs, const double *A, long sa, long fa, const double *B, long fb,
+                      int k, double *host_out);
+lqcd_status bblas_multi_axpy(lqcd_ctx *c, long n2, int nrhs, int k, const double *coef_host, const double *X,
+                             long sa, long fa, double *y, long fy, double sign);
+lqcd_status bblas_dot_dev(lqcd_ctx *c, long n2, int nrhs, const double *A, long sa, long fa, const double *B, long fb,
+                          int k, double2 *out_dev);
+lqcd_status bblas_multi_axpy_dev(lqcd_ctx *c, long n2, int nrhs, int k, const double2 *coef_dev, const double *X,
+                                 long sa, long fa, double *y, long fy, double sign);
 lqcd_status blas_gamma5_native64(lqcd_ctx *c, long nhalf, const double2 *in, double2 *out);
 lqcd_status blas_zero(lqcd_ctx *c, size_t bytes, void *p);
 
@@ -186,8 +194,8 @@ lqcd_status blas_zero(lqcd_ctx *c, size_t bytes, void *p);
 lqcd_status sap_axpby_native(lqcd_ctx *c, lqcd_prec p, const void *eta, void *r);
 void sap_free_plans(lqcd_ctx *c);
 lqcd_status sap_apply(lqcd_ctx *c, const lqcd_sap_params *sp, const void *eta_native,
-                      void *psi_native);
+                      void *psi_native, int nrhs = 1);
 // deflation
 void dfl_free(lqcd_ctx *c);
 lqcd_status dfl_precond_native(lqcd_ctx *c, const lqcd_sap_params *sp, const double2 *rho,
-                               double2 *phi);
+                               double2 *phi, int nrhs);

@@ -317,12 +317,26 @@ struct SapArgs {
     Geom g;
     BlkGeom B;
     const int *blocks;   // block ids of this colour
-    const typename SapPT<R>::SP *r;    // native full field
-    typename SapPT<R>::SP *psi;        // native full field (updated)
+    typename SapPT<R>::SP *r;        // native full fields (residual; the block's part is replaced)
+    typename SapPT<R>::SP *psi;      // native full fields (updated)
+    typename SapPT<R>::SP *delta;    // native full fields: chi of the blocks of this colour
+    long fstride;                    // elements between the fields of consecutive right-hand sides
     const typename SapPT<R>::LK *U;
     const typename SapPT<R>::CL *Ae, *Aio;   // A on even sites, A^-1 on odd sites
     int nmr;
 };
+
+__device__ __forceinline__ void gstore(double2 *f, long Vh, long r, const cx<double> v[12])
+{
+#pragma unroll
+    for (int c = 0; c < 12; c++) f[c * Vh + r] = make_double2(v[c].re, v[c].im);
+}
+__device__ __forceinline__ void gstore(float4 *f, long Vh, long r, const cx<float> v[12])
+{
+#pragma unroll
+    for (int q = 0; q < 6; q++)
+        f[q * Vh + r] = make_float4(v[2 * q].re, v[2 * q].im, v[2 * q + 1].re, v[2 * q + 1].im);
+}
 
 template <class R>
 __global__ void __launch_bounds__(128) k_sap_block(SapArgs<R> a)
@@ -338,8 +352,11 @@ __global__ void __launch_bounds__(128) k_sap_block(SapArgs<R> a)
     cx<R> *ro = to + 12 * nh;
     R *red = (R *)(ro + 12 * nh);
     const long Vh = a.g.Vh;
-    const SP *r_e = a.r, *r_o = a.r + (sizeof(R) == 8 ? 12 : 6) * Vh;
-    SP *psi_e = a.psi, *psi_o = a.psi + (sizeof(R) == 8 ? 12 : 6) * Vh;
+    const long half = (sizeof(R) == 8 ? 12 : 6) * Vh;
+    const long foff = blockIdx.y * a.fstride;
+    SP *r_e = a.r + foff, *r_o = a.r + foff + half;
+    SP *psi_e = a.psi + foff, *psi_o = a.psi + foff + half;
+    SP *d_e = a.delta + foff, *d_o = a.delta + foff + half;
 
     int bid = a.blocks[blockIdx.x];
     int org[4];
@@ -425,7 +442,11 @@ __global__ void __launch_bounds__(128) k_sap_block(SapArgs<R> a)
         }
         __syncthreads();
     }
-    // chi_o = A_oo^-1 (r_o - H_oe,blk chi_e); psi += chi
+    // chi_o = A_oo^-1 (r_o - H_oe,blk chi_e); psi += chi; delta = chi.
+    // The block's new residual r - D_blk chi is (rho, 0): on odd sites it vanishes
+    // by construction of chi_o, on even sites it is the MinRes residual of
+    // Dhat_blk chi_e = b_e.  Hops from chi into other blocks are applied by
+    // k_sap_face afterwards.
     for (int t = threadIdx.x; t < nh; t += blockDim.x) {
         SiteInfo s;
         block_site(a.g, B, org, 1, t, s);
@@ -435,11 +456,399 @@ __global__ void __launch_bounds__(128) k_sap_block(SapArgs<R> a)
         for (int c = 0; c < 12; c++) v[c] = v[c] + R(0.5) * w[c];
         clov_apply<R>(a.Aio, Vh, s.grank, v, w);
         gadd(psi_o, Vh, s.grank, w);
+        gstore(d_o, Vh, s.grank, w);
+#pragma unroll
+        for (int c = 0; c < 12; c++) w[c] = mk(R(0), R(0));
+        gstore(r_o, Vh, s.grank, w);
         SiteInfo se;
         block_site(a.g, B, org, 0, t, se);
         sload(chi, nh, t, v);
         gadd(psi_e, Vh, se.grank, v);
+        gstore(d_e, Vh, se.grank, v);
+        sload(rho, nh, t, v);
+        gstore(r_e, Vh, se.grank, v);
     }
+}
+
+// ------------------------------------------------------------------------
+// FP32 block solve with the whole block resident in shared memory.
+//
+// At the start of a block visit the CTA stages the block's forward links (two
+// rows, all sites and directions), A_ee on its even sites, A_oo^-1 on its odd
+// sites and r_o into shared memory with coalesced loads; all MinRes phases
+// then run from shared memory.  Two threads per site: in a hop phase thread
+// h = 0 sums the four forward hops and h = 1 the four backward hops, the pair
+// exchanges its partial sums by a lane shuffle, and each thread then applies
+// one chirality block (spins 2h, 2h+1) of the clover term.  Same arithmetic
+// as k_sap_block, different summation order.
+constexpr int SAPS_NH = 128;   // sites of one parity per block (4^4 blocks)
+
+struct SapSmem {
+    float4 U[4][3][2 * SAPS_NH];   // forward links, two rows, local lexicographic site
+    float4 A[18][2 * SAPS_NH];     // A (even sites) or A^-1 (odd sites), local lexicographic site
+    float4 rho[6][SAPS_NH], chi[6][SAPS_NH], p[6][SAPS_NH], to[6][SAPS_NH], ro[6][SAPS_NH];
+    float red[3][8];
+};
+
+__device__ __forceinline__ int blk_lex(const BlkGeom &B, const int l[4])
+{
+    return l[3] + B.bs[3] * (l[2] + B.bs[2] * (l[1] + B.bs[1] * l[0]));
+}
+
+// local lexicographic index of the in-block neighbour l + d mu, or -1
+__device__ __forceinline__ int blk_nbr_lex(const BlkGeom &B, const int l[4], int mu, int d)
+{
+    int m[4] = {l[0], l[1], l[2], l[3]};
+    int v = m[mu] + d;
+    if (v < 0 || v >= B.bs[mu]) {
+        if (!B.wrap[mu]) return -1;
+        v = v < 0 ? v + B.bs[mu] : v - B.bs[mu];
+    }
+    m[mu] = v;
+    return blk_lex(B, m);
+}
+
+__device__ __forceinline__ void s_spinor(const float4 (*f)[SAPS_NH], int t, cx<float> v[12])
+{
+#pragma unroll
+    for (int q = 0; q < 6; q++) {
+        float4 a = f[q][t];
+        v[2 * q] = mk(a.x, a.y);
+        v[2 * q + 1] = mk(a.z, a.w);
+    }
+}
+__device__ __forceinline__ void s_link(const SapSmem &S, int mu, int ls, cx<float> u[3][3])
+{
+#pragma unroll
+    for (int q = 0; q < 3; q++) {
+        float4 a = S.U[mu][q][ls];
+        u[(2 * q) / 3][(2 * q) % 3] = mk(a.x, a.y);
+        u[(2 * q + 1) / 3][(2 * q + 1) % 3] = mk(a.z, a.w);
+    }
+    u[2][0] = conjx(u[0][1] * u[1][2] - u[0][2] * u[1][1]);
+    u[2][1] = conjx(u[0][2] * u[1][0] - u[0][0] * u[1][2]);
+    u[2][2] = conjx(u[0][0] * u[1][1] - u[0][1] * u[1][0]);
+}
+// one chirality block h of the clover matrix at local site ls applied to v[6]
+__device__ __forceinline__ void s_clover_half(const SapSmem &S, int ls, int h, const cx<float> v[6], cx<float> w[6])
+{
+    float a[36];
+#pragma unroll
+    for (int q = 0; q < 9; q++) {
+        float4 t = S.A[9 * h + q][ls];
+        a[4 * q] = t.x;
+        a[4 * q + 1] = t.y;
+        a[4 * q + 2] = t.z;
+        a[4 * q + 3] = t.w;
+    }
+#pragma unroll
+    for (int i = 0; i < 6; i++) w[i] = a[i] * v[i];
+    int k = 0;
+#pragma unroll
+    for (int i = 0; i < 6; i++)
+#pragma unroll
+        for (int j = i + 1; j < 6; j++) {
+            cx<float> o = mk(a[6 + 2 * k], a[7 + 2 * k]);
+            w[i] = w[i] + o * v[j];
+            w[j] = w[j] + cmulc(o, v[i]);
+            k++;
+        }
+}
+
+// half of the in-block hop sum at site (l, x, ls) from the smem field src of the
+// other parity: h = 0 forward hops, h = 1 backward hops; then the pair's halves
+// are added so both threads hold the full sum S (before the -1/2).
+__device__ __forceinline__ void s_hopsum(const Geom &g, const BlkGeom &B, const SapSmem &S, int h, const int l[4],
+                                         const int x[4], int ls, const float4 (*src)[SAPS_NH], cx<float> acc[12])
+{
+#pragma unroll
+    for (int i = 0; i < 12; i++) acc[i] = mk(0.f, 0.f);
+    cx<float> u[3][3], v[12];
+#pragma unroll
+    for (int mu = 0; mu < 4; mu++) {
+        if (h == 0) {
+            int ln = blk_nbr_lex(B, l, mu, +1);
+            if (ln >= 0) {
+                float sg = (mu == 0 && x[0] == g.L[0] - 1) ? float(g.bc_t) : 1.f;
+                s_link(S, mu, ls, u);
+                s_spinor(src, ln >> 1, v);
+                proj_apply<float>(mu, -1, v, u, false, sg, acc);
+            }
+        } else {
+            int ln = blk_nbr_lex(B, l, mu, -1);
+            if (ln >= 0) {
+                float sg = (mu == 0 && x[0] == 0) ? float(g.bc_t) : 1.f;
+                s_link(S, mu, ln, u);
+                s_spinor(src, ln >> 1, v);
+                proj_apply<float>(mu, +1, v, u, true, sg, acc);
+            }
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 12; i++) {
+        acc[i].re += __shfl_xor_sync(0xffffffffu, acc[i].re, 1);
+        acc[i].im += __shfl_xor_sync(0xffffffffu, acc[i].im, 1);
+    }
+}
+
+// the chirality half h of a 12-component spinor (predicated select, no local memory)
+__device__ __forceinline__ void s_half(const cx<float> acc[12], int h, cx<float> out[6])
+{
+#pragma unroll
+    for (int i = 0; i < 6; i++) out[i] = h ? acc[6 + i] : acc[i];
+}
+
+__global__ void __launch_bounds__(2 * SAPS_NH, 1) k_sap_block_s(SapArgs<float> a)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    SapSmem &S = *reinterpret_cast<SapSmem *>(smem_raw);
+    const BlkGeom &B = a.B;
+    const int nh = B.nh;
+    const long Vh = a.g.Vh;
+    const long half = 6 * Vh;
+    const long foff = blockIdx.y * a.fstride;
+    float4 *r_e = a.r + foff, *r_o = a.r + foff + half;
+    float4 *psi_e = a.psi + foff, *psi_o = a.psi + foff + half;
+    float4 *d_e = a.delta + foff, *d_o = a.delta + foff + half;
+    int org[4];
+    {
+        int t = a.blocks[blockIdx.x];
+        int c3 = t % B.nb[3];
+        t /= B.nb[3];
+        int c2 = t % B.nb[2];
+        t /= B.nb[2];
+        int c1 = t % B.nb[1];
+        int c0 = t / B.nb[1];
+        org[0] = c0 * B.bs[0];
+        org[1] = c1 * B.bs[1];
+        org[2] = c2 * B.bs[2];
+        org[3] = c3 * B.bs[3];
+    }
+    const int tid = threadIdx.x;
+    // ---- stage links, clover and r_o (one thread per block site, both parities)
+    for (int i = tid; i < 2 * nh; i += blockDim.x) {
+        const int par = i >= nh, t = par ? i - nh : i;
+        SiteInfo s;
+        block_site(a.g, B, org, par, t, s);
+        const int ls = blk_lex(B, s.l);
+#pragma unroll
+        for (int mu = 0; mu < 4; mu++)
+#pragma unroll
+            for (int q = 0; q < 3; q++) S.U[mu][q][ls] = __ldg(a.U + ((long)(par * 4 + mu) * 3 + q) * Vh + s.grank);
+        const float4 *A = par ? a.Aio : a.Ae;
+#pragma unroll
+        for (int q = 0; q < 18; q++) S.A[q][ls] = __ldg(A + q * Vh + s.grank);
+        if (par) {
+#pragma unroll
+            for (int q = 0; q < 6; q++) S.ro[q][t] = r_o[q * Vh + s.grank];
+        } else {
+#pragma unroll
+            for (int q = 0; q < 6; q++) {
+                S.rho[q][t] = r_e[q * Vh + s.grank];
+                S.chi[q][t] = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+        }
+    }
+    __syncthreads();
+    const int h = tid & 1, t = tid >> 1;   // chirality half / hop direction, site rank
+    const bool act = t < nh;
+    SiteInfo so, se;
+    int lso = 0, lse = 0;
+    if (act) {
+        block_site(a.g, B, org, 1, t, so);
+        block_site(a.g, B, org, 0, t, se);
+        lso = blk_lex(B, so.l);
+        lse = blk_lex(B, se.l);
+    }
+    cx<float> acc[12], v[6], w[6];
+    // to = A_oo^-1 r_o (chirality half h)
+    if (act) {
+#pragma unroll
+        for (int q = 0; q < 3; q++) {
+            float4 x = S.ro[3 * h + q][t];
+            v[2 * q] = mk(x.x, x.y);
+            v[2 * q + 1] = mk(x.z, x.w);
+        }
+        s_clover_half(S, lso, h, v, w);
+#pragma unroll
+        for (int q = 0; q < 3; q++) S.to[3 * h + q][t] = make_float4(w[2 * q].re, w[2 * q].im, w[2 * q + 1].re, w[2 * q + 1].im);
+    }
+    __syncthreads();
+    // rho = r_e - H_eo to = r_e + 1/2 S
+    if (act) {
+        s_hopsum(a.g, B, S, h, se.l, se.x, lse, S.to, acc);
+        cx<float> ah[6];
+        s_half(acc, h, ah);
+#pragma unroll
+        for (int q = 0; q < 3; q++) {
+            float4 x = S.rho[3 * h + q][t];
+            const cx<float> s0 = ah[2 * q], s1 = ah[2 * q + 1];
+            S.rho[3 * h + q][t] = make_float4(x.x + 0.5f * s0.re, x.y + 0.5f * s0.im, x.z + 0.5f * s1.re, x.w + 0.5f * s1.im);
+        }
+    }
+    __syncthreads();
+    for (int it = 0; it < a.nmr; it++) {
+        // to = A_oo^-1 (-1/2 S(rho))
+        if (act) {
+            s_hopsum(a.g, B, S, h, so.l, so.x, lso, S.rho, acc);
+            s_half(acc, h, v);
+#pragma unroll
+            for (int i = 0; i < 6; i++) v[i] = -0.5f * v[i];
+            s_clover_half(S, lso, h, v, w);
+#pragma unroll
+            for (int q = 0; q < 3; q++) S.to[3 * h + q][t] = make_float4(w[2 * q].re, w[2 * q].im, w[2 * q + 1].re, w[2 * q + 1].im);
+        }
+        __syncthreads();
+        // p = A_ee rho + 1/2 S(to); partial <p,p>, <p,rho>
+        float pp = 0.f, pr = 0.f, pi = 0.f;
+        if (act) {
+            s_hopsum(a.g, B, S, h, se.l, se.x, lse, S.to, acc);
+            cx<float> x[6];
+#pragma unroll
+            for (int q = 0; q < 3; q++) {
+                float4 y = S.rho[3 * h + q][t];
+                x[2 * q] = mk(y.x, y.y);
+                x[2 * q + 1] = mk(y.z, y.w);
+            }
+            s_clover_half(S, lse, h, x, w);
+            cx<float> ah[6];
+            s_half(acc, h, ah);
+#pragma unroll
+            for (int i = 0; i < 6; i++) {
+                w[i] = w[i] + 0.5f * ah[i];
+                pp += w[i].re * w[i].re + w[i].im * w[i].im;
+                pr += w[i].re * x[i].re + w[i].im * x[i].im;
+                pi += w[i].re * x[i].im - w[i].im * x[i].re;
+            }
+#pragma unroll
+            for (int q = 0; q < 3; q++) S.p[3 * h + q][t] = make_float4(w[2 * q].re, w[2 * q].im, w[2 * q + 1].re, w[2 * q + 1].im);
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            pp += __shfl_down_sync(0xffffffffu, pp, o);
+            pr += __shfl_down_sync(0xffffffffu, pr, o);
+            pi += __shfl_down_sync(0xffffffffu, pi, o);
+        }
+        if ((tid & 31) == 0) {
+            S.red[0][tid >> 5] = pp;
+            S.red[1][tid >> 5] = pr;
+            S.red[2][tid >> 5] = pi;
+        }
+        __syncthreads();
+        pp = pr = pi = 0.f;
+        for (int wv = 0; wv < (int)(blockDim.x >> 5); wv++) {
+            pp += S.red[0][wv];
+            pr += S.red[1][wv];
+            pi += S.red[2][wv];
+        }
+        __syncthreads();
+        if (pp == 0.f) break;   // rho = 0: the block is solved
+        const float ar = pr / pp, ai = pi / pp;
+        if (act) {
+#pragma unroll
+            for (int q = 0; q < 3; q++) {
+                float4 rv = S.rho[3 * h + q][t], pv = S.p[3 * h + q][t], cv = S.chi[3 * h + q][t];
+                // chi += alpha rho, rho -= alpha p
+                cv.x += ar * rv.x - ai * rv.y;
+                cv.y += ar * rv.y + ai * rv.x;
+                cv.z += ar * rv.z - ai * rv.w;
+                cv.w += ar * rv.w + ai * rv.z;
+                rv.x -= ar * pv.x - ai * pv.y;
+                rv.y -= ar * pv.y + ai * pv.x;
+                rv.z -= ar * pv.z - ai * pv.w;
+                rv.w -= ar * pv.w + ai * pv.z;
+                S.chi[3 * h + q][t] = cv;
+                S.rho[3 * h + q][t] = rv;
+            }
+        }
+        __syncthreads();
+    }
+    // chi_o = A_oo^-1 (r_o + 1/2 S(chi_e)); psi += chi; delta = chi; r <- (rho, 0)
+    if (act) {
+        s_hopsum(a.g, B, S, h, so.l, so.x, lso, S.chi, acc);
+        cx<float> ah[6];
+        s_half(acc, h, ah);
+#pragma unroll
+        for (int q = 0; q < 3; q++) {
+            float4 x = S.ro[3 * h + q][t];
+            v[2 * q] = mk(x.x + 0.5f * ah[2 * q].re, x.y + 0.5f * ah[2 * q].im);
+            v[2 * q + 1] = mk(x.z + 0.5f * ah[2 * q + 1].re, x.w + 0.5f * ah[2 * q + 1].im);
+        }
+        s_clover_half(S, lso, h, v, w);
+#pragma unroll
+        for (int q = 0; q < 3; q++) {
+            const int c = 3 * h + q;
+            float4 co = make_float4(w[2 * q].re, w[2 * q].im, w[2 * q + 1].re, w[2 * q + 1].im);
+            float4 po = psi_o[c * Vh + so.grank];
+            psi_o[c * Vh + so.grank] = make_float4(po.x + co.x, po.y + co.y, po.z + co.z, po.w + co.w);
+            d_o[c * Vh + so.grank] = co;
+            r_o[c * Vh + so.grank] = make_float4(0.f, 0.f, 0.f, 0.f);
+            float4 ce = S.chi[c][t];
+            float4 pe = psi_e[c * Vh + se.grank];
+            psi_e[c * Vh + se.grank] = make_float4(pe.x + ce.x, pe.y + ce.y, pe.z + ce.z, pe.w + ce.w);
+            d_e[c * Vh + se.grank] = ce;
+            r_e[c * Vh + se.grank] = S.rho[c][t];
+        }
+    }
+}
+
+// r(x) -= sum of the hops into x from neighbours y that lie in another block
+// of colour col (delta holds chi there).  One thread per (site, rhs).
+template <class R>
+__global__ void __launch_bounds__(128) k_sap_face(SapArgs<R> a, int col)
+{
+    using SP = typename SapPT<R>::SP;
+    const BlkGeom &B = a.B;
+    long i = blockIdx.x * (long)blockDim.x + threadIdx.x;   // 0 .. V-1: parity-major
+    if (i >= 2L * a.g.Vh) return;
+    const long Vh = a.g.Vh;
+    const int par = i >= Vh;
+    const long rk = par ? i - Vh : i;
+    const long half = (sizeof(R) == 8 ? 12 : 6) * Vh;
+    const long foff = blockIdx.y * a.fstride;
+    int x[4];
+    rank_coords(a.g, par, (int)rk, x);
+    int bx[4];
+    for (int m = 0; m < 4; m++) bx[m] = x[m] / B.bs[m];
+    cx<R> acc[12], u[3][3], v[12];
+    bool any = false;
+#pragma unroll
+    for (int c = 0; c < 12; c++) acc[c] = mk(R(0), R(0));
+    const SP *din = a.delta + foff + (1 - par) * half;
+    for (int mu = 0; mu < 4; mu++)
+        for (int d = -1; d <= 1; d += 2) {
+            int y[4] = {x[0], x[1], x[2], x[3]};
+            int vv = y[mu] + d;
+            y[mu] = vv < 0 ? vv + a.g.L[mu] : (vv >= a.g.L[mu] ? vv - a.g.L[mu] : vv);
+            int by = y[mu] / B.bs[mu];
+            if (by == bx[mu]) continue;   // same block (also covers a block spanning the direction)
+            int csum = by - bx[mu];
+            for (int m = 0; m < 4; m++) csum += bx[m];
+            if ((csum & 1) != col) continue;
+            long ry = coords_rank(a.g, y);
+            gload(din, Vh, ry, v);
+            if (d > 0) {
+                R sg = (mu == 0 && x[0] == a.g.L[0] - 1) ? R(a.g.bc_t) : R(1);
+                glink(a.U, Vh, par, mu, rk, u);
+                proj_apply<R>(mu, -1, v, u, false, sg, acc);
+            } else {
+                R sg = (mu == 0 && x[0] == 0) ? R(a.g.bc_t) : R(1);
+                glink(a.U, Vh, 1 - par, mu, ry, u);
+                proj_apply<R>(mu, +1, v, u, true, sg, acc);
+            }
+            any = true;
+        }
+    if (!any) return;
+    // r -= H delta = r + 1/2 S
+#pragma unroll
+    for (int c = 0; c < 12; c++) acc[c] = R(0.5) * acc[c];
+    gadd(a.r + foff + par * half, Vh, rk, acc);
+}
+
+// LQCD_SAP_GENERIC=1 selects the generic (L1-cached) FP32 block kernel
+bool sap_force_generic()
+{
+    const char *e = getenv("LQCD_SAP_GENERIC");
+    return e && e[0] == '1';
 }
 
 struct SapPlan {
@@ -498,7 +907,8 @@ lqcd_status get_plan(lqcd_ctx *c, const int bs[4], SapPlan **out)
 }
 
 template <class R>
-lqcd_status sap_run(lqcd_ctx *c, const SapPlan &P, int ncy, int nmr, const void *eta, void *psi, void *r)
+lqcd_status sap_run(lqcd_ctx *c, const SapPlan &P, int ncy, int nmr, const void *eta, void *psi, void *r,
+                    void *delta, int nrhs)
 {
     using SP = typename SapPT<R>::SP;
     const lqcd_prec prec = sizeof(R) == 8 ? LQCD_F64 : LQCD_F32;
@@ -510,13 +920,16 @@ lqcd_status sap_run(lqcd_ctx *c, const SapPlan &P, int ncy, int nmr, const void 
         attr_set = true;
     }
     if (smem > 200 * 1024) return set_err(c, LQCD_ERR_ARG, "SAP block needs %zu bytes of shared memory", smem);
-    LQCD_CUDA_CHECK(c, cudaMemsetAsync(psi, 0, fb, c->stream));
-    LQCD_CUDA_CHECK(c, cudaMemcpyAsync(r, eta, fb, cudaMemcpyDeviceToDevice, c->stream));
+    if (nrhs < 1 || nrhs > 65535) return set_err(c, LQCD_ERR_ARG, "SAP nrhs=%d", nrhs);
+    LQCD_CUDA_CHECK(c, cudaMemsetAsync(psi, 0, fb * nrhs, c->stream));
+    LQCD_CUDA_CHECK(c, cudaMemcpyAsync(r, eta, fb * nrhs, cudaMemcpyDeviceToDevice, c->stream));
     SapArgs<R> a;
     a.g = c->g;
     a.B = P.B;
-    a.r = (const SP *)r;
+    a.r = (SP *)r;
     a.psi = (SP *)psi;
+    a.delta = (SP *)delta;
+    a.fstride = 2 * (sizeof(R) == 8 ? 12 : 6) * (long)c->g.Vh;
     if (sizeof(R) == 8) {
         a.U = (const typename SapPT<R>::LK *)c->U64;
         a.Ae = (const typename SapPT<R>::CL *)c->A64[0];
@@ -528,18 +941,35 @@ lqcd_status sap_run(lqcd_ctx *c, const SapPlan &P, int ncy, int nmr, const void 
     }
     a.nmr = nmr;
     int threads = std::min(128, P.B.nh);
-    bool first = true;
+    // FP32 with blocks of <= 128 sites per parity (whole warps of site pairs):
+    // the shared-memory resident kernel
+    bool resident = false;
+    if constexpr (sizeof(R) == 4) {
+        static bool attr_s = false;
+        if (!attr_s) {
+            cudaFuncSetAttribute(k_sap_block_s, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(SapSmem));
+            attr_s = true;
+        }
+        resident = P.B.nh <= SAPS_NH && (2 * P.B.nh) % 32 == 0 && !sap_force_generic();
+    }
+    // the residual is not needed after the last sweep
+    int last_col = P.count[1] > 0 ? 1 : 0;
     for (int cyc = 0; cyc < ncy; cyc++)
         for (int col = 0; col < 2; col++) {
             if (P.count[col] == 0) continue;
-            if (!first) {
-                // r = eta - D psi
-                LQCD_TRY(dirac_D(c, prec, psi, r, 1));
-                LQCD_TRY(sap_axpby_native(c, prec, eta, r));
-            }
-            first = false;
             a.blocks = P.blocks_dev + (col == 0 ? 0 : P.count[0]);
-            k_sap_block<R><<<P.count[col], threads, smem, c->stream>>>(a);
+            if constexpr (sizeof(R) == 4) {
+                if (resident)
+                    k_sap_block_s<<<dim3(P.count[col], nrhs), 2 * P.B.nh, sizeof(SapSmem), c->stream>>>(a);
+                else
+                    k_sap_block<R><<<dim3(P.count[col], nrhs), threads, smem, c->stream>>>(a);
+            } else {
+                k_sap_block<R><<<dim3(P.count[col], nrhs), threads, smem, c->stream>>>(a);
+            }
+            c->n_kernel_launches++;
+            LQCD_LAUNCH_CHECK(c);
+            if (cyc == ncy - 1 && col == last_col) continue;
+            k_sap_face<R><<<dim3(div_up(2L * c->g.Vh, 128), nrhs), 128, 0, c->stream>>>(a, col);
             c->n_kernel_launches++;
             LQCD_LAUNCH_CHECK(c);
         }
@@ -583,16 +1013,18 @@ lqcd_status sap_axpby_native(lqcd_ctx *c, lqcd_prec p, const void *eta, void *r)
     return LQCD_OK;
 }
 
-lqcd_status sap_apply(lqcd_ctx *c, const lqcd_sap_params *sp, const void *eta, void *psi)
+lqcd_status sap_apply(lqcd_ctx *c, const lqcd_sap_params *sp, const void *eta, void *psi, int nrhs)
 {
     if (!c->have_clover) return set_err(c, LQCD_ERR_STATE, "clover term not built");
     if (sp->ncy < 1 || sp->nmr < 0) return set_err(c, LQCD_ERR_ARG, "bad SAP cycle counts");
     SapPlan *P;
     LQCD_TRY(get_plan(c, sp->bs, &P));
     void *r;
-    LQCD_TRY(ws_get(c, WS_SAP_R, 2 * native_half_bytes(c, sp->prec), &r));
-    if (sp->prec == LQCD_F64) return sap_run<double>(c, *P, sp->ncy, sp->nmr, eta, psi, r);
-    if (sp->prec == LQCD_F32) return sap_run<float>(c, *P, sp->ncy, sp->nmr, eta, psi, r);
+    const size_t fb = 2 * native_half_bytes(c, sp->prec);
+    LQCD_TRY(ws_get(c, WS_SAP_R, 2 * fb * nrhs, &r));
+    void *delta = (char *)r + fb * nrhs;
+    if (sp->prec == LQCD_F64) return sap_run<double>(c, *P, sp->ncy, sp->nmr, eta, psi, r, delta, nrhs);
+    if (sp->prec == LQCD_F32) return sap_run<float>(c, *P, sp->ncy, sp->nmr, eta, psi, r, delta, nrhs);
     return set_err(c, LQCD_ERR_ARG, "SAP precision %d not supported", (int)sp->prec);
 }
 

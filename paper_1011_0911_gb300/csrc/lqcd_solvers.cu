@@ -114,153 +114,267 @@ lqcd_status cgnr_native(lqcd_ctx *c, const double2 *eta, double2 *x, double tol,
 }
 
 // ---------------------------------------------------------------- GCR
-struct GcrParams {
-    const lqcd_solver_params *sp;
-    double tol;
-};
+// All fields below are native full FP64 fields; nrhs of them are stored one
+// after the other (stride nf double2).  The GCR of every right-hand side runs
+// in lockstep so that the preconditioner, D and the BLAS-1 kernels each cover
+// the whole batch in one launch; every right-hand side keeps its own
+// Gram-Schmidt coefficients, and a converged one receives zero updates.
 
-// phi = M rho (all native full FP64)
-lqcd_status precond(lqcd_ctx *c, const lqcd_solver_params *sp, const double2 *rho, double2 *phi)
+// phi = M rho
+lqcd_status precond(lqcd_ctx *c, const lqcd_solver_params *sp, const double2 *rho, double2 *phi, int nrhs)
 {
     const lqcd_sap_params &sap = sp->sap;
-    if (sp->solver == LQCD_SOLVER_DFL_SAP_GCR) return dfl_precond_native(c, &sap, rho, phi);
-    if (sap.prec == LQCD_F64) return sap_apply(c, &sap, rho, phi);
+    if (sp->solver == LQCD_SOLVER_DFL_SAP_GCR) return dfl_precond_native(c, &sap, rho, phi, nrhs);
+    if (sap.prec == LQCD_F64) return sap_apply(c, &sap, rho, phi, nrhs);
     void *a, *b;
-    size_t fb = 2 * native_half_bytes(c, sap.prec);
+    size_t fb = 2 * native_half_bytes(c, sap.prec) * nrhs;
     LQCD_TRY(ws_get(c, WS_SAP_IN, fb, &a));
     LQCD_TRY(ws_get(c, WS_SAP_PSI, fb, &b));
-    LQCD_TRY(convert_native(c, LQCD_F64, sap.prec, rho, a, 2));
-    LQCD_TRY(sap_apply(c, &sap, a, b));
-    return convert_native(c, sap.prec, LQCD_F64, b, phi, 2);
+    LQCD_TRY(convert_native(c, LQCD_F64, sap.prec, rho, a, 2 * nrhs));
+    LQCD_TRY(sap_apply(c, &sap, a, b, nrhs));
+    return convert_native(c, sap.prec, LQCD_F64, b, phi, 2 * nrhs);
 }
 
 // chi = D phi in the inner precision, result FP64
-lqcd_status apply_D_inner(lqcd_ctx *c, lqcd_prec inner, const double2 *phi, double2 *chi)
+lqcd_status apply_D_inner(lqcd_ctx *c, lqcd_prec inner, const double2 *phi, double2 *chi, int nrhs)
 {
-    if (inner == LQCD_F64) return dirac_D(c, LQCD_F64, phi, chi, 1);
+    if (inner == LQCD_F64) return dirac_D(c, LQCD_F64, phi, chi, nrhs);
     void *a, *b;
-    size_t fb = 2 * native_half_bytes(c, inner);
+    size_t fb = 2 * native_half_bytes(c, inner) * nrhs;
     LQCD_TRY(ws_get(c, WS_MISC, fb, &a));
     LQCD_TRY(ws_get(c, WS_MISC2, fb, &b));
-    LQCD_TRY(convert_native(c, LQCD_F64, inner, phi, a, 2));
-    LQCD_TRY(dirac_D(c, inner, a, b, 1));
-    return convert_native(c, inner, LQCD_F64, b, chi, 2);
+    LQCD_TRY(convert_native(c, LQCD_F64, inner, phi, a, 2 * nrhs));
+    LQCD_TRY(dirac_D(c, inner, a, b, nrhs));
+    return convert_native(c, inner, LQCD_F64, b, chi, 2 * nrhs);
 }
 
-// flexible GCR on D psi = eta, warm start from psi; native full FP64 fields
-lqcd_status gcr_native(lqcd_ctx *c, const lqcd_solver_params *sp, double tol, const double2 *eta, double2 *psi,
-                       int *iters, int *restarts, double *relres, int nmx)
+struct GcrState {
+    std::vector<int> iters, restarts;
+    std::vector<double> relres;
+    std::vector<lqcd_status> status;
+};
+
+// LQCD_PROFILE=1: synchronise around the phases of the GCR and report their
+// wall time on stderr (developer instrumentation; off by default)
+struct PhaseProf {
+    bool on;
+    double t[4] = {0, 0, 0, 0};
+    double t0 = 0;
+    explicit PhaseProf(lqcd_ctx *c) : on(getenv("LQCD_PROFILE") && getenv("LQCD_PROFILE")[0] == '1'), ctx(c) {}
+    lqcd_ctx *ctx;
+    void start()
+    {
+        if (!on) return;
+        cudaStreamSynchronize(ctx->stream);
+        t0 = now_s();
+    }
+    void stop(int i)
+    {
+        if (!on) return;
+        cudaStreamSynchronize(ctx->stream);
+        t[i] += now_s() - t0;
+    }
+    ~PhaseProf()
+    {
+        if (on)
+            fprintf(stderr, "[lqcd gcr] precond %.4f s, D_inner %.4f s, gram-schmidt %.4f s, restart %.4f s\n", t[0],
+                    t[1], t[2], t[3]);
+    }
+};
+
+// per-rhs squared norms of nrhs fields
+lqcd_status bnorm2(lqcd_ctx *c, long n2, int nrhs, const double2 *x, std::vector<double> &out)
+{
+    std::vector<double> d(2 * nrhs);
+    LQCD_TRY(bblas_dot(c, n2, nrhs, (const double *)x, 0, n2, (const double *)x, n2, 1, d.data()));
+    out.resize(nrhs);
+    for (int r = 0; r < nrhs; r++) out[r] = d[2 * r];
+    return LQCD_OK;
+}
+
+// flexible GCR on D psi_r = eta_r, warm start from psi; tol per rhs
+lqcd_status gcr_native(lqcd_ctx *c, const lqcd_solver_params *sp, const std::vector<double> &tol,
+                       const double2 *eta, double2 *psi, int nrhs, int nmx, GcrState &S)
 {
     const long Vh = c->g.Vh;
     const long n2 = 48 * Vh;   // doubles in one full field
     const long nf = 24 * Vh;   // double2 in one full field
     const int nkv = sp->nkv;
     if (nkv < 1 || nkv > 64) return set_err(c, LQCD_ERR_ARG, "nkv=%d", nkv);
+    if (nrhs * nkv > 2048) return set_err(c, LQCD_ERR_ARG, "nrhs*nkv too large");
+    const long bf = nrhs * nf;   // double2 per batch of fields
     void *buf;
-    LQCD_TRY(ws_get(c, WS_SOLVER, (size_t)(2 * nkv + 2) * nf * sizeof(double2), &buf));
-    double2 *phi = (double2 *)buf, *chi = phi + nkv * nf, *rho = chi + nkv * nf, *w = rho + nf;
+    LQCD_TRY(ws_get(c, WS_SOLVER, (size_t)(2 * nkv + 2) * bf * sizeof(double2), &buf));
+    double2 *phi = (double2 *)buf, *chi = phi + nkv * bf, *rho = chi + nkv * bf, *w = rho + bf;
     const double inner_gain = sp->inner == LQCD_F64 ? 0.0 : 1e-5;
-    double eta2;
-    LQCD_TRY(blas_norm2(c, n2, (const double *)eta, &eta2));
-    double eta_n = std::sqrt(eta2);
-    // rho = eta - D psi
-    LQCD_TRY(dirac_D(c, LQCD_F64, psi, w, 1));
-    LQCD_TRY(blas_sub(c, n2, (const double *)eta, (const double *)w, (double *)rho));
-    double rn2;
-    LQCD_TRY(blas_norm2(c, n2, (const double *)rho, &rn2));
-    double res = std::sqrt(rn2);
-    if (!std::isfinite(res)) return set_err(c, LQCD_ERR_NAN, "non-finite residual");
-    int it = 0, rs = 0;
-    std::vector<Cplx> a(nkv * nkv), cc(nkv), alpha(nkv);
-    std::vector<double> b(nkv);
-    std::vector<double> dots(2 * 64), coef(2 * 64);
-    lqcd_status st = LQCD_ERR_NOT_CONVERGED;
-    if (eta_n == 0 || res <= tol * eta_n) st = LQCD_OK;
-    while (st != LQCD_OK && it < nmx) {
+    PhaseProf prof(c);
+    std::vector<double> eta2, rn2, eta_n(nrhs), res(nrhs), cycle_start(nrhs);
+    LQCD_TRY(bnorm2(c, n2, nrhs, eta, eta2));
+    LQCD_TRY(dirac_D(c, LQCD_F64, psi, w, nrhs));
+    LQCD_TRY(blas_sub(c, n2 * nrhs, (const double *)eta, (const double *)w, (double *)rho));
+    LQCD_TRY(bnorm2(c, n2, nrhs, rho, rn2));
+    std::vector<char> active(nrhs);
+    for (int r = 0; r < nrhs; r++) {
+        eta_n[r] = std::sqrt(eta2[r]);
+        res[r] = std::sqrt(rn2[r]);
+        if (!std::isfinite(res[r])) S.status[r] = LQCD_ERR_NAN;
+        else if (eta_n[r] == 0 || res[r] <= tol[r] * eta_n[r]) S.status[r] = LQCD_OK;
+        else S.status[r] = LQCD_ERR_NOT_CONVERGED;
+        active[r] = S.status[r] == LQCD_ERR_NOT_CONVERGED;
+    }
+    // per rhs: a[r][i][k], b[r][k], cc[r][k], alpha[r][k]
+    std::vector<Cplx> a((size_t)nrhs * nkv * nkv), cc((size_t)nrhs * nkv), alpha((size_t)nrhs * nkv);
+    std::vector<double> b((size_t)nrhs * nkv), dots(2 * (size_t)nrhs * 64), coef(2 * (size_t)nrhs * 64);
+    int it = 0;
+    auto any_active = [&]() {
+        for (int r = 0; r < nrhs; r++)
+            if (active[r]) return true;
+        return false;
+    };
+    while (any_active() && it < nmx) {
         int nk = 0;
-        double cycle_start = res;
+        std::vector<char> done(nrhs, 0);
+        for (int r = 0; r < nrhs; r++) cycle_start[r] = res[r];
         for (int k = 0; k < nkv && it < nmx; k++) {
-            double2 *ph = phi + k * nf, *ch = chi + k * nf;
-            LQCD_TRY(precond(c, sp, rho, ph));
-            LQCD_TRY(apply_D_inner(c, sp->inner, ph, ch));
-            for (int i = 0; i < k; i++) a[i * nkv + k] = {0, 0};
+            double2 *ph = phi + k * bf, *ch = chi + k * bf;
+            prof.start();
+            LQCD_TRY(precond(c, sp, rho, ph, nrhs));
+            prof.stop(0);
+            prof.start();
+            LQCD_TRY(apply_D_inner(c, sp->inner, ph, ch, nrhs));
+            prof.stop(1);
+            prof.start();
+            for (int r = 0; r < nrhs; r++)
+                for (int i = 0; i < k; i++) a[((size_t)r * nkv + i) * nkv + k] = {0, 0};
+            // classical Gram-Schmidt; a second pass only where the first removed more
+            // than half of |chi_k|^2 (Daniel-Gragg-Kaufman-Stewart criterion).  The
+            // first pass reduces chi_0..chi_k against chi_k, which also gives |chi_k|^2.
             for (int pass = 0; pass < 2 && k > 0; pass++) {
-                LQCD_TRY(blas_dot(c, n2, (const double *)chi, (const double *)ch, k, n2, dots.data()));
-                for (int i = 0; i < k; i++) {
-                    a[i * nkv + k].re += dots[2 * i];
-                    a[i * nkv + k].im += dots[2 * i + 1];
+                const int kk = pass == 0 ? k + 1 : k;
+                LQCD_TRY(bblas_dot(c, n2, nrhs, (const double *)chi, 2 * bf, n2, (const double *)ch, n2, kk,
+                                   dots.data()));
+                bool again = false;
+                std::vector<double> cf(2 * (size_t)nrhs * k);
+                for (int r = 0; r < nrhs; r++) {
+                    double removed = 0;
+                    for (int i = 0; i < k; i++) {
+                        const double dr = dots[2 * (r * kk + i)], di = dots[2 * (r * kk + i) + 1];
+                        a[((size_t)r * nkv + i) * nkv + k].re += dr;
+                        a[((size_t)r * nkv + i) * nkv + k].im += di;
+                        cf[2 * (r * k + i)] = dr;
+                        cf[2 * (r * k + i) + 1] = di;
+                        removed += dr * dr + di * di;
+                    }
+                    if (pass == 0 && active[r] && removed > 0.5 * dots[2 * (r * kk + k)]) again = true;
                 }
-                LQCD_TRY(blas_multi_axpy(c, n2, k, dots.data(), (const double *)chi, n2, (double *)ch, -1.0));
+                LQCD_TRY(bblas_multi_axpy(c, n2, nrhs, k, cf.data(), (const double *)chi, 2 * bf, n2,
+                                          (double *)ch, n2, -1.0));
+                if (!again) break;
             }
-            double bb;
-            LQCD_TRY(blas_norm2(c, n2, (const double *)ch, &bb));
-            b[k] = std::sqrt(bb);
-            if (!std::isfinite(b[k])) return set_err(c, LQCD_ERR_NAN, "non-finite Krylov vector");
-            if (b[k] == 0) {
-                st = LQCD_ERR_BREAKDOWN;
-                break;
+            // |chi_k|^2 and <rho, chi_k> in one reduction (family {chi_k, rho} against chi_k)
+            LQCD_TRY(bblas_dot(c, n2, nrhs, (const double *)ch, 2 * (rho - ch), n2, (const double *)ch, n2, 2,
+                               dots.data()));
+            std::vector<double> coef2(2 * (size_t)nrhs);
+            for (int r = 0; r < nrhs; r++) {
+                const double bk = std::sqrt(dots[2 * (2 * r)]);
+                b[(size_t)r * nkv + k] = bk;
+                const double s = (bk > 0 && std::isfinite(bk)) ? 1.0 / bk : 0.0;
+                if (active[r] && s == 0.0) {
+                    S.status[r] = std::isfinite(bk) ? LQCD_ERR_BREAKDOWN : LQCD_ERR_NAN;
+                    active[r] = 0;
+                }
+                // c_k = <chi_k / b_k, rho> = conj(<rho, chi_k>) / b_k
+                const double cr = dots[2 * (2 * r + 1)] * s, ci = -dots[2 * (2 * r + 1) + 1] * s;
+                cc[(size_t)r * nkv + k] = {cr, ci};
+                // rho -= c_k chi_k / b_k (chi_k not yet normalised); chi_k *= 1/b_k
+                coef[2 * r] = active[r] ? cr * s : 0.0;
+                coef[2 * r + 1] = active[r] ? ci * s : 0.0;
+                coef2[2 * r] = s - 1.0;
+                coef2[2 * r + 1] = 0.0;
+                if (active[r]) rn2[r] = std::max(0.0, rn2[r] - (cr * cr + ci * ci));
             }
-            LQCD_TRY(blas_scal(c, n2, 1.0 / b[k], 0, (double *)ch));
-            LQCD_TRY(blas_dot(c, n2, (const double *)ch, (const double *)rho, 1, 0, dots.data()));
-            cc[k] = {dots[0], dots[1]};
-            LQCD_TRY(blas_axpy(c, n2, -cc[k].re, -cc[k].im, (const double *)ch, (double *)rho));
+            LQCD_TRY(bblas_multi_axpy(c, n2, nrhs, 1, coef.data(), (const double *)ch, 0, n2, (double *)rho, n2, -1.0));
+            LQCD_TRY(bblas_multi_axpy(c, n2, nrhs, 1, coef2.data(), (const double *)ch, 0, n2, (double *)ch, n2, 1.0));
             it++;
             nk = k + 1;
-            double r2;
-            LQCD_TRY(blas_norm2(c, n2, (const double *)rho, &r2));
-            double rr = std::sqrt(r2);
-            if (rr <= tol * eta_n || rr <= inner_gain * cycle_start) break;
-        }
-        if (st == LQCD_ERR_BREAKDOWN && nk == 0) break;
-        for (int j = nk - 1; j >= 0; j--) {
-            Cplx s = cc[j];
-            for (int i = j + 1; i < nk; i++) {
-                Cplx t = cmul(a[j * nkv + i], alpha[i]);
-                s.re -= t.re;
-                s.im -= t.im;
+            bool recompute = false;
+            for (int r = 0; r < nrhs; r++) {
+                if (active[r]) S.iters[r]++;
+                // |rho|^2 - |c|^2 loses digits once |rho| has dropped ~1e7 within the cycle
+                if (active[r] && rn2[r] < 1e-14 * cycle_start[r] * cycle_start[r]) recompute = true;
             }
-            alpha[j] = cdiv(s, b[j]);
+            if (recompute) LQCD_TRY(bnorm2(c, n2, nrhs, rho, rn2));
+            prof.stop(2);
+            bool all_done = true;
+            for (int r = 0; r < nrhs; r++) {
+                double rr = std::sqrt(rn2[r]);
+                if (!active[r] || rr <= tol[r] * eta_n[r] || rr <= inner_gain * cycle_start[r]) done[r] = 1;
+                all_done = all_done && done[r];
+            }
+            if (all_done) break;
         }
-        for (int j = 0; j < nk; j++) {
-            coef[2 * j] = alpha[j].re;
-            coef[2 * j + 1] = alpha[j].im;
+        // back substitution per rhs: alpha_j = (c_j - sum_{i>j} a_ji alpha_i) / b_j
+        for (int r = 0; r < nrhs; r++) {
+            for (int j = nk - 1; j >= 0; j--) {
+                Cplx s = cc[(size_t)r * nkv + j];
+                for (int i = j + 1; i < nk; i++) {
+                    Cplx t = cmul(a[((size_t)r * nkv + j) * nkv + i], alpha[(size_t)r * nkv + i]);
+                    s.re -= t.re;
+                    s.im -= t.im;
+                }
+                double bj = b[(size_t)r * nkv + j];
+                alpha[(size_t)r * nkv + j] = (active[r] && bj > 0) ? cdiv(s, bj) : Cplx{0, 0};
+            }
+            for (int j = 0; j < nk; j++) {
+                coef[2 * (r * nk + j)] = alpha[(size_t)r * nkv + j].re;
+                coef[2 * (r * nk + j) + 1] = alpha[(size_t)r * nkv + j].im;
+            }
         }
-        LQCD_TRY(blas_multi_axpy(c, n2, nk, coef.data(), (const double *)phi, n2, (double *)psi, 1.0));
+        prof.start();
+        if (nk > 0)
+            LQCD_TRY(bblas_multi_axpy(c, n2, nrhs, nk, coef.data(), (const double *)phi, 2 * bf, n2, (double *)psi, n2,
+                                      1.0));
         // restart from the FP64 true residual
-        LQCD_TRY(dirac_D(c, LQCD_F64, psi, w, 1));
-        LQCD_TRY(blas_sub(c, n2, (const double *)eta, (const double *)w, (double *)rho));
-        LQCD_TRY(blas_norm2(c, n2, (const double *)rho, &rn2));
-        res = std::sqrt(rn2);
-        rs++;
-        if (!std::isfinite(res)) {
-            st = LQCD_ERR_NAN;
-            break;
+        LQCD_TRY(dirac_D(c, LQCD_F64, psi, w, nrhs));
+        LQCD_TRY(blas_sub(c, n2 * nrhs, (const double *)eta, (const double *)w, (double *)rho));
+        LQCD_TRY(bnorm2(c, n2, nrhs, rho, rn2));
+        prof.stop(3);
+        for (int r = 0; r < nrhs; r++) {
+            if (!active[r]) continue;
+            res[r] = std::sqrt(rn2[r]);
+            S.restarts[r]++;
+            if (!std::isfinite(res[r])) {
+                S.status[r] = LQCD_ERR_NAN;
+                active[r] = 0;
+            } else if (res[r] <= tol[r] * eta_n[r]) {
+                S.status[r] = LQCD_OK;
+                active[r] = 0;
+            }
         }
-        if (res <= tol * eta_n) st = LQCD_OK;
-        else if (st == LQCD_ERR_BREAKDOWN)
-            break;
     }
-    if (iters) *iters += it;
-    if (restarts) *restarts += rs;
-    if (relres) *relres = eta_n > 0 ? res / eta_n : 0;
-    return st;
+    for (int r = 0; r < nrhs; r++) S.relres[r] = eta_n[r] > 0 ? res[r] / eta_n[r] : 0;
+    return LQCD_OK;
 }
 
-// even-odd helpers on native fields: even half of a full field is its first half
-lqcd_status dhat_relres(lqcd_ctx *c, const double2 *eta_e, const double2 *psi_e, double *out)
+// |eta_e - Dhat psi_e| / |eta_e| per rhs; eta, psi: nrhs native full fields (even halves used)
+lqcd_status dhat_relres(lqcd_ctx *c, const double2 *eta, const double2 *psi, int nrhs, std::vector<double> &out)
 {
     const long Vh = c->g.Vh;
-    const long n2 = 24 * Vh;
+    const long n2 = 24 * Vh;   // doubles in one even field
+    const long nf = 24 * Vh;   // double2 per full field
     void *b, *tmp_o;
     LQCD_TRY(ws_get(c, WS_MISC, 2 * native_half_bytes(c, LQCD_F64), &b));
     LQCD_TRY(ws_get(c, WS_TMP_O, native_half_bytes(c, LQCD_F64), &tmp_o));
-    double2 *w = (double2 *)b, *r = w + 12 * Vh;
-    LQCD_TRY(dirac_dhat(c, LQCD_F64, psi_e, w, tmp_o, 1));
-    LQCD_TRY(blas_sub(c, n2, (const double *)eta_e, (const double *)w, (double *)r));
-    double rr, ee;
-    LQCD_TRY(blas_norm2(c, n2, (const double *)r, &rr));
-    LQCD_TRY(blas_norm2(c, n2, (const double *)eta_e, &ee));
-    *out = ee > 0 ? std::sqrt(rr / ee) : 0;
+    double2 *w = (double2 *)b, *rr = w + 12 * Vh;
+    out.resize(nrhs);
+    for (int r = 0; r < nrhs; r++) {
+        LQCD_TRY(dirac_dhat(c, LQCD_F64, psi + r * nf, w, tmp_o, 1));
+        LQCD_TRY(blas_sub(c, n2, (const double *)(eta + r * nf), (const double *)w, (double *)rr));
+        double x, e;
+        LQCD_TRY(blas_norm2(c, n2, (const double *)rr, &x));
+        LQCD_TRY(blas_norm2(c, n2, (const double *)(eta + r * nf), &e));
+        out[r] = e > 0 ? std::sqrt(x / e) : 0;
+    }
     return LQCD_OK;
 }
 
@@ -288,45 +402,65 @@ lqcd_status lqcd_solve_dhat(lqcd_ctx *c, const lqcd_solver_params *p, const doub
     if (!c || !eta || !psi) return set_err(c, LQCD_ERR_ARG, "null argument");
     LQCD_TRY(check_params(c, p, nrhs));
     const long Vh = c->g.Vh;
+    const long nf = 24 * Vh;
     const size_t hb = native_half_bytes(c, LQCD_F64);
     lqcd_status all = LQCD_OK;
-    for (int k = 0; k < nrhs; k++) {
-        const double *eta_k = eta + (size_t)k * 24 * Vh;
-        double *psi_k = psi + (size_t)k * 24 * Vh;
-        lqcd_solve_info li{};
-        double t0 = now_s();
-        void *io;
-        LQCD_TRY(ws_get(c, WS_SOLVE_IO, 4 * hb, &io));
-        double2 *eta_f = (double2 *)io, *psi_f = eta_f + 24 * Vh;   // full native fields
-        LQCD_TRY(blas_zero(c, 4 * hb, io));
-        LQCD_TRY(pack_field(c, LQCD_F64, 1, eta_k, eta_f, 1, false));   // even half, odd = 0
-        lqcd_status st;
-        if (p->solver == LQCD_SOLVER_CGNR) {
-            st = cgnr_native(c, eta_f, psi_f, p->tol, p->nmx, &li);
-        } else {
-            double tol = p->tol;
-            int iters = 0, restarts = 0;
-            double rel = 0, rh = 0;
-            st = LQCD_OK;
-            for (int attempt = 0; attempt < 4; attempt++) {
-                st = gcr_native(c, p, tol, eta_f, psi_f, &iters, &restarts, &rel, p->nmx - iters);
-                if (st != LQCD_OK) break;
-                LQCD_TRY(dhat_relres(c, eta_f, psi_f, &rh));
-                if (rh <= p->tol) break;
-                // the Dhat residual r_e - H_eo A_oo^-1 r_o is not bounded by |r|: tighten
-                tol = tol * std::max(0.05, 0.5 * p->tol / rh);
-            }
-            if (st == LQCD_OK && rh > p->tol) st = LQCD_ERR_NOT_CONVERGED;
-            li.iters = iters;
-            li.restarts = restarts;
-            li.true_relres = rel;
-            li.relres_dhat = rh;
-            li.status = st;
-            li.seconds = now_s() - t0;
+    double t0 = now_s();
+    if (p->solver == LQCD_SOLVER_CGNR) {
+        for (int k = 0; k < nrhs; k++) {
+            lqcd_solve_info li{};
+            void *io;
+            LQCD_TRY(ws_get(c, WS_SOLVE_IO, 4 * hb, &io));
+            double2 *eta_f = (double2 *)io, *psi_f = eta_f + nf;
+            LQCD_TRY(blas_zero(c, 4 * hb, io));
+            LQCD_TRY(pack_field(c, LQCD_F64, 1, eta + (size_t)k * 24 * Vh, eta_f, 1, false));
+            lqcd_status st = cgnr_native(c, eta_f, psi_f, p->tol, p->nmx, &li);
+            LQCD_TRY(pack_field(c, LQCD_F64, 1, psi + (size_t)k * 24 * Vh, psi_f, 1, true));
+            if (info) info[k] = li;
+            all = worst(all, st);
         }
-        LQCD_TRY(pack_field(c, LQCD_F64, 1, psi_k, psi_f, 1, true));
-        if (info) info[k] = li;
-        all = worst(all, st);
+    } else {
+        // full fields (eta_e, 0) for every rhs, solved together
+        void *io;
+        LQCD_TRY(ws_get(c, WS_SOLVE_IO, 4 * hb * nrhs, &io));
+        double2 *eta_f = (double2 *)io, *psi_f = eta_f + nrhs * nf;
+        LQCD_TRY(blas_zero(c, 4 * hb * nrhs, io));
+        for (int k = 0; k < nrhs; k++)
+            LQCD_TRY(pack_field(c, LQCD_F64, 1, eta + (size_t)k * 24 * Vh, eta_f + k * nf, 1, false));
+        GcrState S;
+        S.iters.assign(nrhs, 0);
+        S.restarts.assign(nrhs, 0);
+        S.relres.assign(nrhs, 0);
+        S.status.assign(nrhs, LQCD_ERR_NOT_CONVERGED);
+        std::vector<double> tol(nrhs, p->tol), rh(nrhs, 0);
+        for (int attempt = 0; attempt < 4; attempt++) {
+            int used = 0;
+            for (int k = 0; k < nrhs; k++) used = std::max(used, S.iters[k]);
+            LQCD_TRY(gcr_native(c, p, tol, eta_f, psi_f, nrhs, p->nmx - used, S));
+            LQCD_TRY(dhat_relres(c, eta_f, psi_f, nrhs, rh));
+            bool again = false;
+            for (int k = 0; k < nrhs; k++)
+                if (S.status[k] == LQCD_OK && rh[k] > p->tol) {
+                    // the Dhat residual r_e - H_eo A_oo^-1 r_o is not bounded by |r|: tighten
+                    tol[k] = tol[k] * std::max(0.05, 0.5 * p->tol / rh[k]);
+                    S.status[k] = LQCD_ERR_NOT_CONVERGED;
+                    again = true;
+                }
+            if (!again) break;
+        }
+        for (int k = 0; k < nrhs; k++) {
+            if (S.status[k] == LQCD_OK && rh[k] > p->tol) S.status[k] = LQCD_ERR_NOT_CONVERGED;
+            LQCD_TRY(pack_field(c, LQCD_F64, 1, psi + (size_t)k * 24 * Vh, psi_f + k * nf, 1, true));
+            if (info) {
+                info[k].iters = S.iters[k];
+                info[k].restarts = S.restarts[k];
+                info[k].true_relres = S.relres[k];
+                info[k].relres_dhat = rh[k];
+                info[k].status = S.status[k];
+                info[k].seconds = now_s() - t0;
+            }
+            all = worst(all, S.status[k]);
+        }
     }
     if (all != LQCD_OK && all != LQCD_ERR_CUDA) set_err(c, all, "solve did not converge (status %d)", (int)all);
     return all;
@@ -339,28 +473,33 @@ lqcd_status lqcd_solve_D(lqcd_ctx *c, const lqcd_solver_params *p, const double 
     LQCD_TRY(check_params(c, p, nrhs));
     if (p->solver == LQCD_SOLVER_CGNR) return set_err(c, LQCD_ERR_ARG, "CGNR solves Dhat only");
     const long Vh = c->g.Vh;
+    const long nf = 24 * Vh;
     const size_t hb = native_half_bytes(c, LQCD_F64);
+    double t0 = now_s();
+    void *io;
+    LQCD_TRY(ws_get(c, WS_SOLVE_IO, 4 * hb * nrhs, &io));
+    double2 *eta_f = (double2 *)io, *psi_f = eta_f + nrhs * nf;
+    LQCD_TRY(pack_field(c, LQCD_F64, 2, eta, eta_f, nrhs, false));
+    LQCD_TRY(blas_zero(c, 2 * hb * nrhs, psi_f));
+    GcrState S;
+    S.iters.assign(nrhs, 0);
+    S.restarts.assign(nrhs, 0);
+    S.relres.assign(nrhs, 0);
+    S.status.assign(nrhs, LQCD_ERR_NOT_CONVERGED);
+    std::vector<double> tol(nrhs, p->tol);
+    LQCD_TRY(gcr_native(c, p, tol, eta_f, psi_f, nrhs, p->nmx, S));
+    LQCD_TRY(pack_field(c, LQCD_F64, 2, psi, psi_f, nrhs, true));
     lqcd_status all = LQCD_OK;
     for (int k = 0; k < nrhs; k++) {
-        void *io;
-        LQCD_TRY(ws_get(c, WS_SOLVE_IO, 4 * hb, &io));
-        double2 *eta_f = (double2 *)io, *psi_f = eta_f + 24 * Vh;
-        double t0 = now_s();
-        LQCD_TRY(pack_field(c, LQCD_F64, 2, eta + (size_t)k * 48 * Vh, eta_f, 1, false));
-        LQCD_TRY(blas_zero(c, 2 * hb, psi_f));
-        lqcd_solve_info li{};
-        int iters = 0, restarts = 0;
-        double rel = 0;
-        lqcd_status st = gcr_native(c, p, p->tol, eta_f, psi_f, &iters, &restarts, &rel, p->nmx);
-        LQCD_TRY(pack_field(c, LQCD_F64, 2, psi + (size_t)k * 48 * Vh, psi_f, 1, true));
-        li.iters = iters;
-        li.restarts = restarts;
-        li.true_relres = rel;
-        li.relres_dhat = -1;
-        li.status = st;
-        li.seconds = now_s() - t0;
-        if (info) info[k] = li;
-        all = worst(all, st);
+        if (info) {
+            info[k].iters = S.iters[k];
+            info[k].restarts = S.restarts[k];
+            info[k].true_relres = S.relres[k];
+            info[k].relres_dhat = -1;
+            info[k].status = S.status[k];
+            info[k].seconds = now_s() - t0;
+        }
+        all = worst(all, S.status[k]);
     }
     return all;
 }

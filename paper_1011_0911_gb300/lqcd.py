@@ -42,7 +42,8 @@ class SapParams(C.Structure):
 
 class DflParams(C.Structure):
     _fields_ = [("bs", C.c_int * 4), ("Ns", C.c_int), ("ninv", C.c_int), ("ncy", C.c_int), ("nmr", C.c_int),
-                ("prec", C.c_int), ("coarse_tol", C.c_double), ("coarse_nkv", C.c_int), ("coarse_nmx", C.c_int)]
+                ("prec", C.c_int), ("coarse_tol", C.c_double), ("coarse_nkv", C.c_int), ("coarse_nmx", C.c_int),
+                ("coarse_prec", C.c_int)]
 
 
 class SolverParams(C.Structure):
@@ -108,6 +109,8 @@ def lib():
         L.lqcd_native_bytes.restype = S
         L.lqcd_kernel_launches.argtypes = [P]
         L.lqcd_kernel_launches.restype = C.c_long
+        L.lqcd_dfl_stats.argtypes = [P, C.POINTER(C.c_long), C.POINTER(C.c_long)]
+        L.lqcd_dfl_stats.restype = C.c_int
         _lib = L
     return _lib
 
@@ -237,7 +240,7 @@ class Context:
 
     # ------------------------------------------------------------ deflation
     def dfl_build(self, v0: torch.Tensor, bs=(4, 4, 4, 4), ninv=4, ncy=4, nmr=4, prec=F32, coarse_tol=1e-8,
-                  coarse_nkv=16, coarse_nmx=4096):
+                  coarse_nkv=16, coarse_nmx=4096, coarse_prec=F64):
         v0 = v0.to(torch.complex128).contiguous()
         Ns = v0.numel() // (12 * self.V)
         self.Ns = Ns
@@ -245,7 +248,7 @@ class Context:
         for L, b in zip(self.dims, bs):
             nb *= L // b
         self.nblk = nb
-        p = DflParams((C.c_int * 4)(*bs), Ns, ninv, ncy, nmr, prec, coarse_tol, coarse_nkv, coarse_nmx)
+        p = DflParams((C.c_int * 4)(*bs), Ns, ninv, ncy, nmr, prec, coarse_tol, coarse_nkv, coarse_nmx, coarse_prec)
         self._check(lib().lqcd_dfl_build(self._h, C.byref(p), _ptr(v0)), "lqcd_dfl_build")
 
     def dfl_export(self):
@@ -253,6 +256,12 @@ class Context:
         A = torch.empty((self.nblk, 9, self.Ns, self.Ns), dtype=torch.complex128, device="cuda")
         self._check(lib().lqcd_dfl_export(self._h, _ptr(phi), _ptr(A)), "lqcd_dfl_export")
         return phi, A
+
+    def dfl_stats(self):
+        """(coarse solves, coarse GCR iterations) since the subspace was built."""
+        s, i = C.c_long(), C.c_long()
+        self._check(lib().lqcd_dfl_stats(self._h, C.byref(s), C.byref(i)), "lqcd_dfl_stats")
+        return s.value, i.value
 
     def dfl_project(self, x):
         x = x.to(torch.complex128).contiguous()

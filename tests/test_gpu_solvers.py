@@ -32,14 +32,17 @@ def test_cgnr_8x4(p8):
 @pytest.mark.parametrize("dims,bs", [((8, 8, 8, 8), (4, 4, 4, 4)), ((8, 4, 4, 8), (4, 4, 4, 4)),
                                      ((12, 8, 4, 4), (4, 4, 4, 4)), ((4, 4, 4, 4), (4, 4, 4, 4))],
                          ids=["8x8x8x8", "8x4x4x8", "12x8x4x4-odd-blocks", "one-block"])
-def test_sap_parity(dims, bs, prec, tol):
+def test_sap_parity(dims, bs, prec, tol, monkeypatch):
     """M_sap eta on the GPU equals the oracle's SAP (same procedure, same data).
-    12x8x4x4 has 3 blocks along time: same-colour blocks touch across the wrap."""
+    12x8x4x4 has 3 blocks along time: same-colour blocks touch across the wrap.
+    FP32 runs both block kernels (shared-memory resident and L1-cached)."""
     P = Pair(dims, kappa=0.1355)
     eta = synth.gaussian_spinor(P.V, 2)
-    out = P.ctx.sap(to_gpu(eta), bs=bs, ncy=4, nmr=5, prec=prec)
     ref = P.o.sap(eta, bs=bs, ncy=4, nmr=5)
-    assert relerr(out, ref) < tol
+    for generic in (("0", "1") if prec == lqcd.F32 else ("0",)):
+        monkeypatch.setenv("LQCD_SAP_GENERIC", generic)
+        out = P.ctx.sap(to_gpu(eta), bs=bs, ncy=4, nmr=5, prec=prec)
+        assert relerr(out, ref) < tol, generic
 
 
 @pytest.mark.parametrize("inner", [lqcd.F64, lqcd.F32], ids=["f64", "f32"])
