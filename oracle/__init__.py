@@ -61,6 +61,9 @@ def lib():
             "or_dfl_precond": (None, [P, IP, I, I, D, P, P]),
             "or_dfl_subspace": (None, [P, P]),
             "or_num_threads": (I, []),
+            "or_ptc_transport": (None, [P, I, P, P]),
+            "or_ptc_forward": (None, [P, I, IP, P, P, P, P]),
+            "or_ptc_backward": (None, [P, I, IP, P, P, P, P, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -262,6 +265,44 @@ class Oracle:
         out = np.empty_like(rho)
         lib().or_dfl_precond(self._o, self._bs(bs), ncy, nmr, ctol, _p(rho), _p(out))
         return out
+
+
+def ptc_weight_count(chans) -> int:
+    """complex weights of a network with channel counts chans[0..nl]"""
+    return sum(chans[l] * chans[l + 1] * 9 * 16 for l in range(len(chans) - 1))
+
+
+def ptc_transport(o: Oracle, d: int, f: np.ndarray) -> np.ndarray:
+    f = _c(f).reshape(o.V, 4, 3)
+    out = np.empty_like(f)
+    lib().or_ptc_transport(o._o, d, _p(f), _p(out))
+    return out
+
+
+def ptc_forward(o: Oracle, chans, W: np.ndarray, x: np.ndarray, keep_acts=False):
+    """N(x) for input fields x [chans[0]][V][4][3]; weights W flat complex."""
+    chans = [int(c) for c in chans]
+    nl = len(chans) - 1
+    ch = (C.c_int * len(chans))(*chans)
+    W = _c(W)
+    x = _c(x).reshape(chans[0], o.V, 4, 3)
+    out = np.empty((chans[-1], o.V, 4, 3), dtype=np.complex128)
+    acts = np.empty((sum(chans[:-1]), o.V, 4, 3), dtype=np.complex128) if keep_acts else None
+    lib().or_ptc_forward(o._o, nl, ch, _p(W), _p(x), _p(out), _p(acts) if keep_acts else None)
+    return (out, acts) if keep_acts else out
+
+
+def ptc_backward(o: Oracle, chans, W: np.ndarray, acts: np.ndarray, gout: np.ndarray):
+    """(dW, g_in) for the conjugate gradient gout at the output."""
+    chans = [int(c) for c in chans]
+    nl = len(chans) - 1
+    ch = (C.c_int * len(chans))(*chans)
+    W = _c(W)
+    dW = np.empty_like(W)
+    gout = _c(gout).reshape(chans[-1], o.V, 4, 3)
+    gin = np.empty((chans[0], o.V, 4, 3), dtype=np.complex128)
+    lib().or_ptc_backward(o._o, nl, ch, _p(W), _p(_c(acts)), _p(gout), _p(dW), _p(gin))
+    return dW, gin
 
 
 def even_odd_split(o: Oracle, x: np.ndarray):

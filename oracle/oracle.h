@@ -108,4 +108,11 @@ void or_dfl_precond(const oracle *o, const int bs[4], int ncy, int nmr, double c
 void or_dfl_subspace(const oracle *o, double *phi);
 void or_dfl_free(oracle *o);
 
+/* --- parallel-transport network (oracle_ptc.c) --- */
+void or_ptc_transport(const oracle *o, int d, const double *f, double *out);
+void or_ptc_forward(const oracle *o, int nl, const int *chans, const double *W, const double *in, double *out,
+                    double *acts);
+void or_ptc_backward(const oracle *o, int nl, const int *chans, const double *W, const double *acts,
+                     const double *gout, double *dW, double *gin);
+
 #endif
