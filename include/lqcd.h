@@ -71,7 +71,8 @@ typedef enum {
 typedef enum {
     LQCD_F64 = 0,   /* double storage and arithmetic */
     LQCD_F32 = 1,   /* float storage and arithmetic, SU(3) links stored as 2 rows */
-    LQCD_F16S = 2   /* half storage with one float scale per site and field, float arithmetic */
+    LQCD_F16S = 2,  /* half storage with one float scale per site and field, float arithmetic */
+    LQCD_BF16 = 3   /* bfloat16 storage, tensor-core products, float accumulation (network only) */
 } lqcd_prec;
 
 typedef struct {
@@ -204,7 +205,8 @@ LQCD_API lqcd_status lqcd_dfl_precond(lqcd_ctx *ctx, const lqcd_sap_params *sap,
 typedef enum {
     LQCD_SOLVER_CGNR = 0,     /* even-odd CG on Dhat^dag Dhat (FP64) */
     LQCD_SOLVER_SAP_GCR = 1,  /* flexible GCR, SAP preconditioner */
-    LQCD_SOLVER_DFL_SAP_GCR = 2 /* flexible GCR, deflated SAP preconditioner */
+    LQCD_SOLVER_DFL_SAP_GCR = 2, /* flexible GCR, deflated SAP preconditioner */
+    LQCD_SOLVER_NET_GCR = 3   /* flexible GCR, network preconditioner, SAP where it fails */
 } lqcd_solver;
 
 typedef struct {
@@ -223,6 +225,7 @@ typedef struct {
     double relres_dhat;      /* |eta_e - Dhat psi_e| / |eta_e| in FP64 */
     double seconds;          /* wall time of the solve */
     lqcd_status status;
+    int net_fallbacks;       /* GCR steps where the network was replaced by SAP */
 } lqcd_solve_info;
 
 /* Solve Dhat psi_e = eta_e (Eq. 2) for nrhs even fields to a true relative
@@ -233,6 +236,46 @@ typedef struct {
  * entries (may be NULL).  Returns the worst per-RHS status. */
 LQCD_API lqcd_status lqcd_solve_dhat(lqcd_ctx *ctx, const lqcd_solver_params *p, const double *eta_dev,
                             double *psi_dev, int nrhs, lqcd_solve_info *info);
+
+/* ------------------------------------------------- learned preconditioner */
+/* A gauge-equivariant parallel-transport network N (no counterpart in the
+ * paper; it is the learned preconditioner of the benchmark workload):
+ *   y_o(x) = sum_i sum_d W_{o,i,d} (T_d y_i)(x),  T_0 = 1,
+ *   (T_+mu f)(x) = U_mu(x) f(x+mu),  (T_-mu f)(x) = U_mu(x-mu)^dag f(x-mu),
+ * with the antiperiodic sign on hops across the time boundary; W_{o,i,d} is a
+ * complex 4x4 spin matrix (identity on colour), d = 0, 1+2mu (+mu), 2+2mu (-mu).
+ * Weights (host, complex float interleaved re,im) are laid out layer after
+ * layer as W[o][i][d][s][s'].  Activations are stored as act (LQCD_BF16:
+ * bfloat16 with tensor-core products and float accumulation; LQCD_F32).
+ * The network keeps FP32 master weights; it survives lqcd_set_gauge. */
+typedef struct {
+    int nlayers;      /* 1..4 */
+    int chans[5];     /* chans[0] = chans[nlayers] = 1; every entry 1 or 2 */
+    lqcd_prec act;    /* LQCD_BF16 or LQCD_F32 */
+} lqcd_net_desc;
+
+LQCD_API lqcd_status lqcd_net_set(lqcd_ctx *ctx, const lqcd_net_desc *desc, const float *W_host);
+LQCD_API lqcd_status lqcd_net_get(lqcd_ctx *ctx, float *W_host);
+/* out = N(in) for nrhs canonical FP64 full fields (device). */
+LQCD_API lqcd_status lqcd_net_apply(lqcd_ctx *ctx, const double *in_dev, double *out_dev, int nrhs);
+/* Loss L = (1/nb) sum_b |N(in_b) - t_b|^2 / |t_b|^2 over nb canonical FP64 full
+ * fields and its gradient dL/dRe W + i dL/dIm W (host, same layout as W). */
+LQCD_API lqcd_status lqcd_net_loss_grad(lqcd_ctx *ctx, const double *in_dev, const double *target_dev, int nb,
+                                        double *loss, float *grad_host);
+
+typedef struct {
+    int steps;             /* Adam steps */
+    int batch;             /* sources per step */
+    double lr, beta1, beta2, eps;
+    lqcd_sap_params sap;   /* targets t = M_sap(source) */
+} lqcd_net_train_params;
+/* Train on (gauge field of ctx, source, M_sap source) pairs: the nsrc sources
+ * (canonical FP64 full fields, device; the caller draws them) are paired with
+ * their SAP outputs computed here; Adam on the loss above, cycling through
+ * the sources in batches.  loss_history (host, may be NULL) receives steps
+ * values.  Requires lqcd_clover_invert and lqcd_net_set. */
+LQCD_API lqcd_status lqcd_net_train(lqcd_ctx *ctx, const lqcd_net_train_params *p, const double *sources_dev,
+                                    int nsrc, double *loss_history);
 
 /* Solve D psi = eta on the full lattice (GCR solvers only); canonical FP64. */
 LQCD_API lqcd_status lqcd_solve_D(lqcd_ctx *ctx, const lqcd_solver_params *p, const double *eta_dev,

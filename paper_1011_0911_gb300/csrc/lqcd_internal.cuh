@@ -86,6 +86,7 @@ struct Workspace {
 };
 
 struct DflState;   // deflation subspace (lqcd_dfl.cu)
+struct NetState;   // learned preconditioner (lqcd_ptc.cu)
 
 struct lqcd_ctx {
     lqcd_geom geom;
@@ -109,6 +110,7 @@ struct lqcd_ctx {
     // named temporary buffers, grown on demand
     Workspace ws[24];
     DflState *dfl = nullptr;
+    NetState *net = nullptr;
     long n_kernel_launches = 0;
 };
 
@@ -143,6 +145,11 @@ enum {
     WS_MISC2,
     WS_COARSE,
     WS_SOLVE_IO,
+    WS_NET_PART,
+    WS_NET_ACT,
+    WS_NET_TGT,
+    WS_NET_BATCH_T,
+    WS_NET_FALLBACK,
 };
 lqcd_status ws_get(lqcd_ctx *c, int slot, size_t bytes, void **out);
 
@@ -195,6 +202,9 @@ lqcd_status sap_axpby_native(lqcd_ctx *c, lqcd_prec p, const void *eta, void *r)
 void sap_free_plans(lqcd_ctx *c);
 lqcd_status sap_apply(lqcd_ctx *c, const lqcd_sap_params *sp, const void *eta_native,
                       void *psi_native, int nrhs = 1);
+// learned preconditioner
+void net_free(lqcd_ctx *c);
+lqcd_status net_apply_native(lqcd_ctx *c, const double2 *rho, double2 *phi, int nrhs);
 // deflation
 void dfl_free(lqcd_ctx *c);
 lqcd_status dfl_precond_native(lqcd_ctx *c, const lqcd_sap_params *sp, const double2 *rho,

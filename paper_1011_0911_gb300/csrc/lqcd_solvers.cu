@@ -125,6 +125,7 @@ lqcd_status precond(lqcd_ctx *c, const lqcd_solver_params *sp, const double2 *rh
 {
     const lqcd_sap_params &sap = sp->sap;
     if (sp->solver == LQCD_SOLVER_DFL_SAP_GCR) return dfl_precond_native(c, &sap, rho, phi, nrhs);
+    if (sp->solver == LQCD_SOLVER_NET_GCR) return net_apply_native(c, rho, phi, nrhs);
     if (sap.prec == LQCD_F64) return sap_apply(c, &sap, rho, phi, nrhs);
     void *a, *b;
     size_t fb = 2 * native_half_bytes(c, sap.prec) * nrhs;
@@ -149,9 +150,14 @@ lqcd_status apply_D_inner(lqcd_ctx *c, lqcd_prec inner, const double2 *phi, doub
 }
 
 struct GcrState {
-    std::vector<int> iters, restarts;
+    std::vector<int> iters, restarts, net_fallbacks;
     std::vector<double> relres;
     std::vector<lqcd_status> status;
+    explicit GcrState(int nrhs)
+        : iters(nrhs, 0), restarts(nrhs, 0), net_fallbacks(nrhs, 0), relres(nrhs, 0),
+          status(nrhs, LQCD_ERR_NOT_CONVERGED)
+    {
+    }
 };
 
 // LQCD_PROFILE=1: synchronise around the phases of the GCR and report their
@@ -240,40 +246,71 @@ lqcd_status gcr_native(lqcd_ctx *c, const lqcd_solver_params *sp, const std::vec
             prof.start();
             LQCD_TRY(precond(c, sp, rho, ph, nrhs));
             prof.stop(0);
-            prof.start();
-            LQCD_TRY(apply_D_inner(c, sp->inner, ph, ch, nrhs));
-            prof.stop(1);
-            prof.start();
-            for (int r = 0; r < nrhs; r++)
-                for (int i = 0; i < k; i++) a[((size_t)r * nkv + i) * nkv + k] = {0, 0};
-            // classical Gram-Schmidt; a second pass only where the first removed more
-            // than half of |chi_k|^2 (Daniel-Gragg-Kaufman-Stewart criterion).  The
-            // first pass reduces chi_0..chi_k against chi_k, which also gives |chi_k|^2.
-            for (int pass = 0; pass < 2 && k > 0; pass++) {
-                const int kk = pass == 0 ? k + 1 : k;
-                LQCD_TRY(bblas_dot(c, n2, nrhs, (const double *)chi, 2 * bf, n2, (const double *)ch, n2, kk,
-                                   dots.data()));
-                bool again = false;
-                std::vector<double> cf(2 * (size_t)nrhs * k);
-                for (int r = 0; r < nrhs; r++) {
-                    double removed = 0;
-                    for (int i = 0; i < k; i++) {
-                        const double dr = dots[2 * (r * kk + i)], di = dots[2 * (r * kk + i) + 1];
-                        a[((size_t)r * nkv + i) * nkv + k].re += dr;
-                        a[((size_t)r * nkv + i) * nkv + k].im += di;
-                        cf[2 * (r * k + i)] = dr;
-                        cf[2 * (r * k + i) + 1] = di;
-                        removed += dr * dr + di * di;
+            // chi_k = D phi_k, orthogonalised against chi_0..chi_{k-1}; leaves |chi_k|^2
+            // and <rho, chi_k> in dots
+            auto orth = [&]() -> lqcd_status {
+                prof.start();
+                LQCD_TRY(apply_D_inner(c, sp->inner, ph, ch, nrhs));
+                prof.stop(1);
+                prof.start();
+                for (int r = 0; r < nrhs; r++)
+                    for (int i = 0; i < k; i++) a[((size_t)r * nkv + i) * nkv + k] = {0, 0};
+                // classical Gram-Schmidt; a second pass only where the first removed more
+                // than half of |chi_k|^2 (Daniel-Gragg-Kaufman-Stewart criterion).  The
+                // first pass reduces chi_0..chi_k against chi_k, which also gives |chi_k|^2.
+                for (int pass = 0; pass < 2 && k > 0; pass++) {
+                    const int kk = pass == 0 ? k + 1 : k;
+                    LQCD_TRY(bblas_dot(c, n2, nrhs, (const double *)chi, 2 * bf, n2, (const double *)ch, n2, kk,
+                                       dots.data()));
+                    bool again = false;
+                    std::vector<double> cf(2 * (size_t)nrhs * k);
+                    for (int r = 0; r < nrhs; r++) {
+                        double removed = 0;
+                        for (int i = 0; i < k; i++) {
+                            const double dr = dots[2 * (r * kk + i)], di = dots[2 * (r * kk + i) + 1];
+                            a[((size_t)r * nkv + i) * nkv + k].re += dr;
+                            a[((size_t)r * nkv + i) * nkv + k].im += di;
+                            cf[2 * (r * k + i)] = dr;
+                            cf[2 * (r * k + i) + 1] = di;
+                            removed += dr * dr + di * di;
+                        }
+                        if (pass == 0 && active[r] && removed > 0.5 * dots[2 * (r * kk + k)]) again = true;
                     }
-                    if (pass == 0 && active[r] && removed > 0.5 * dots[2 * (r * kk + k)]) again = true;
+                    LQCD_TRY(bblas_multi_axpy(c, n2, nrhs, k, cf.data(), (const double *)chi, 2 * bf, n2,
+                                              (double *)ch, n2, -1.0));
+                    if (!again) break;
                 }
-                LQCD_TRY(bblas_multi_axpy(c, n2, nrhs, k, cf.data(), (const double *)chi, 2 * bf, n2,
-                                          (double *)ch, n2, -1.0));
-                if (!again) break;
+                // |chi_k|^2 and <rho, chi_k> in one reduction (family {chi_k, rho} against chi_k)
+                return bblas_dot(c, n2, nrhs, (const double *)ch, 2 * (rho - ch), n2, (const double *)ch, n2, 2,
+                                 dots.data());
+            };
+            LQCD_TRY(orth());
+            if (sp->solver == LQCD_SOLVER_NET_GCR) {
+                // the network's direction must cut |rho| to 0.95 |rho| at least, i.e.
+                // |c_k|^2 >= (1 - 0.95^2) |rho|^2; where it does not, SAP replaces it
+                std::vector<int> reject;
+                for (int r = 0; r < nrhs; r++) {
+                    if (!active[r]) continue;
+                    const double q2 = dots[2 * (2 * r)];
+                    const double c2 = q2 > 0 ? (dots[2 * (2 * r + 1)] * dots[2 * (2 * r + 1)] +
+                                                dots[2 * (2 * r + 1) + 1] * dots[2 * (2 * r + 1) + 1]) / q2
+                                             : 0.0;
+                    if (!std::isfinite(c2) || !std::isfinite(q2) || c2 < (1.0 - 0.95 * 0.95) * rn2[r]) reject.push_back(r);
+                }
+                if (!reject.empty()) {
+                    void *fb;
+                    LQCD_TRY(ws_get(c, WS_NET_FALLBACK, (size_t)bf * sizeof(double2), &fb));
+                    lqcd_solver_params sap_only = *sp;
+                    sap_only.solver = LQCD_SOLVER_SAP_GCR;
+                    LQCD_TRY(precond(c, &sap_only, rho, (double2 *)fb, nrhs));
+                    for (int r : reject) {
+                        LQCD_CUDA_CHECK(c, cudaMemcpyAsync(ph + r * nf, (double2 *)fb + r * nf, nf * sizeof(double2),
+                                                           cudaMemcpyDeviceToDevice, c->stream));
+                        S.net_fallbacks[r]++;
+                    }
+                    LQCD_TRY(orth());
+                }
             }
-            // |chi_k|^2 and <rho, chi_k> in one reduction (family {chi_k, rho} against chi_k)
-            LQCD_TRY(bblas_dot(c, n2, nrhs, (const double *)ch, 2 * (rho - ch), n2, (const double *)ch, n2, 2,
-                               dots.data()));
             std::vector<double> coef2(2 * (size_t)nrhs);
             for (int r = 0; r < nrhs; r++) {
                 const double bk = std::sqrt(dots[2 * (2 * r)]);
@@ -385,6 +422,9 @@ lqcd_status check_params(lqcd_ctx *c, const lqcd_solver_params *p, int nrhs)
     if (!c->have_clover) return set_err(c, LQCD_ERR_STATE, "clover term not built");
     if (p->solver == LQCD_SOLVER_DFL_SAP_GCR && !c->dfl)
         return set_err(c, LQCD_ERR_STATE, "deflation subspace not built");
+    if (p->solver == LQCD_SOLVER_NET_GCR && !c->net) return set_err(c, LQCD_ERR_STATE, "network not set");
+    if (p->solver < LQCD_SOLVER_CGNR || p->solver > LQCD_SOLVER_NET_GCR)
+        return set_err(c, LQCD_ERR_ARG, "solver %d", (int)p->solver);
     if (p->solver != LQCD_SOLVER_CGNR && (p->inner != LQCD_F64 && p->inner != LQCD_F32))
         return set_err(c, LQCD_ERR_ARG, "inner precision %d", (int)p->inner);
     return LQCD_OK;
@@ -427,11 +467,7 @@ lqcd_status lqcd_solve_dhat(lqcd_ctx *c, const lqcd_solver_params *p, const doub
         LQCD_TRY(blas_zero(c, 4 * hb * nrhs, io));
         for (int k = 0; k < nrhs; k++)
             LQCD_TRY(pack_field(c, LQCD_F64, 1, eta + (size_t)k * 24 * Vh, eta_f + k * nf, 1, false));
-        GcrState S;
-        S.iters.assign(nrhs, 0);
-        S.restarts.assign(nrhs, 0);
-        S.relres.assign(nrhs, 0);
-        S.status.assign(nrhs, LQCD_ERR_NOT_CONVERGED);
+        GcrState S(nrhs);
         std::vector<double> tol(nrhs, p->tol), rh(nrhs, 0);
         for (int attempt = 0; attempt < 4; attempt++) {
             int used = 0;
@@ -458,6 +494,7 @@ lqcd_status lqcd_solve_dhat(lqcd_ctx *c, const lqcd_solver_params *p, const doub
                 info[k].relres_dhat = rh[k];
                 info[k].status = S.status[k];
                 info[k].seconds = now_s() - t0;
+                info[k].net_fallbacks = S.net_fallbacks[k];
             }
             all = worst(all, S.status[k]);
         }
@@ -481,11 +518,7 @@ lqcd_status lqcd_solve_D(lqcd_ctx *c, const lqcd_solver_params *p, const double 
     double2 *eta_f = (double2 *)io, *psi_f = eta_f + nrhs * nf;
     LQCD_TRY(pack_field(c, LQCD_F64, 2, eta, eta_f, nrhs, false));
     LQCD_TRY(blas_zero(c, 2 * hb * nrhs, psi_f));
-    GcrState S;
-    S.iters.assign(nrhs, 0);
-    S.restarts.assign(nrhs, 0);
-    S.relres.assign(nrhs, 0);
-    S.status.assign(nrhs, LQCD_ERR_NOT_CONVERGED);
+    GcrState S(nrhs);
     std::vector<double> tol(nrhs, p->tol);
     LQCD_TRY(gcr_native(c, p, tol, eta_f, psi_f, nrhs, p->nmx, S));
     LQCD_TRY(pack_field(c, LQCD_F64, 2, psi, psi_f, nrhs, true));
@@ -498,6 +531,7 @@ lqcd_status lqcd_solve_D(lqcd_ctx *c, const lqcd_solver_params *p, const double 
             info[k].relres_dhat = -1;
             info[k].status = S.status[k];
             info[k].seconds = now_s() - t0;
+            info[k].net_fallbacks = S.net_fallbacks[k];
         }
         all = worst(all, S.status[k]);
     }

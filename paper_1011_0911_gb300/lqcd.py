@@ -17,8 +17,8 @@ import torch
 
 from . import build_lib
 
-F64, F32, F16S = 0, 1, 2
-SOLVER_CGNR, SOLVER_SAP_GCR, SOLVER_DFL_SAP_GCR = 0, 1, 2
+F64, F32, F16S, BF16 = 0, 1, 2, 3
+SOLVER_CGNR, SOLVER_SAP_GCR, SOLVER_DFL_SAP_GCR, SOLVER_NET_GCR = 0, 1, 2, 3
 
 STATUS = {
     0: "OK", 1: "ERR_ARG", 2: "ERR_CUDA", 3: "ERR_NOMEM", 4: "ERR_SINGULAR_CLOVER",
@@ -53,10 +53,20 @@ class SolverParams(C.Structure):
 
 class SolveInfo(C.Structure):
     _fields_ = [("iters", C.c_int), ("restarts", C.c_int), ("true_relres", C.c_double),
-                ("relres_dhat", C.c_double), ("seconds", C.c_double), ("status", C.c_int)]
+                ("relres_dhat", C.c_double), ("seconds", C.c_double), ("status", C.c_int),
+                ("net_fallbacks", C.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class NetDesc(C.Structure):
+    _fields_ = [("nlayers", C.c_int), ("chans", C.c_int * 5), ("act", C.c_int)]
+
+
+class NetTrainParams(C.Structure):
+    _fields_ = [("steps", C.c_int), ("batch", C.c_int), ("lr", C.c_double), ("beta1", C.c_double),
+                ("beta2", C.c_double), ("eps", C.c_double), ("sap", SapParams)]
 
 
 _lib = None
@@ -96,6 +106,11 @@ def lib():
             "lqcd_dfl_little_apply": [P, P, P],
             "lqcd_dfl_coarse_solve": [P, P, P, C.POINTER(I)],
             "lqcd_dfl_precond": [P, C.POINTER(SapParams), P, P],
+            "lqcd_net_set": [P, C.POINTER(NetDesc), P],
+            "lqcd_net_get": [P, P],
+            "lqcd_net_apply": [P, P, P, I],
+            "lqcd_net_loss_grad": [P, P, P, I, C.POINTER(D), P],
+            "lqcd_net_train": [P, C.POINTER(NetTrainParams), P, I, P],
             "lqcd_solve_dhat": [P, C.POINTER(SolverParams), P, P, I, C.POINTER(SolveInfo)],
             "lqcd_solve_D": [P, C.POINTER(SolverParams), P, P, I, C.POINTER(SolveInfo)],
         }
@@ -294,6 +309,54 @@ class Context:
         p = sap_params(bs, ncy, nmr, prec)
         self._check(lib().lqcd_dfl_precond(self._h, C.byref(p), _ptr(rho), _ptr(out)), "dfl_precond")
         return out
+
+    # --------------------------------------------------- learned preconditioner
+    @staticmethod
+    def net_weight_count(chans) -> int:
+        return sum(chans[l] * chans[l + 1] * 144 for l in range(len(chans) - 1))
+
+    def net_set(self, chans, W, act=BF16):
+        """W: complex numpy array (flat, layer after layer, [o][i][d][s][s'])."""
+        import numpy as np
+        chans = [int(c) for c in chans]
+        W = np.ascontiguousarray(np.asarray(W, dtype=np.complex64))
+        assert W.size == self.net_weight_count(chans)
+        d = NetDesc(len(chans) - 1, (C.c_int * 5)(*(chans + [0] * (5 - len(chans)))), act)
+        self._net_chans = chans
+        self._check(lib().lqcd_net_set(self._h, C.byref(d), W.ctypes.data_as(C.c_void_p)), "lqcd_net_set")
+
+    def net_get(self):
+        import numpy as np
+        W = np.empty(self.net_weight_count(self._net_chans), dtype=np.complex64)
+        self._check(lib().lqcd_net_get(self._h, W.ctypes.data_as(C.c_void_p)), "lqcd_net_get")
+        return W
+
+    def net_apply(self, x: torch.Tensor) -> torch.Tensor:
+        x = x.to(torch.complex128).contiguous()
+        out = torch.empty_like(x)
+        self._check(lib().lqcd_net_apply(self._h, _ptr(x), _ptr(out), self._nrhs(x, self.V)), "lqcd_net_apply")
+        return out
+
+    def net_loss_grad(self, x: torch.Tensor, t: torch.Tensor):
+        import numpy as np
+        x = x.to(torch.complex128).contiguous()
+        t = t.to(torch.complex128).contiguous()
+        g = np.empty(self.net_weight_count(self._net_chans), dtype=np.complex64)
+        loss = C.c_double()
+        st = lib().lqcd_net_loss_grad(self._h, _ptr(x), _ptr(t), self._nrhs(x, self.V), C.byref(loss),
+                                      g.ctypes.data_as(C.c_void_p))
+        self._check(st, "lqcd_net_loss_grad")
+        return loss.value, g
+
+    def net_train(self, sources: torch.Tensor, steps, batch=8, lr=1e-3, bs=(4, 4, 4, 4), ncy=4, nmr=5, sap_prec=F32):
+        import numpy as np
+        sources = sources.to(torch.complex128).contiguous()
+        nsrc = self._nrhs(sources, self.V)
+        p = NetTrainParams(steps, batch, lr, 0.9, 0.999, 1e-8, sap_params(bs, ncy, nmr, sap_prec))
+        hist = np.zeros(max(steps, 1))
+        self._check(lib().lqcd_net_train(self._h, C.byref(p), _ptr(sources), nsrc, hist.ctypes.data_as(C.c_void_p)),
+                    "lqcd_net_train")
+        return hist[:steps]
 
     # -------------------------------------------------------------- solvers
     def _solve(self, fn, eta, nsites, solver, tol, nkv, nmx, bs, ncy, nmr, sap_prec, inner, check):

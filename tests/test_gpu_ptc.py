@@ -1,0 +1,179 @@
+"""GPU parity of the parallel-transport network (forward, loss gradient) against
+the FP64 oracle, gauge equivariance on the GPU, training, and the network as
+the preconditioner of the flexible GCR (convergence, fallback, gain)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as orc
+from paper_1011_0911_gb300 import lqcd, synth
+from tests import util
+from tests.gpu_util import Pair
+
+pytestmark = pytest.mark.gpu
+
+CHANS = (1, 2, 2, 1)
+# relative error of a whole output field / gradient against the FP64 oracle
+NET_TOL = {lqcd.F32: 1e-5, lqcd.BF16: 2e-2}
+
+
+def rand_weights(chans, seed, scale=0.3, ident=0.0):
+    n = orc.ptc_weight_count(chans)
+    g = synth.gaussians(seed, synth.STREAM_NET, 2 * n)
+    W = scale * (g[0::2] + 1j * g[1::2])
+    off = 0
+    for l in range(len(chans) - 1):
+        cin, cout = chans[l], chans[l + 1]
+        W[off:off + cout * cin * 144].reshape(cout, cin, 9, 4, 4)[0, 0, 0] += ident * np.eye(4)
+        off += cout * cin * 144
+    return W.astype(np.complex64)
+
+
+def sources(V, n, seed):
+    return np.stack([synth.gaussian_spinor(V, seed + k) for k in range(n)])
+
+
+def oracle_loss_grad(o, chans, W, x, t):
+    """mean_b |N(x_b) - t_b|^2 / |t_b|^2 and its conjugate gradient in W."""
+    nb = len(x)
+    L, G = 0.0, np.zeros(orc.ptc_weight_count(chans), dtype=np.complex128)
+    for b in range(nb):
+        out, acts = orc.ptc_forward(o, chans, W, x[b][None], keep_acts=True)
+        tt = np.vdot(t[b], t[b]).real
+        L += np.vdot(out[0] - t[b], out[0] - t[b]).real / tt / nb
+        dW, _ = orc.ptc_backward(o, chans, W, acts, (2.0 * (out[0] - t[b].reshape(out[0].shape)) / (tt * nb))[None])
+        G += dW
+    return L, G
+
+
+@pytest.mark.parametrize("act", [lqcd.F32, lqcd.BF16])
+@pytest.mark.parametrize("dims", [(6, 6, 6, 6), (8, 8, 4, 8)])
+def test_forward_parity(dims, act):
+    """V = 1296 ends in a partial tile of sites; three samples in one launch."""
+    P = Pair(dims)
+    W = rand_weights(CHANS, 11, ident=0.8)
+    P.ctx.net_set(CHANS, W, act=act)
+    x = sources(P.V, 3, 40)
+    got = P.ctx.net_apply(torch.from_numpy(x).cuda()).cpu().numpy()
+    for b in range(3):
+        ref = orc.ptc_forward(P.o, CHANS, W.astype(np.complex128), x[b][None])[0]
+        assert util.relerr(got[b].reshape(ref.shape), ref) < NET_TOL[act], (b, act)
+
+
+@pytest.mark.parametrize("act", [lqcd.F32, lqcd.BF16])
+def test_loss_grad_parity(act):
+    P = Pair((6, 6, 6, 6))
+    W = rand_weights(CHANS, 12, ident=0.8)
+    P.ctx.net_set(CHANS, W, act=act)
+    x = sources(P.V, 2, 50)
+    t = sources(P.V, 2, 60)
+    L, G = P.ctx.net_loss_grad(torch.from_numpy(x).cuda(), torch.from_numpy(t).cuda())
+    Lr, Gr = oracle_loss_grad(P.o, CHANS, W.astype(np.complex128), x, t)
+    assert abs(L - Lr) < NET_TOL[act] * Lr
+    assert util.relerr(G, Gr) < NET_TOL[act]
+    # the weights the library holds are the ones it was given
+    assert np.array_equal(P.ctx.net_get(), W)
+
+
+def test_single_layer_wilson_hop():
+    """One 1->1 layer with W_0 = (4 + m0), W_+mu = -(1 - gamma_mu)/2 and
+    W_-mu = -(1 + gamma_mu)/2 is D at c_sw = 0 (Eq. 1)."""
+    kappa = 0.1355
+    P = Pair((4, 4, 4, 8), kappa=kappa, csw=0.0)
+    m0 = 1 / (2 * kappa) - 4
+    W = np.zeros((9, 4, 4), dtype=np.complex128)
+    W[0] = (4 + m0) * np.eye(4)
+    for mu in range(4):
+        gm = orc.gamma(mu)
+        W[1 + 2 * mu] = -0.5 * (np.eye(4) - gm)
+        W[2 + 2 * mu] = -0.5 * (np.eye(4) + gm)
+    P.ctx.net_set((1, 1), W.ravel().astype(np.complex64), act=lqcd.F32)
+    x = synth.gaussian_spinor(P.V, 70)
+    got = P.ctx.net_apply(torch.from_numpy(x[None]).cuda()).cpu().numpy()[0]
+    ref = P.o.D(x)
+    assert util.relerr(got.reshape(ref.shape), ref) < 1e-5
+
+
+def test_equivariance_gpu():
+    dims = (8, 4, 4, 8)
+    P = Pair(dims)
+    W = rand_weights(CHANS, 13, ident=0.8)
+    g = synth.random_su3(P.V, 19)
+    Ug = util.gauge_transform(dims, P.U, g)
+    Pg = Pair(dims, U=Ug)
+    P.ctx.net_set(CHANS, W, act=lqcd.F32)
+    Pg.ctx.net_set(CHANS, W, act=lqcd.F32)
+    rho = synth.gaussian_spinor(P.V, 80).reshape(P.V, 4, 3)
+    lhs = Pg.ctx.net_apply(torch.from_numpy(util.colour_rotate(g, rho)[None]).cuda()).cpu().numpy()[0]
+    rhs = util.colour_rotate(g, P.ctx.net_apply(torch.from_numpy(rho[None]).cuda()).cpu().numpy()[0].reshape(P.V, 4, 3))
+    assert util.relerr(lhs.reshape(rhs.shape), rhs) < 1e-5
+
+
+def test_net_set_rejects_bad_shapes():
+    P = Pair((4, 4, 4, 4))
+    with pytest.raises(lqcd.LqcdError):
+        P.ctx.net_set((1, 3, 1), np.zeros(orc.ptc_weight_count((1, 3, 1)), np.complex64))
+    with pytest.raises(lqcd.LqcdError):
+        P.ctx.net_set((2, 1), np.zeros(orc.ptc_weight_count((2, 1)), np.complex64))
+    with pytest.raises(lqcd.LqcdError):
+        P.ctx.net_apply(torch.zeros((1, P.V, 4, 3), dtype=torch.complex128).cuda())
+
+
+def one_step_residual(ctx, eta, phi):
+    """|eta - D phi| / |eta| for each field."""
+    r = eta - ctx.apply_D(phi)
+    return (torch.linalg.vector_norm(r.reshape(len(eta), -1), dim=1) /
+            torch.linalg.vector_norm(eta.reshape(len(eta), -1), dim=1)).cpu().numpy()
+
+
+def scalar_residual(ctx, eta):
+    """min over alpha of |eta - alpha D eta| / |eta|: the best scaled identity."""
+    De = ctx.apply_D(eta)
+    out = []
+    for b in range(len(eta)):
+        e, d = eta[b].reshape(-1), De[b].reshape(-1)
+        a = torch.vdot(d, e) / torch.vdot(d, d)
+        out.append((torch.linalg.vector_norm(e - a * d) / torch.linalg.vector_norm(e)).item())
+    return np.array(out)
+
+
+@pytest.fixture(scope="module")
+def trained():
+    dims = (8, 8, 8, 8)
+    P = Pair(dims, kappa=0.1355, csw=1.9)
+    W = rand_weights(CHANS, 14, scale=0.02, ident=0.7)
+    P.ctx.net_set(CHANS, W, act=lqcd.BF16)
+    src = torch.from_numpy(sources(P.V, 16, 100)).cuda()
+    hist = P.ctx.net_train(src, steps=120, batch=4, lr=4e-3, sap_prec=lqcd.F32)
+    return P, hist
+
+
+def test_training_reduces_loss(trained):
+    _, hist = trained
+    assert np.all(np.isfinite(hist))
+    assert hist[-10:].mean() < 0.7 * hist[:4].mean(), (hist[:4], hist[-10:])
+
+
+def test_trained_net_gain(trained):
+    """On sources it has not seen, the trained network is a better one-step
+    preconditioner of D than the best multiple of the identity."""
+    P, _ = trained
+    eta = torch.from_numpy(sources(P.V, 4, 500)).cuda()
+    r_net = one_step_residual(P.ctx, eta, P.ctx.net_apply(eta))
+    r_id = scalar_residual(P.ctx, eta)
+    assert np.all(r_net < 0.9 * r_id), (r_net, r_id)
+
+
+def test_net_gcr_solve(trained):
+    """The network inside the flexible GCR: FP64 true residual at 1e-10, with
+    SAP taking over the steps where the network's direction is poor."""
+    P, _ = trained
+    eta = torch.from_numpy(sources(P.V, 2, 600)).cuda()
+    psi, infos, st = P.ctx.solve_D(eta, solver=lqcd.SOLVER_NET_GCR, tol=1e-10, nkv=16, nmx=2000,
+                                   sap_prec=lqcd.F32)
+    assert st == 0
+    for k, inf in enumerate(infos):
+        assert inf["true_relres"] <= 1e-10
+        assert 0 <= inf["net_fallbacks"] <= inf["iters"]
+        r = eta[k] - P.ctx.apply_D(psi[k][None])[0]
+        assert (torch.linalg.vector_norm(r) / torch.linalg.vector_norm(eta[k])).item() <= 1.5e-10
