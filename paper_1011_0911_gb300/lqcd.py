@@ -98,6 +98,7 @@ def lib():
             "lqcd_unpack": [P, I, I, P, P, I],
             "lqcd_apply_Dhat_native": [P, I, P, P, I],
             "lqcd_apply_D_native": [P, I, P, P, I],
+            "lqcd_apply_Dhat_native_static": [P, I, P, P, I],
             "lqcd_sap": [P, C.POINTER(SapParams), P, P],
             "lqcd_dfl_build": [P, C.POINTER(DflParams), P],
             "lqcd_dfl_export": [P, P, P],
@@ -240,6 +241,12 @@ class Context:
     def apply_Dhat_native(self, x_native, out_native, prec, nrhs):
         self._check(lib().lqcd_apply_Dhat_native(self._h, prec, _ptr(x_native), _ptr(out_native), nrhs),
                     "apply_Dhat_native")
+
+    def apply_Dhat_native_static(self, x_native, out_native, prec, nrhs):
+        """As apply_Dhat_native, with the odd-site intermediate in the library's
+        fixed device array (no device allocation; see lqcd.h for the limit)."""
+        self._check(lib().lqcd_apply_Dhat_native_static(self._h, prec, _ptr(x_native), _ptr(out_native), nrhs),
+                    "apply_Dhat_native_static")
 
     def apply_D_native(self, x_native, out_native, prec, nrhs):
         self._check(lib().lqcd_apply_D_native(self._h, prec, _ptr(x_native), _ptr(out_native), nrhs),
