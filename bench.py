@@ -40,6 +40,8 @@ def dhat_bytes_per_site(prec: str, nrhs: int) -> int:
     Links: each of the two half-hops reads every link once (8 per site);
     clover: A_ee and A_oo^-1 (2 x 72 reals); per field: psi_e read by both
     kernels, chi_o written and read, out written (5 x 24 reals)."""
+    if prec == "f16s":   # FP16 links (2 rows) and clover; a field site is 48 B of halves + a 4 B scale
+        return 2 * (2 * 8 * 12 + 144) + 5 * 52 * nrhs
     word = 8 if prec == "f64" else 4
     link_words = 2 * 8 * (18 if prec == "f64" else 12)
     return word * (link_words + 144 + 120 * nrhs)
@@ -238,7 +240,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--nrhs", type=int, default=12)
-    ap.add_argument("--prec", default="f32", choices=["f32", "f64"])
+    ap.add_argument("--prec", default="f32", choices=["f32", "f64", "f16s"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
     ap.add_argument("--no-solve", action="store_true", help="skip the time-to-solution comparison")
@@ -271,7 +273,7 @@ def main():
         dist.init_process_group("nccl")
 
     from paper_1011_0911_gb300 import lqcd, synth
-    prec = lqcd.F32 if args.prec == "f32" else lqcd.F64
+    prec = {"f32": lqcd.F32, "f64": lqcd.F64, "f16s": lqcd.F16S}[args.prec]
     nrhs = args.nrhs
     U = synth.su3_links(DIMS, 0)
     ctx = lqcd.Context(DIMS)
@@ -279,7 +281,7 @@ def main():
     ctx.clover_invert(KAPPA, CSW)
     Vh = ctx.Vh
     eta = synth.gaussian_spinor(nrhs * Vh, 1 + rank).reshape(nrhs, Vh, 4, 3)
-    cdt = torch.complex64 if prec == lqcd.F32 else torch.complex128
+    cdt = torch.complex128 if prec == lqcd.F64 else torch.complex64
     eta_host = torch.from_numpy(eta).to(cdt).pin_memory()
     eta_dev = eta_host.cuda()
     nin = ctx.pack(eta_dev, prec, 1)
@@ -356,7 +358,8 @@ def main():
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": args.prec, "data": "synthetic",
             "config": {"workload": WORKLOAD, "lattice": args.lattice, "nrhs": nrhs, "precision": args.prec,
-                       "links": "2-row SU(3)" if prec == lqcd.F32 else "full SU(3)",
+                       "links": {lqcd.F32: "2-row SU(3)", lqcd.F64: "full SU(3)",
+                                 lqcd.F16S: "2-row SU(3) FP16, FP16 clover"}[prec],
                        "l2": "inputs larger than L2 (links+clover+12 fields = %.2f GB)" % (
                            (dhat_bytes_per_site(args.prec, nrhs) * Vh) / 1e9),
                        "parallelism": f"replicas x{world}"},

@@ -18,7 +18,7 @@
  *             ("even" or "odd") field lists the sites of that parity in
  *             increasing site order (rank r holds site 2r or 2r+1).
  *   Spinor    canonical layout [site][spin 4][colour 3][re,im]; LQCD_F64
- *             uses double, LQCD_F32 float.  nrhs fields are stored one after
+ *             uses double, LQCD_F32 and LQCD_F16S float.  nrhs fields are stored one after
  *             the other ([rhs][site]...).
  *   Links     [site][mu 0..3][row 3][col 3][re,im] double, forward links
  *             U_mu(x), SU(3); the gauge field is periodic.
@@ -115,7 +115,9 @@ LQCD_API lqcd_status lqcd_apply_clover(lqcd_ctx *ctx, int parity, int inverse, c
 /* -------------------------------------------------------------- operators */
 
 /* out = D in on the full lattice (Eq. 1).  in, out: nrhs canonical full
- * spinor fields of precision prec (F64: double, F32: float).  in != out. */
+ * spinor fields of precision prec (F64: double; F32 and F16S: float, the
+ * F16S operator storing every field in half precision with a per-site scale
+ * and computing in float).  in != out. */
 LQCD_API lqcd_status lqcd_apply_D(lqcd_ctx *ctx, lqcd_prec prec, const void *in_dev, void *out_dev,
                          int nrhs);
 
@@ -130,8 +132,10 @@ LQCD_API lqcd_status lqcd_apply_Dhat(lqcd_ctx *ctx, lqcd_prec prec, const void *
  * even half first).  Layout, for sites s of one parity, rhs k:
  *   F64:  double2 at [(k*12 + c) * Vh + s], c = 3*spin+colour
  *   F32:  float4  at [(k*6 + q) * Vh + s],  q-th group of 4 reals of the site
- *   F16S: uint4 (8 halves) at [(k*3 + q) * Vh + s], then one float scale per
- *         (k, s) after all nrhs*3*Vh uint4 (value = half * scale).
+ *   F16S: per half field (one parity, one rhs) uint4 (8 halves = 4 complex)
+ *         at [q * Vh + s], q = 0..2, then float scale[s]: value = half * scale,
+ *         scale = largest |real component| of the site (52 bytes per site).
+ *         The F16S operators read FP16 copies of the links and clover term.
  * Pack / unpack convert between canonical and native fields. */
 LQCD_API size_t lqcd_native_bytes(const lqcd_ctx *ctx, lqcd_prec prec, int nsub, int nrhs);
 LQCD_API lqcd_status lqcd_pack(lqcd_ctx *ctx, lqcd_prec prec, int nsub, const void *canon_dev,

@@ -154,7 +154,7 @@ __device__ int lu_inv6(C a[6][6], C inv[6][6], double *logabsdet)
 }
 
 // write a Hermitian 6x6 (upper triangle taken) to the packed native slots
-__device__ void store_herm(const C m[6][6], int blk, int r, long Vh, double2 *A64, float4 *A32)
+__device__ void store_herm(const C m[6][6], int blk, int r, long Vh, double2 *A64, float4 *A32, uint2 *A16)
 {
     double v[36];
     for (int i = 0; i < 6; i++) v[i] = m[i][i].re;
@@ -169,6 +169,11 @@ __device__ void store_herm(const C m[6][6], int blk, int r, long Vh, double2 *A6
     for (int q = 0; q < 9; q++)
         A32[(9 * blk + q) * Vh + r] = make_float4((float)v[4 * q], (float)v[4 * q + 1], (float)v[4 * q + 2],
                                                   (float)v[4 * q + 3]);
+    for (int q = 0; q < 9; q++) {
+        __half2 a = __floats2half2_rn((float)v[4 * q], (float)v[4 * q + 1]);
+        __half2 b = __floats2half2_rn((float)v[4 * q + 2], (float)v[4 * q + 3]);
+        A16[(9 * blk + q) * Vh + r] = make_uint2(*reinterpret_cast<unsigned *>(&a), *reinterpret_cast<unsigned *>(&b));
+    }
 }
 
 struct CloverArgs {
@@ -177,6 +182,7 @@ struct CloverArgs {
     double m0, csw;
     double2 *A64[2], *Ai64[2];
     float4 *A32[2], *Ai32[2];
+    uint2 *A16[2], *Ai16[2];
     double *logdet;   // [2][Vh]
     int *singular;    // count of singular blocks
 };
@@ -208,7 +214,7 @@ __global__ void __launch_bounds__(128) k_clover(CloverArgs a)
                 A[3 + i][3 + j] = -(f * z);
             }
         for (int i = 0; i < 6; i++) A[i][i].re += 4.0 + a.m0;
-        store_herm(A, blk, r, a.g.Vh, a.A64[p], a.A32[p]);
+        store_herm(A, blk, r, a.g.Vh, a.A64[p], a.A32[p], a.A16[p]);
         double ld = 0;
         if (lu_inv6(A, Ai, &ld)) {
             atomicAdd(a.singular, 1);
@@ -216,7 +222,7 @@ __global__ void __launch_bounds__(128) k_clover(CloverArgs a)
                 for (int j = 0; j < 6; j++) Ai[i][j] = mk(0.0, 0.0);
         }
         ldsum += ld;
-        store_herm(Ai, blk, r, a.g.Vh, a.Ai64[p], a.Ai32[p]);
+        store_herm(Ai, blk, r, a.g.Vh, a.Ai64[p], a.Ai32[p], a.Ai16[p]);
     }
     a.logdet[p * (long)a.g.Vh + r] = ldsum;
 }
@@ -285,6 +291,8 @@ lqcd_status clover_build(lqcd_ctx *c, double kappa, double csw, double *ld_e, do
             LQCD_CUDA_CHECK(c, cudaMalloc(&c->Ai64[p], 36 * Vh * sizeof(double2)));
             LQCD_CUDA_CHECK(c, cudaMalloc(&c->A32[p], 18 * Vh * sizeof(float4)));
             LQCD_CUDA_CHECK(c, cudaMalloc(&c->Ai32[p], 18 * Vh * sizeof(float4)));
+            LQCD_CUDA_CHECK(c, cudaMalloc(&c->A16[p], 18 * Vh * sizeof(uint2)));
+            LQCD_CUDA_CHECK(c, cudaMalloc(&c->Ai16[p], 18 * Vh * sizeof(uint2)));
         }
     }
     void *scratch;
@@ -303,6 +311,8 @@ lqcd_status clover_build(lqcd_ctx *c, double kappa, double csw, double *ld_e, do
         a.Ai64[p] = c->Ai64[p];
         a.A32[p] = c->A32[p];
         a.Ai32[p] = c->Ai32[p];
+        a.A16[p] = c->A16[p];
+        a.Ai16[p] = c->Ai16[p];
     }
     a.logdet = logdet;
     a.singular = sing;

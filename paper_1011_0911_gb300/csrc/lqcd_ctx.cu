@@ -3,6 +3,9 @@
 #include <cstdarg>
 #include <cstring>
 
+#include <type_traits>
+
+#include "lqcd_f16s.cuh"
 #include "lqcd_internal.cuh"
 
 lqcd_status set_err(lqcd_ctx *c, lqcd_status s, const char *fmt, ...)
@@ -120,6 +123,19 @@ __global__ void k_pack(Geom g, int nsub, int nrhs, const CT *__restrict__ canon,
                 n[c * Vh] = make_double2((double)cs[2 * c], (double)cs[2 * c + 1]);
             }
         }
+    } else if (PREC == LQCD_F16S) {
+        h16s *n = (h16s *)native + half * f16s_half_units(Vh);
+        cx<float> v[12];
+        if (unpack) {
+            f16s_load<false>(n, Vh, r, v);
+            for (int c = 0; c < 12; c++) {
+                cs[2 * c] = (CT)v[c].re;
+                cs[2 * c + 1] = (CT)v[c].im;
+            }
+        } else {
+            for (int c = 0; c < 12; c++) v[c] = mk((float)cs[2 * c], (float)cs[2 * c + 1]);
+            f16s_store(n, Vh, r, v);
+        }
     } else if (PREC == LQCD_F32) {
         float4 *n = (float4 *)native + half * 6 * Vh + r;
         for (int q = 0; q < 6; q++) {
@@ -164,6 +180,51 @@ __global__ void k_conv32to64(long Vh, long nhalf, const float4 *__restrict__ in,
     }
 }
 
+// native F64 / F32 <-> native F16S, nhalf half fields
+__device__ __forceinline__ void nat_load(const double2 *f, long Vh, long r, cx<float> v[12])
+{
+    for (int c = 0; c < 12; c++) {
+        double2 a = f[c * Vh + r];
+        v[c] = mk((float)a.x, (float)a.y);
+    }
+}
+__device__ __forceinline__ void nat_load(const float4 *f, long Vh, long r, cx<float> v[12])
+{
+    for (int q = 0; q < 6; q++) {
+        float4 a = f[q * Vh + r];
+        v[2 * q] = mk(a.x, a.y);
+        v[2 * q + 1] = mk(a.z, a.w);
+    }
+}
+__device__ __forceinline__ void nat_store(double2 *f, long Vh, long r, const cx<float> v[12])
+{
+    for (int c = 0; c < 12; c++) f[c * Vh + r] = make_double2(v[c].re, v[c].im);
+}
+__device__ __forceinline__ void nat_store(float4 *f, long Vh, long r, const cx<float> v[12])
+{
+    for (int q = 0; q < 6; q++) f[q * Vh + r] = make_float4(v[2 * q].re, v[2 * q].im, v[2 * q + 1].re, v[2 * q + 1].im);
+}
+template <class T>
+__global__ void k_conv_to16s(long Vh, long nhalf, const T *__restrict__ in, h16s *out)
+{
+    long r = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    long h = blockIdx.y;
+    if (r >= Vh || h >= nhalf) return;
+    cx<float> v[12];
+    nat_load(in + h * (std::is_same<T, double2>::value ? 12 : 6) * Vh, Vh, r, v);
+    f16s_store(out + h * f16s_half_units(Vh), Vh, r, v);
+}
+template <class T>
+__global__ void k_conv_from16s(long Vh, long nhalf, const h16s *__restrict__ in, T *out)
+{
+    long r = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    long h = blockIdx.y;
+    if (r >= Vh || h >= nhalf) return;
+    cx<float> v[12];
+    f16s_load<true>(in + h * f16s_half_units(Vh), Vh, r, v);
+    nat_store(out + h * (std::is_same<T, double2>::value ? 12 : 6) * Vh, Vh, r, v);
+}
+
 }  // namespace
 
 lqcd_status convert_native(lqcd_ctx *c, lqcd_prec from, lqcd_prec to, const void *in, void *out, long nhalf)
@@ -173,6 +234,14 @@ lqcd_status convert_native(lqcd_ctx *c, lqcd_prec from, lqcd_prec to, const void
         k_conv64to32<<<grid, 256, 0, c->stream>>>(c->g.Vh, nhalf, (const double2 *)in, (float4 *)out);
     else if (from == LQCD_F32 && to == LQCD_F64)
         k_conv32to64<<<grid, 256, 0, c->stream>>>(c->g.Vh, nhalf, (const float4 *)in, (double2 *)out);
+    else if (from == LQCD_F64 && to == LQCD_F16S)
+        k_conv_to16s<double2><<<grid, 256, 0, c->stream>>>(c->g.Vh, nhalf, (const double2 *)in, (h16s *)out);
+    else if (from == LQCD_F32 && to == LQCD_F16S)
+        k_conv_to16s<float4><<<grid, 256, 0, c->stream>>>(c->g.Vh, nhalf, (const float4 *)in, (h16s *)out);
+    else if (from == LQCD_F16S && to == LQCD_F64)
+        k_conv_from16s<double2><<<grid, 256, 0, c->stream>>>(c->g.Vh, nhalf, (const h16s *)in, (double2 *)out);
+    else if (from == LQCD_F16S && to == LQCD_F32)
+        k_conv_from16s<float4><<<grid, 256, 0, c->stream>>>(c->g.Vh, nhalf, (const h16s *)in, (float4 *)out);
     else if (from == to) {
         LQCD_CUDA_CHECK(c, cudaMemcpyAsync(out, in, nhalf * native_half_bytes(c, from),
                                            cudaMemcpyDeviceToDevice, c->stream));
@@ -196,6 +265,9 @@ lqcd_status pack_field(lqcd_ctx *c, lqcd_prec p, int nsub, const void *canon, vo
     else if (p == LQCD_F32)
         k_pack<float, LQCD_F32><<<grid, 256, 0, c->stream>>>(c->g, nsub, nrhs, (const float *)canon, native,
                                                              unpack);
+    else if (p == LQCD_F16S)
+        k_pack<float, LQCD_F16S><<<grid, 256, 0, c->stream>>>(c->g, nsub, nrhs, (const float *)canon, native,
+                                                               unpack);
     else
         return set_err(c, LQCD_ERR_ARG, "pack: precision %d has no canonical form", (int)p);
     c->n_kernel_launches++;
@@ -250,6 +322,8 @@ lqcd_status lqcd_destroy(lqcd_ctx *c)
         cudaFree(c->Ai64[p]);
         cudaFree(c->A32[p]);
         cudaFree(c->Ai32[p]);
+        cudaFree(c->A16[p]);
+        cudaFree(c->Ai16[p]);
     }
     cudaFree(c->red);
     cudaFree(c->red_out);
@@ -332,7 +406,7 @@ lqcd_status lqcd_unpack(lqcd_ctx *c, lqcd_prec p, int nsub, const void *native, 
 lqcd_status lqcd_apply_Dhat_native(lqcd_ctx *c, lqcd_prec p, const void *in, void *out, int nrhs)
 {
     if (!c || !in || !out || nrhs < 1) return set_err(c, LQCD_ERR_ARG, "bad argument");
-    if (p != LQCD_F64 && p != LQCD_F32) return set_err(c, LQCD_ERR_ARG, "precision %d", (int)p);
+    if (p != LQCD_F64 && p != LQCD_F32 && p != LQCD_F16S) return set_err(c, LQCD_ERR_ARG, "precision %d", (int)p);
     void *tmp;
     LQCD_TRY(ws_get(c, WS_TMP_O, native_half_bytes(c, p) * nrhs, &tmp));
     return dirac_dhat(c, p, in, out, tmp, nrhs);
@@ -341,14 +415,14 @@ lqcd_status lqcd_apply_Dhat_native(lqcd_ctx *c, lqcd_prec p, const void *in, voi
 lqcd_status lqcd_apply_D_native(lqcd_ctx *c, lqcd_prec p, const void *in, void *out, int nrhs)
 {
     if (!c || !in || !out || nrhs < 1) return set_err(c, LQCD_ERR_ARG, "bad argument");
-    if (p != LQCD_F64 && p != LQCD_F32) return set_err(c, LQCD_ERR_ARG, "precision %d", (int)p);
+    if (p != LQCD_F64 && p != LQCD_F32 && p != LQCD_F16S) return set_err(c, LQCD_ERR_ARG, "precision %d", (int)p);
     return dirac_D(c, p, in, out, nrhs);
 }
 
 lqcd_status lqcd_apply_Dhat(lqcd_ctx *c, lqcd_prec p, const void *in, void *out, int nrhs)
 {
     if (!c || !in || !out || nrhs < 1) return set_err(c, LQCD_ERR_ARG, "bad argument");
-    if (p != LQCD_F64 && p != LQCD_F32) return set_err(c, LQCD_ERR_ARG, "precision %d", (int)p);
+    if (p != LQCD_F64 && p != LQCD_F32 && p != LQCD_F16S) return set_err(c, LQCD_ERR_ARG, "precision %d", (int)p);
     size_t hb = native_half_bytes(c, p) * nrhs;
     void *a, *b;
     LQCD_TRY(ws_get(c, WS_PACK_IN, hb, &a));
@@ -361,7 +435,7 @@ lqcd_status lqcd_apply_Dhat(lqcd_ctx *c, lqcd_prec p, const void *in, void *out,
 lqcd_status lqcd_apply_D(lqcd_ctx *c, lqcd_prec p, const void *in, void *out, int nrhs)
 {
     if (!c || !in || !out || nrhs < 1) return set_err(c, LQCD_ERR_ARG, "bad argument");
-    if (p != LQCD_F64 && p != LQCD_F32) return set_err(c, LQCD_ERR_ARG, "precision %d", (int)p);
+    if (p != LQCD_F64 && p != LQCD_F32 && p != LQCD_F16S) return set_err(c, LQCD_ERR_ARG, "precision %d", (int)p);
     size_t fb = native_half_bytes(c, p) * 2 * nrhs;
     void *a, *b;
     LQCD_TRY(ws_get(c, WS_PACK_IN, fb, &a));

@@ -14,6 +14,9 @@
 // h = psi_up -+ e_mu psi_lo: the upper half of the result is h and the lower
 // half is -+ e_mu^dag h.  Each hop therefore multiplies only two colour
 // vectors by the link (spin projection), 1320 flops per output site.
+#include <type_traits>
+
+#include "lqcd_f16s.cuh"
 #include "lqcd_internal.cuh"
 #include "lqcd_tune.h"
 
@@ -73,6 +76,22 @@ __device__ __forceinline__ void store_spinor(float4 *__restrict__ f, long Vh, in
     }
 }
 
+// FP16 + per-site scale storage (arithmetic in FP32)
+__device__ __forceinline__ void load_spinor(const h16s *__restrict__ f, long Vh, int r, Spinor<float> &o)
+{
+    cx<float> v[12];
+    f16s_load<true>(f, Vh, r, v);
+#pragma unroll
+    for (int c = 0; c < 12; c++) o.s[c / 3][c % 3] = v[c];
+}
+__device__ __forceinline__ void store_spinor(h16s *__restrict__ f, long Vh, int r, const Spinor<float> &o)
+{
+    cx<float> v[12];
+#pragma unroll
+    for (int c = 0; c < 12; c++) v[c] = o.s[c / 3][c % 3];
+    f16s_store(f, Vh, r, v);
+}
+
 // SU(3) link of parity p, direction mu, at rank r
 __device__ __forceinline__ void load_link(const double2 *__restrict__ U, long Vh, int p, int mu, int r,
                                           cx<double> u[3][3])
@@ -99,6 +118,12 @@ __device__ __forceinline__ void load_link(const float4 *__restrict__ U, long Vh,
     u[2][0] = conjx(u[0][1] * u[1][2] - u[0][2] * u[1][1]);
     u[2][1] = conjx(u[0][2] * u[1][0] - u[0][0] * u[1][2]);
     u[2][2] = conjx(u[0][0] * u[1][1] - u[0][1] * u[1][0]);
+}
+
+__device__ __forceinline__ void load_link(const uint2 *__restrict__ U, long Vh, int p, int mu, int r,
+                                          cx<float> u[3][3])
+{
+    f16s_link(U, Vh, p, mu, r, u);
 }
 
 // packed Hermitian 6x6 pair: per block 6 real diagonal entries then the 15
@@ -137,6 +162,16 @@ __device__ __forceinline__ void load_herm(const float4 *__restrict__ A, long Vh,
         v[4 * q + 2] = t.z;
         v[4 * q + 3] = t.w;
     }
+#pragma unroll
+    for (int i = 0; i < 6; i++) h.d[i] = v[i];
+#pragma unroll
+    for (int i = 0; i < 15; i++) h.o[i] = mk(v[6 + 2 * i], v[7 + 2 * i]);
+}
+
+__device__ __forceinline__ void load_herm(const uint2 *__restrict__ A, long Vh, int r, int blk, Herm6<float> &h)
+{
+    float v[36];
+    f16s_clover(A, Vh, r, blk, v);
 #pragma unroll
     for (int i = 0; i < 6; i++) h.d[i] = v[i];
 #pragma unroll
@@ -427,7 +462,7 @@ lqcd_status launch_hop(lqcd_ctx *c, int p_out, const SP *in_other, long in_rs, c
     a.out_rs = out_rs;
     a.U = U;
     a.clov = clov;
-    const int prec = sizeof(R) == 8 ? 0 : 1;
+    const int prec = sizeof(R) == 8 ? 0 : (std::is_same<SP, h16s>::value ? 2 : 1);
     std::string key = tune_key(c, "k_hop", MODE, prec, nrhs);
     TuneChoice tc;
     if (!tune_lookup(key, &tc)) {
@@ -484,6 +519,17 @@ lqcd_status dirac_dhat(lqcd_ctx *c, lqcd_prec p, const void *in, void *out, void
             c, 0, t, rs, i, rs, o, rs, c->U32, c->A32[0], nrhs)));
         return LQCD_OK;
     }
+    if (p == LQCD_F16S) {
+        const long rs = f16s_half_units(Vh);
+        auto *i = (const h16s *)in;
+        auto *o = (h16s *)out;
+        auto *t = (h16s *)tmp_o;
+        LQCD_TRY((launch_hop<float, h16s, uint2, uint2, MODE_DHAT1>(c, 1, i, rs, nullptr, 0, t, rs, c->U16,
+                                                                    c->Ai16[1], nrhs)));
+        LQCD_TRY((launch_hop<float, h16s, uint2, uint2, MODE_DHAT2>(c, 0, t, rs, i, rs, o, rs, c->U16, c->A16[0],
+                                                                    nrhs)));
+        return LQCD_OK;
+    }
     return set_err(c, LQCD_ERR_ARG, "precision %d not supported for Dhat", (int)p);
 }
 
@@ -508,6 +554,15 @@ lqcd_status dirac_D(lqcd_ctx *c, lqcd_prec p, const void *in, void *out, int nrh
         for (int po = 0; po < 2; po++)
             LQCD_TRY((launch_hop<float, float4, float4, float4, MODE_D>(
                 c, po, i + (1 - po) * h, rs, i + po * h, rs, o + po * h, rs, c->U32, c->A32[po], nrhs)));
+        return LQCD_OK;
+    }
+    if (p == LQCD_F16S) {
+        const long h = f16s_half_units(Vh), rs = 2 * h;
+        auto *i = (const h16s *)in;
+        auto *o = (h16s *)out;
+        for (int po = 0; po < 2; po++)
+            LQCD_TRY((launch_hop<float, h16s, uint2, uint2, MODE_D>(c, po, i + (1 - po) * h, rs, i + po * h, rs,
+                                                                    o + po * h, rs, c->U16, c->A16[po], nrhs)));
         return LQCD_OK;
     }
     return set_err(c, LQCD_ERR_ARG, "precision %d not supported for D", (int)p);

@@ -101,6 +101,7 @@ struct lqcd_ctx {
     // clover term: A and A^-1 for both parities, packed Hermitian 6x6 pairs
     double2 *A64[2] = {nullptr, nullptr}, *Ai64[2] = {nullptr, nullptr};  // [36][Vh]
     float4 *A32[2] = {nullptr, nullptr}, *Ai32[2] = {nullptr, nullptr};   // [18][Vh]
+    uint2 *A16[2] = {nullptr, nullptr}, *Ai16[2] = {nullptr, nullptr};    // [18][Vh], FP16
     bool have_clover = false;
     double kappa = 0, csw = 0;
     // device scratch for reductions

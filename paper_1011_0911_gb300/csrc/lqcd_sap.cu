@@ -13,6 +13,7 @@
 // that spans a whole lattice direction keeps the wrapped hop of that direction.
 #include <algorithm>
 
+#include "lqcd_f16s.cuh"
 #include "lqcd_internal.cuh"
 
 namespace {
@@ -25,19 +26,33 @@ struct BlkGeom {
     int wrap[4];     // block spans the whole direction
 };
 
-template <class R>
-struct SapPT;
+// storage per precision tag: arithmetic type, spinor unit, link and clover
+// element types, and the length of one native half field in spinor units
+template <int P>
+struct SapT;
 template <>
-struct SapPT<double> {
+struct SapT<LQCD_F64> {
+    using R = double;
     using SP = double2;
     using LK = double2;
     using CL = double2;
+    static __host__ __device__ long half(long Vh) { return 12 * Vh; }
 };
 template <>
-struct SapPT<float> {
+struct SapT<LQCD_F32> {
+    using R = float;
     using SP = float4;
     using LK = float4;
     using CL = float4;
+    static __host__ __device__ long half(long Vh) { return 6 * Vh; }
+};
+template <>
+struct SapT<LQCD_F16S> {
+    using R = float;
+    using SP = h16s;
+    using LK = uint2;
+    using CL = uint2;
+    static __host__ __device__ long half(long Vh) { return f16s_half_units(Vh); }
 };
 
 // global native accessors (duplicated minimal forms of the stencil loaders)
@@ -96,6 +111,28 @@ __device__ __forceinline__ void glink(const float4 *U, long Vh, int p, int mu, l
     u[2][0] = conjx(u[0][1] * u[1][2] - u[0][2] * u[1][1]);
     u[2][1] = conjx(u[0][2] * u[1][0] - u[0][0] * u[1][2]);
     u[2][2] = conjx(u[0][0] * u[1][1] - u[0][1] * u[1][0]);
+}
+__device__ __forceinline__ void gload(const h16s *f, long Vh, long r, cx<float> v[12]) { f16s_load<false>(f, Vh, r, v); }
+__device__ __forceinline__ void gadd(h16s *f, long Vh, long r, const cx<float> v[12])
+{
+    cx<float> t[12];
+    f16s_load<false>(f, Vh, r, t);
+#pragma unroll
+    for (int c = 0; c < 12; c++) t[c] = t[c] + v[c];
+    f16s_store(f, Vh, r, t);
+}
+__device__ __forceinline__ void glink(const uint2 *U, long Vh, int p, int mu, long r, cx<float> u[3][3])
+{
+    f16s_link(U, Vh, p, mu, r, u);
+}
+__device__ __forceinline__ void gclov(const uint2 *A, long Vh, long r, int blk, float d[6], cx<float> o[15])
+{
+    float v[36];
+    f16s_clover(A, Vh, r, blk, v);
+#pragma unroll
+    for (int i = 0; i < 6; i++) d[i] = v[i];
+#pragma unroll
+    for (int i = 0; i < 15; i++) o[i] = mk(v[6 + 2 * i], v[7 + 2 * i]);
 }
 __device__ __forceinline__ void gclov(const double2 *A, long Vh, long r, int blk, double d[6], cx<double> o[15])
 {
@@ -312,17 +349,17 @@ __device__ __forceinline__ void block_reduce2(R &a, R &b, R &c, R *red)
     }
 }
 
-template <class R>
+template <int P>
 struct SapArgs {
     Geom g;
     BlkGeom B;
     const int *blocks;   // block ids of this colour
-    typename SapPT<R>::SP *r;        // native full fields (residual; the block's part is replaced)
-    typename SapPT<R>::SP *psi;      // native full fields (updated)
-    typename SapPT<R>::SP *delta;    // native full fields: chi of the blocks of this colour
-    long fstride;                    // elements between the fields of consecutive right-hand sides
-    const typename SapPT<R>::LK *U;
-    const typename SapPT<R>::CL *Ae, *Aio;   // A on even sites, A^-1 on odd sites
+    typename SapT<P>::SP *r;        // native full fields (residual; the block's part is replaced)
+    typename SapT<P>::SP *psi;      // native full fields (updated)
+    typename SapT<P>::SP *delta;    // native full fields: chi of the blocks of this colour
+    long fstride;                    // spinor units between the fields of consecutive right-hand sides
+    const typename SapT<P>::LK *U;
+    const typename SapT<P>::CL *Ae, *Aio;   // A on even sites, A^-1 on odd sites
     int nmr;
 };
 
@@ -337,11 +374,13 @@ __device__ __forceinline__ void gstore(float4 *f, long Vh, long r, const cx<floa
     for (int q = 0; q < 6; q++)
         f[q * Vh + r] = make_float4(v[2 * q].re, v[2 * q].im, v[2 * q + 1].re, v[2 * q + 1].im);
 }
+__device__ __forceinline__ void gstore(h16s *f, long Vh, long r, const cx<float> v[12]) { f16s_store(f, Vh, r, v); }
 
-template <class R>
-__global__ void __launch_bounds__(128) k_sap_block(SapArgs<R> a)
+template <int P>
+__global__ void __launch_bounds__(128) k_sap_block(SapArgs<P> a)
 {
-    using SP = typename SapPT<R>::SP;
+    using R = typename SapT<P>::R;
+    using SP = typename SapT<P>::SP;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const BlkGeom &B = a.B;
     const int nh = B.nh;
@@ -352,7 +391,7 @@ __global__ void __launch_bounds__(128) k_sap_block(SapArgs<R> a)
     cx<R> *ro = to + 12 * nh;
     R *red = (R *)(ro + 12 * nh);
     const long Vh = a.g.Vh;
-    const long half = (sizeof(R) == 8 ? 12 : 6) * Vh;
+    const long half = SapT<P>::half(Vh);
     const long foff = blockIdx.y * a.fstride;
     SP *r_e = a.r + foff, *r_o = a.r + foff + half;
     SP *psi_e = a.psi + foff, *psi_o = a.psi + foff + half;
@@ -598,18 +637,99 @@ __device__ __forceinline__ void s_half(const cx<float> acc[12], int h, cx<float>
     for (int i = 0; i < 6; i++) out[i] = h ? acc[6 + i] : acc[i];
 }
 
-__global__ void __launch_bounds__(2 * SAPS_NH, 1) k_sap_block_s(SapArgs<float> a)
+// staging loads of the resident kernel: one 4-real word of a link row pair or
+// of the clover term, and one site of a residual field
+__device__ __forceinline__ float4 stage4(const float4 *p) { return __ldg(p); }
+__device__ __forceinline__ float4 stage4(const uint2 *p)
 {
+    uint2 t = __ldg(p);
+    cx<float> a = f16s_h2c(t.x, 1.f), b = f16s_h2c(t.y, 1.f);
+    return make_float4(a.re, a.im, b.re, b.im);
+}
+__device__ __forceinline__ void stage_site(const float4 *f, long Vh, long r, float4 o[6])
+{
+#pragma unroll
+    for (int q = 0; q < 6; q++) o[q] = f[q * Vh + r];
+}
+__device__ __forceinline__ void stage_site(const h16s *f, long Vh, long r, float4 o[6])
+{
+    cx<float> v[12];
+    f16s_load<false>(f, Vh, r, v);
+#pragma unroll
+    for (int q = 0; q < 6; q++) o[q] = make_float4(v[2 * q].re, v[2 * q].im, v[2 * q + 1].re, v[2 * q + 1].im);
+}
+// chirality half h (components 6h .. 6h+5) of site r.  The F16S forms are
+// called by both threads of a site pair (lanes 2t, 2t+1) together: the pair
+// agrees on the site's scale through a lane shuffle.
+__device__ __forceinline__ void half_load(const float4 *f, long Vh, long r, int h, cx<float> v[6])
+{
+#pragma unroll
+    for (int q = 0; q < 3; q++) {
+        float4 a = f[(3 * h + q) * Vh + r];
+        v[2 * q] = mk(a.x, a.y);
+        v[2 * q + 1] = mk(a.z, a.w);
+    }
+}
+__device__ __forceinline__ void half_store(float4 *f, long Vh, long r, int h, const cx<float> v[6])
+{
+#pragma unroll
+    for (int q = 0; q < 3; q++) f[(3 * h + q) * Vh + r] = make_float4(v[2 * q].re, v[2 * q].im, v[2 * q + 1].re, v[2 * q + 1].im);
+}
+__device__ __forceinline__ void half_load(const h16s *f, long Vh, long r, int h, cx<float> v[6])
+{
+    // h = 0: components 0..3 (uint4 0) and 4, 5 (low half of uint4 1);
+    // h = 1: components 6, 7 (high half of uint4 1) and 8..11 (uint4 2)
+    const uint4 *q = reinterpret_cast<const uint4 *>(f);
+    const float sc = f16s_scales(f, Vh)[r];
+    const uint2 mid = reinterpret_cast<const uint2 *>(q + Vh + r)[h];
+    const uint4 end = q[(h ? 2 : 0) * Vh + r];
+    const cx<float> a0 = f16s_h2c(end.x, sc), a1 = f16s_h2c(end.y, sc), a2 = f16s_h2c(end.z, sc),
+                    a3 = f16s_h2c(end.w, sc), m0 = f16s_h2c(mid.x, sc), m1 = f16s_h2c(mid.y, sc);
+    v[0] = h ? m0 : a0;
+    v[1] = h ? m1 : a1;
+    v[2] = h ? a0 : a2;
+    v[3] = h ? a1 : a3;
+    v[4] = h ? a2 : m0;
+    v[5] = h ? a3 : m1;
+}
+__device__ __forceinline__ void half_store(h16s *f, long Vh, long r, int h, const cx<float> v[6])
+{
+    float m = 0.f;
+#pragma unroll
+    for (int i = 0; i < 6; i++) m = fmaxf(m, fmaxf(fabsf(v[i].re), fabsf(v[i].im)));
+    m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 1));
+    const float inv = m > 0.f ? 1.f / m : 0.f;
+    uint4 *q = reinterpret_cast<uint4 *>(f);
+    const cx<float> e0 = h ? v[2] : v[0], e1 = h ? v[3] : v[1], e2 = h ? v[4] : v[2], e3 = h ? v[5] : v[3];
+    const cx<float> m0 = h ? v[0] : v[4], m1 = h ? v[1] : v[5];
+    q[(h ? 2 : 0) * Vh + r] = make_uint4(f16s_c2h(e0, inv), f16s_c2h(e1, inv), f16s_c2h(e2, inv), f16s_c2h(e3, inv));
+    reinterpret_cast<uint2 *>(q + Vh + r)[h] = make_uint2(f16s_c2h(m0, inv), f16s_c2h(m1, inv));
+    if (h == 0) f16s_scales(f, Vh)[r] = m;
+}
+template <class SP>
+__device__ __forceinline__ void half_add(SP *f, long Vh, long r, int h, const cx<float> v[6])
+{
+    cx<float> t[6];
+    half_load(f, Vh, r, h, t);
+#pragma unroll
+    for (int i = 0; i < 6; i++) t[i] = t[i] + v[i];
+    half_store(f, Vh, r, h, t);
+}
+
+template <int P>
+__global__ void __launch_bounds__(2 * SAPS_NH, 1) k_sap_block_s(SapArgs<P> a)
+{
+    using SP = typename SapT<P>::SP;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SapSmem &S = *reinterpret_cast<SapSmem *>(smem_raw);
     const BlkGeom &B = a.B;
     const int nh = B.nh;
     const long Vh = a.g.Vh;
-    const long half = 6 * Vh;
+    const long half = SapT<P>::half(Vh);
     const long foff = blockIdx.y * a.fstride;
-    float4 *r_e = a.r + foff, *r_o = a.r + foff + half;
-    float4 *psi_e = a.psi + foff, *psi_o = a.psi + foff + half;
-    float4 *d_e = a.delta + foff, *d_o = a.delta + foff + half;
+    SP *r_e = a.r + foff, *r_o = a.r + foff + half;
+    SP *psi_e = a.psi + foff, *psi_o = a.psi + foff + half;
+    SP *d_e = a.delta + foff, *d_o = a.delta + foff + half;
     int org[4];
     {
         int t = a.blocks[blockIdx.x];
@@ -634,17 +754,19 @@ __global__ void __launch_bounds__(2 * SAPS_NH, 1) k_sap_block_s(SapArgs<float> a
 #pragma unroll
         for (int mu = 0; mu < 4; mu++)
 #pragma unroll
-            for (int q = 0; q < 3; q++) S.U[mu][q][ls] = __ldg(a.U + ((long)(par * 4 + mu) * 3 + q) * Vh + s.grank);
-        const float4 *A = par ? a.Aio : a.Ae;
+            for (int q = 0; q < 3; q++) S.U[mu][q][ls] = stage4(a.U + ((long)(par * 4 + mu) * 3 + q) * Vh + s.grank);
+        const typename SapT<P>::CL *A = par ? a.Aio : a.Ae;
 #pragma unroll
-        for (int q = 0; q < 18; q++) S.A[q][ls] = __ldg(A + q * Vh + s.grank);
+        for (int q = 0; q < 18; q++) S.A[q][ls] = stage4(A + q * Vh + s.grank);
+        float4 site[6];
+        stage_site(par ? r_o : r_e, Vh, s.grank, site);
         if (par) {
 #pragma unroll
-            for (int q = 0; q < 6; q++) S.ro[q][t] = r_o[q * Vh + s.grank];
+            for (int q = 0; q < 6; q++) S.ro[q][t] = site[q];
         } else {
 #pragma unroll
             for (int q = 0; q < 6; q++) {
-                S.rho[q][t] = r_e[q * Vh + s.grank];
+                S.rho[q][t] = site[q];
                 S.chi[q][t] = make_float4(0.f, 0.f, 0.f, 0.f);
             }
         }
@@ -774,36 +896,39 @@ __global__ void __launch_bounds__(2 * SAPS_NH, 1) k_sap_block_s(SapArgs<float> a
             v[2 * q + 1] = mk(x.z + 0.5f * ah[2 * q + 1].re, x.w + 0.5f * ah[2 * q + 1].im);
         }
         s_clover_half(S, lso, h, v, w);
+        cx<float> ce[6], re[6], zero[6];
 #pragma unroll
         for (int q = 0; q < 3; q++) {
-            const int c = 3 * h + q;
-            float4 co = make_float4(w[2 * q].re, w[2 * q].im, w[2 * q + 1].re, w[2 * q + 1].im);
-            float4 po = psi_o[c * Vh + so.grank];
-            psi_o[c * Vh + so.grank] = make_float4(po.x + co.x, po.y + co.y, po.z + co.z, po.w + co.w);
-            d_o[c * Vh + so.grank] = co;
-            r_o[c * Vh + so.grank] = make_float4(0.f, 0.f, 0.f, 0.f);
-            float4 ce = S.chi[c][t];
-            float4 pe = psi_e[c * Vh + se.grank];
-            psi_e[c * Vh + se.grank] = make_float4(pe.x + ce.x, pe.y + ce.y, pe.z + ce.z, pe.w + ce.w);
-            d_e[c * Vh + se.grank] = ce;
-            r_e[c * Vh + se.grank] = S.rho[c][t];
+            const float4 c4 = S.chi[3 * h + q][t], r4 = S.rho[3 * h + q][t];
+            ce[2 * q] = mk(c4.x, c4.y);
+            ce[2 * q + 1] = mk(c4.z, c4.w);
+            re[2 * q] = mk(r4.x, r4.y);
+            re[2 * q + 1] = mk(r4.z, r4.w);
+            zero[2 * q] = zero[2 * q + 1] = mk(0.f, 0.f);
         }
+        half_add(psi_o, Vh, so.grank, h, w);
+        half_store(d_o, Vh, so.grank, h, w);
+        half_store(r_o, Vh, so.grank, h, zero);
+        half_add(psi_e, Vh, se.grank, h, ce);
+        half_store(d_e, Vh, se.grank, h, ce);
+        half_store(r_e, Vh, se.grank, h, re);
     }
 }
 
 // r(x) -= sum of the hops into x from neighbours y that lie in another block
 // of colour col (delta holds chi there).  One thread per (site, rhs).
-template <class R>
-__global__ void __launch_bounds__(128) k_sap_face(SapArgs<R> a, int col)
+template <int P>
+__global__ void __launch_bounds__(128) k_sap_face(SapArgs<P> a, int col)
 {
-    using SP = typename SapPT<R>::SP;
+    using R = typename SapT<P>::R;
+    using SP = typename SapT<P>::SP;
     const BlkGeom &B = a.B;
     long i = blockIdx.x * (long)blockDim.x + threadIdx.x;   // 0 .. V-1: parity-major
     if (i >= 2L * a.g.Vh) return;
     const long Vh = a.g.Vh;
     const int par = i >= Vh;
     const long rk = par ? i - Vh : i;
-    const long half = (sizeof(R) == 8 ? 12 : 6) * Vh;
+    const long half = SapT<P>::half(Vh);
     const long foff = blockIdx.y * a.fstride;
     int x[4];
     rank_coords(a.g, par, (int)rk, x);
@@ -906,70 +1031,76 @@ lqcd_status get_plan(lqcd_ctx *c, const int bs[4], SapPlan **out)
     return LQCD_OK;
 }
 
-template <class R>
-lqcd_status sap_run(lqcd_ctx *c, const SapPlan &P, int ncy, int nmr, const void *eta, void *psi, void *r,
+template <int P>
+lqcd_status sap_run(lqcd_ctx *c, const SapPlan &P_, int ncy, int nmr, const void *eta, void *psi, void *r,
                     void *delta, int nrhs)
 {
-    using SP = typename SapPT<R>::SP;
-    const lqcd_prec prec = sizeof(R) == 8 ? LQCD_F64 : LQCD_F32;
-    const size_t fb = 2 * native_half_bytes(c, prec);
-    size_t smem = 5 * 12 * P.B.nh * sizeof(cx<R>) + 3 * 32 * sizeof(R);
+    using T = SapT<P>;
+    using R = typename T::R;
+    using SP = typename T::SP;
+    const SapPlan &Pl = P_;
+    const size_t fb = 2 * native_half_bytes(c, (lqcd_prec)P);
+    size_t smem = 5 * 12 * Pl.B.nh * sizeof(cx<R>) + 3 * 32 * sizeof(R);
     static bool attr_set = false;
     if (!attr_set) {
-        cudaFuncSetAttribute(k_sap_block<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        cudaFuncSetAttribute(k_sap_block<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         attr_set = true;
     }
     if (smem > 200 * 1024) return set_err(c, LQCD_ERR_ARG, "SAP block needs %zu bytes of shared memory", smem);
     if (nrhs < 1 || nrhs > 65535) return set_err(c, LQCD_ERR_ARG, "SAP nrhs=%d", nrhs);
     LQCD_CUDA_CHECK(c, cudaMemsetAsync(psi, 0, fb * nrhs, c->stream));
     LQCD_CUDA_CHECK(c, cudaMemcpyAsync(r, eta, fb * nrhs, cudaMemcpyDeviceToDevice, c->stream));
-    SapArgs<R> a;
+    SapArgs<P> a;
     a.g = c->g;
-    a.B = P.B;
+    a.B = Pl.B;
     a.r = (SP *)r;
     a.psi = (SP *)psi;
     a.delta = (SP *)delta;
-    a.fstride = 2 * (sizeof(R) == 8 ? 12 : 6) * (long)c->g.Vh;
-    if (sizeof(R) == 8) {
-        a.U = (const typename SapPT<R>::LK *)c->U64;
-        a.Ae = (const typename SapPT<R>::CL *)c->A64[0];
-        a.Aio = (const typename SapPT<R>::CL *)c->Ai64[1];
+    a.fstride = 2 * T::half(c->g.Vh);
+    if constexpr (P == LQCD_F64) {
+        a.U = c->U64;
+        a.Ae = c->A64[0];
+        a.Aio = c->Ai64[1];
+    } else if constexpr (P == LQCD_F32) {
+        a.U = c->U32;
+        a.Ae = c->A32[0];
+        a.Aio = c->Ai32[1];
     } else {
-        a.U = (const typename SapPT<R>::LK *)c->U32;
-        a.Ae = (const typename SapPT<R>::CL *)c->A32[0];
-        a.Aio = (const typename SapPT<R>::CL *)c->Ai32[1];
+        a.U = c->U16;
+        a.Ae = c->A16[0];
+        a.Aio = c->Ai16[1];
     }
     a.nmr = nmr;
-    int threads = std::min(128, P.B.nh);
-    // FP32 with blocks of <= 128 sites per parity (whole warps of site pairs):
-    // the shared-memory resident kernel
+    int threads = std::min(128, Pl.B.nh);
+    // FP32 / F16S with blocks of <= 128 sites per parity (whole warps of site
+    // pairs): the shared-memory resident kernel
     bool resident = false;
-    if constexpr (sizeof(R) == 4) {
+    if constexpr (P != LQCD_F64) {
         static bool attr_s = false;
         if (!attr_s) {
-            cudaFuncSetAttribute(k_sap_block_s, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(SapSmem));
+            cudaFuncSetAttribute(k_sap_block_s<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(SapSmem));
             attr_s = true;
         }
-        resident = P.B.nh <= SAPS_NH && (2 * P.B.nh) % 32 == 0 && !sap_force_generic();
+        resident = Pl.B.nh <= SAPS_NH && (2 * Pl.B.nh) % 32 == 0 && !sap_force_generic();
     }
     // the residual is not needed after the last sweep
-    int last_col = P.count[1] > 0 ? 1 : 0;
+    int last_col = Pl.count[1] > 0 ? 1 : 0;
     for (int cyc = 0; cyc < ncy; cyc++)
         for (int col = 0; col < 2; col++) {
-            if (P.count[col] == 0) continue;
-            a.blocks = P.blocks_dev + (col == 0 ? 0 : P.count[0]);
-            if constexpr (sizeof(R) == 4) {
+            if (Pl.count[col] == 0) continue;
+            a.blocks = Pl.blocks_dev + (col == 0 ? 0 : Pl.count[0]);
+            if constexpr (P != LQCD_F64) {
                 if (resident)
-                    k_sap_block_s<<<dim3(P.count[col], nrhs), 2 * P.B.nh, sizeof(SapSmem), c->stream>>>(a);
+                    k_sap_block_s<P><<<dim3(Pl.count[col], nrhs), 2 * Pl.B.nh, sizeof(SapSmem), c->stream>>>(a);
                 else
-                    k_sap_block<R><<<dim3(P.count[col], nrhs), threads, smem, c->stream>>>(a);
+                    k_sap_block<P><<<dim3(Pl.count[col], nrhs), threads, smem, c->stream>>>(a);
             } else {
-                k_sap_block<R><<<dim3(P.count[col], nrhs), threads, smem, c->stream>>>(a);
+                k_sap_block<P><<<dim3(Pl.count[col], nrhs), threads, smem, c->stream>>>(a);
             }
             c->n_kernel_launches++;
             LQCD_LAUNCH_CHECK(c);
             if (cyc == ncy - 1 && col == last_col) continue;
-            k_sap_face<R><<<dim3(div_up(2L * c->g.Vh, 128), nrhs), 128, 0, c->stream>>>(a, col);
+            k_sap_face<P><<<dim3(div_up(2L * c->g.Vh, 128), nrhs), 128, 0, c->stream>>>(a, col);
             c->n_kernel_launches++;
             LQCD_LAUNCH_CHECK(c);
         }
@@ -1023,8 +1154,9 @@ lqcd_status sap_apply(lqcd_ctx *c, const lqcd_sap_params *sp, const void *eta, v
     const size_t fb = 2 * native_half_bytes(c, sp->prec);
     LQCD_TRY(ws_get(c, WS_SAP_R, 2 * fb * nrhs, &r));
     void *delta = (char *)r + fb * nrhs;
-    if (sp->prec == LQCD_F64) return sap_run<double>(c, *P, sp->ncy, sp->nmr, eta, psi, r, delta, nrhs);
-    if (sp->prec == LQCD_F32) return sap_run<float>(c, *P, sp->ncy, sp->nmr, eta, psi, r, delta, nrhs);
+    if (sp->prec == LQCD_F64) return sap_run<LQCD_F64>(c, *P, sp->ncy, sp->nmr, eta, psi, r, delta, nrhs);
+    if (sp->prec == LQCD_F32) return sap_run<LQCD_F32>(c, *P, sp->ncy, sp->nmr, eta, psi, r, delta, nrhs);
+    if (sp->prec == LQCD_F16S) return sap_run<LQCD_F16S>(c, *P, sp->ncy, sp->nmr, eta, psi, r, delta, nrhs);
     return set_err(c, LQCD_ERR_ARG, "SAP precision %d not supported", (int)sp->prec);
 }
 
@@ -1043,7 +1175,7 @@ extern "C" lqcd_status lqcd_sap(lqcd_ctx *c, const lqcd_sap_params *sp, const do
 {
     if (!c || !sp || !eta || !psi) return set_err(c, LQCD_ERR_ARG, "null argument");
     lqcd_prec p = sp->prec;
-    if (p != LQCD_F64 && p != LQCD_F32) return set_err(c, LQCD_ERR_ARG, "SAP precision %d", (int)p);
+    if (p != LQCD_F64 && p != LQCD_F32 && p != LQCD_F16S) return set_err(c, LQCD_ERR_ARG, "SAP precision %d", (int)p);
     size_t fb = 2 * native_half_bytes(c, p);
     size_t fb64 = 2 * native_half_bytes(c, LQCD_F64);
     void *a, *b, *t;

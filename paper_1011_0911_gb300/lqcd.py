@@ -140,8 +140,8 @@ def _ptr(t: torch.Tensor):
 
 
 def _dtype(prec):
-    # F16S has no canonical form: such calls pass through and the library rejects them
-    return {F64: torch.complex128, F32: torch.complex64}.get(prec, torch.complex128)
+    # canonical fields of the F16S operators are complex float
+    return {F64: torch.complex128, F32: torch.complex64, F16S: torch.complex64}.get(prec, torch.complex128)
 
 
 def sap_params(bs=(4, 4, 4, 4), ncy=4, nmr=5, prec=F64) -> SapParams:

@@ -12,7 +12,7 @@ from paper_1011_0911_gb300 import lqcd, synth
 from tests import util
 
 # relative-error bounds per application (float storage vs FP64 oracle)
-TOL = {lqcd.F64: 1e-13, lqcd.F32: 1e-6}
+TOL = {lqcd.F64: 1e-13, lqcd.F32: 1e-6, lqcd.F16S: 3e-3}
 
 
 @functools.lru_cache(maxsize=8)
@@ -40,7 +40,7 @@ def to_gpu(x: np.ndarray, prec=lqcd.F64) -> torch.Tensor:
 
 def rounded(x: np.ndarray, prec) -> np.ndarray:
     """x as the library stores it at precision prec, back in complex128."""
-    if prec == lqcd.F32:
+    if prec in (lqcd.F32, lqcd.F16S):
         return x.astype(np.complex64).astype(np.complex128)
     return x
 

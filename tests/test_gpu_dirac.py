@@ -33,7 +33,7 @@ def test_clover_and_inverse(pair):
             assert relerr(out, ref.reshape(x.shape)) < 1e-14
 
 
-@pytest.mark.parametrize("prec", [lqcd.F64, lqcd.F32], ids=["f64", "f32"])
+@pytest.mark.parametrize("prec", [lqcd.F64, lqcd.F32, lqcd.F16S], ids=["f64", "f32", "f16s"])
 def test_D(pair, prec):
     P = pair
     psi = rounded(synth.gaussian_spinor(P.V, 3), prec)
@@ -41,7 +41,7 @@ def test_D(pair, prec):
     assert relerr(out, P.o.D(psi)) < TOL[prec]
 
 
-@pytest.mark.parametrize("prec", [lqcd.F64, lqcd.F32], ids=["f64", "f32"])
+@pytest.mark.parametrize("prec", [lqcd.F64, lqcd.F32, lqcd.F16S], ids=["f64", "f32", "f16s"])
 def test_Dhat(pair, prec):
     P = pair
     pe = rounded(synth.gaussian_spinor(P.Vh, 4), prec)
@@ -49,7 +49,7 @@ def test_Dhat(pair, prec):
     assert relerr(out, P.o.Dhat(pe)) < TOL[prec]
 
 
-@pytest.mark.parametrize("prec", [lqcd.F64, lqcd.F32], ids=["f64", "f32"])
+@pytest.mark.parametrize("prec", [lqcd.F64, lqcd.F32, lqcd.F16S], ids=["f64", "f32", "f16s"])
 @pytest.mark.parametrize("nrhs", [3, 12])
 def test_multi_rhs_matches_single(pair, prec, nrhs):
     """The multi-RHS launch shape computes each field exactly as the single one."""
@@ -72,9 +72,24 @@ def test_native_roundtrip_and_bad_args(pair):
         n = P.ctx.pack(g, prec, 1)
         back = P.ctx.unpack(n, prec, 1, 2)
         assert torch.equal(back.reshape(g.shape), g)
-    with pytest.raises(lqcd.LqcdError) as e:
-        P.ctx.apply_Dhat(to_gpu(x[0]), prec=lqcd.F16S)
+    with pytest.raises(lqcd.LqcdError) as e:   # bfloat16 is the network's storage only
+        P.ctx.apply_Dhat(to_gpu(x[0]), prec=lqcd.BF16)
     assert e.value.status == 1
+
+
+def test_f16s_storage_roundtrip(pair):
+    """Half precision with a per-site scale: every site is reproduced to the
+    FP16 rounding of its own largest component; zero sites stay zero."""
+    P = pair
+    x = synth.gaussian_spinor(2 * P.Vh, 21).reshape(2, P.Vh, 4, 3).astype(np.complex64)
+    x[1, ::3] *= 1e-30          # tiny sites keep their relative precision
+    x[0, 1] = 0
+    g = torch.from_numpy(x).cuda()
+    back = P.ctx.unpack(P.ctx.pack(g, lqcd.F16S, 1), lqcd.F16S, 1, 2).cpu().numpy()
+    site_max = np.abs(np.stack([x.real, x.imag], -1)).reshape(2, P.Vh, -1).max(-1)
+    err = np.abs(np.stack([(back - x).real, (back - x).imag], -1)).reshape(2, P.Vh, -1).max(-1)
+    assert np.all(err <= 2.0 ** -11 * site_max * (1 + 1e-6))
+    assert np.all(back[0, 1] == 0)
 
 
 def test_unit_links_free_field_on_gpu():
@@ -97,7 +112,7 @@ def test_dhat_full_size_sampled():
     P = Pair(dims, kappa=0.13625)
     rng = np.random.default_rng(0)
     sample = np.concatenate([[0, 1, P.Vh - 1], rng.integers(0, P.Vh, 61)])
-    for prec in (lqcd.F32, lqcd.F64):
+    for prec in (lqcd.F32, lqcd.F64, lqcd.F16S):
         pe = rounded(synth.gaussian_spinor(P.Vh, 11), prec)
         g = to_gpu(pe, prec)
         nin = P.ctx.pack(g, prec, 1)

@@ -28,7 +28,8 @@ def test_cgnr_8x4(p8):
     assert util.relerr(x, ref) < 1e-7
 
 
-@pytest.mark.parametrize("prec,tol", [(lqcd.F64, 1e-12), (lqcd.F32, 2e-5)], ids=["f64", "f32"])
+@pytest.mark.parametrize("prec,tol", [(lqcd.F64, 1e-12), (lqcd.F32, 2e-5), (lqcd.F16S, 1e-2)],
+                         ids=["f64", "f32", "f16s"])
 @pytest.mark.parametrize("dims,bs", [((8, 8, 8, 8), (4, 4, 4, 4)), ((8, 4, 4, 8), (4, 4, 4, 4)),
                                      ((12, 8, 4, 4), (4, 4, 4, 4)), ((4, 4, 4, 4), (4, 4, 4, 4))],
                          ids=["8x8x8x8", "8x4x4x8", "12x8x4x4-odd-blocks", "one-block"])
@@ -39,7 +40,7 @@ def test_sap_parity(dims, bs, prec, tol, monkeypatch):
     P = Pair(dims, kappa=0.1355)
     eta = synth.gaussian_spinor(P.V, 2)
     ref = P.o.sap(eta, bs=bs, ncy=4, nmr=5)
-    for generic in (("0", "1") if prec == lqcd.F32 else ("0",)):
+    for generic in (("0", "1") if prec != lqcd.F64 else ("0",)):
         monkeypatch.setenv("LQCD_SAP_GENERIC", generic)
         out = P.ctx.sap(to_gpu(eta), bs=bs, ncy=4, nmr=5, prec=prec)
         assert relerr(out, ref) < tol, generic
@@ -56,6 +57,19 @@ def test_sap_gcr_solve_dhat(p8, inner):
     for k in range(2):
         assert util.relerr(P.o.Dhat(x[k]), eta[k]) <= 1e-10
         assert info[k]["relres_dhat"] <= 1e-10
+
+
+def test_sap_gcr_f16s_sap(p8):
+    """FP16 (per-site scale) SAP inside the FP64 GCR, FP32 stencil: the true
+    residual still reaches 1e-10."""
+    P = p8
+    eta = synth.gaussian_spinor(2 * P.Vh, 13).reshape(2, P.Vh, 4, 3)
+    psi, info, st = P.ctx.solve_dhat(to_gpu(eta), solver=lqcd.SOLVER_SAP_GCR, tol=1e-10, nkv=16, nmx=2000,
+                                     sap_prec=lqcd.F16S, inner=lqcd.F32)
+    assert st == 0
+    x = psi.cpu().numpy()
+    for k in range(2):
+        assert util.relerr(P.o.Dhat(x[k]), eta[k]) <= 1e-10
 
 
 def test_sap_gcr_full_D(p8):
