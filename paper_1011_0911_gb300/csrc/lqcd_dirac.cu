@@ -1,341 +1,19 @@
-// Wilson-clover stencil kernels on native (site-minor) layouts.
-//
-//   H psi(x) = -1/2 sum_mu [(1-g_mu) U_mu(x) psi(x+mu) + (1+g_mu) U_mu(x-mu)^dag psi(x-mu)]
-//   D = A + H (Eq. 1),  Dhat = A_ee - H_eo A_oo^-1 H_oe (Eq. 2).
+// Wilson-clover stencil kernels on native (site-minor) layouts: the
+// single-field form and the dispatch of D, Dhat (Eq. 1, Eq. 2) over it and
+// the register-blocked multi-field form (lqcd_dirac_mr.cu).
 //
 // One thread per (output site, right-hand side).  A CTA is blockDim.x sites
 // by blockDim.y right-hand sides, so a warp reads 32 consecutive sites of one
 // field (coalesced 16-byte loads) and the warps of the other right-hand
-// sides reuse the same link / clover words from L1: links and clover are
-// fetched from HBM once per CTA however many fields it serves.
-//
-// In the chiral basis g_mu = [[0, e_mu], [e_mu^dag, 0]] with e_0 = -1 and
-// e_k = -i sigma_k, so (1 -+ g_mu) psi is determined by the half spinor
-// h = psi_up -+ e_mu psi_lo: the upper half of the result is h and the lower
-// half is -+ e_mu^dag h.  Each hop therefore multiplies only two colour
-// vectors by the link (spin projection), 1320 flops per output site.
+// sides reuse the same link / clover words from L1.
 #include <type_traits>
 
-#include "lqcd_f16s.cuh"
-#include "lqcd_internal.cuh"
+#include "lqcd_stencil.cuh"
 #include "lqcd_tune.h"
 
 namespace {
 
-template <lqcd_prec P>
-struct PT;
-template <>
-struct PT<LQCD_F64> {
-    using R = double;
-};
-template <>
-struct PT<LQCD_F32> {
-    using R = float;
-};
-
-// ---------------------------------------------------------------- loads
-template <class R>
-struct Spinor {
-    cx<R> s[4][3];
-};
-
-__device__ __forceinline__ void load_spinor(const double2 *__restrict__ f, long Vh, int r,
-                                            Spinor<double> &o)
-{
-#pragma unroll
-    for (int c = 0; c < 12; c++) {
-        double2 v = __ldg(f + c * Vh + r);
-        o.s[c / 3][c % 3] = mk(v.x, v.y);
-    }
-}
-__device__ __forceinline__ void load_spinor(const float4 *__restrict__ f, long Vh, int r,
-                                            Spinor<float> &o)
-{
-#pragma unroll
-    for (int q = 0; q < 6; q++) {
-        float4 v = __ldg(f + q * Vh + r);
-        int c0 = 2 * q, c1 = 2 * q + 1;
-        o.s[c0 / 3][c0 % 3] = mk(v.x, v.y);
-        o.s[c1 / 3][c1 % 3] = mk(v.z, v.w);
-    }
-}
-__device__ __forceinline__ void store_spinor(double2 *__restrict__ f, long Vh, int r,
-                                             const Spinor<double> &o)
-{
-#pragma unroll
-    for (int c = 0; c < 12; c++) f[c * Vh + r] = make_double2(o.s[c / 3][c % 3].re, o.s[c / 3][c % 3].im);
-}
-__device__ __forceinline__ void store_spinor(float4 *__restrict__ f, long Vh, int r,
-                                             const Spinor<float> &o)
-{
-#pragma unroll
-    for (int q = 0; q < 6; q++) {
-        int c0 = 2 * q, c1 = 2 * q + 1;
-        f[q * Vh + r] = make_float4(o.s[c0 / 3][c0 % 3].re, o.s[c0 / 3][c0 % 3].im,
-                                    o.s[c1 / 3][c1 % 3].re, o.s[c1 / 3][c1 % 3].im);
-    }
-}
-
-// FP16 + per-site scale storage (arithmetic in FP32)
-__device__ __forceinline__ void load_spinor(const h16s *__restrict__ f, long Vh, int r, Spinor<float> &o)
-{
-    cx<float> v[12];
-    f16s_load<true>(f, Vh, r, v);
-#pragma unroll
-    for (int c = 0; c < 12; c++) o.s[c / 3][c % 3] = v[c];
-}
-__device__ __forceinline__ void store_spinor(h16s *__restrict__ f, long Vh, int r, const Spinor<float> &o)
-{
-    cx<float> v[12];
-#pragma unroll
-    for (int c = 0; c < 12; c++) v[c] = o.s[c / 3][c % 3];
-    f16s_store(f, Vh, r, v);
-}
-
-// SU(3) link of parity p, direction mu, at rank r
-__device__ __forceinline__ void load_link(const double2 *__restrict__ U, long Vh, int p, int mu, int r,
-                                          cx<double> u[3][3])
-{
-    const double2 *b = U + (long)((p * 4 + mu) * 9) * Vh + r;
-#pragma unroll
-    for (int e = 0; e < 9; e++) {
-        double2 v = __ldg(b + e * Vh);
-        u[e / 3][e % 3] = mk(v.x, v.y);
-    }
-}
-// two stored rows, third = (row0 x row1)^*
-__device__ __forceinline__ void load_link(const float4 *__restrict__ U, long Vh, int p, int mu, int r,
-                                          cx<float> u[3][3])
-{
-    const float4 *b = U + (long)((p * 4 + mu) * 3) * Vh + r;
-#pragma unroll
-    for (int q = 0; q < 3; q++) {
-        float4 v = __ldg(b + q * Vh);
-        int e0 = 2 * q, e1 = 2 * q + 1;
-        u[e0 / 3][e0 % 3] = mk(v.x, v.y);
-        u[e1 / 3][e1 % 3] = mk(v.z, v.w);
-    }
-    u[2][0] = conjx(u[0][1] * u[1][2] - u[0][2] * u[1][1]);
-    u[2][1] = conjx(u[0][2] * u[1][0] - u[0][0] * u[1][2]);
-    u[2][2] = conjx(u[0][0] * u[1][1] - u[0][1] * u[1][0]);
-}
-
-__device__ __forceinline__ void load_link(const uint2 *__restrict__ U, long Vh, int p, int mu, int r,
-                                          cx<float> u[3][3])
-{
-    f16s_link(U, Vh, p, mu, r, u);
-}
-
-// packed Hermitian 6x6 pair: per block 6 real diagonal entries then the 15
-// complex entries above the diagonal in row-major order (36 reals)
-template <class R>
-struct Herm6 {
-    R d[6];
-    cx<R> o[15];
-};
-__device__ __forceinline__ void load_herm(const double2 *__restrict__ A, long Vh, int r, int blk,
-                                          Herm6<double> &h)
-{
-    const double2 *b = A + (long)(18 * blk) * Vh + r;
-#pragma unroll
-    for (int i = 0; i < 3; i++) {
-        double2 v = __ldg(b + i * Vh);
-        h.d[2 * i] = v.x;
-        h.d[2 * i + 1] = v.y;
-    }
-#pragma unroll
-    for (int i = 0; i < 15; i++) {
-        double2 v = __ldg(b + (3 + i) * Vh);
-        h.o[i] = mk(v.x, v.y);
-    }
-}
-__device__ __forceinline__ void load_herm(const float4 *__restrict__ A, long Vh, int r, int blk,
-                                          Herm6<float> &h)
-{
-    const float4 *b = A + (long)(9 * blk) * Vh + r;
-    float v[36];
-#pragma unroll
-    for (int q = 0; q < 9; q++) {
-        float4 t = __ldg(b + q * Vh);
-        v[4 * q] = t.x;
-        v[4 * q + 1] = t.y;
-        v[4 * q + 2] = t.z;
-        v[4 * q + 3] = t.w;
-    }
-#pragma unroll
-    for (int i = 0; i < 6; i++) h.d[i] = v[i];
-#pragma unroll
-    for (int i = 0; i < 15; i++) h.o[i] = mk(v[6 + 2 * i], v[7 + 2 * i]);
-}
-
-__device__ __forceinline__ void load_herm(const uint2 *__restrict__ A, long Vh, int r, int blk, Herm6<float> &h)
-{
-    float v[36];
-    f16s_clover(A, Vh, r, blk, v);
-#pragma unroll
-    for (int i = 0; i < 6; i++) h.d[i] = v[i];
-#pragma unroll
-    for (int i = 0; i < 15; i++) h.o[i] = mk(v[6 + 2 * i], v[7 + 2 * i]);
-}
-
-// out[6] = H in[6]
-template <class R>
-__device__ __forceinline__ void herm_apply(const Herm6<R> &h, const cx<R> in[6], cx<R> out[6])
-{
-#pragma unroll
-    for (int i = 0; i < 6; i++) out[i] = h.d[i] * in[i];
-    int k = 0;
-#pragma unroll
-    for (int i = 0; i < 6; i++)
-#pragma unroll
-        for (int j = i + 1; j < 6; j++) {
-            out[i] = out[i] + h.o[k] * in[j];
-            out[j] = out[j] + cmulc(h.o[k], in[i]);
-            k++;
-        }
-}
-
-template <class R, class CL>
-__device__ __forceinline__ void clover_apply(const CL *A, long Vh, int r, const Spinor<R> &in,
-                                             Spinor<R> &out)
-{
-#pragma unroll
-    for (int blk = 0; blk < 2; blk++) {
-        Herm6<R> h;
-        load_herm(A, Vh, r, blk, h);
-        cx<R> v[6], w[6];
-#pragma unroll
-        for (int s = 0; s < 2; s++)
-#pragma unroll
-            for (int c = 0; c < 3; c++) v[3 * s + c] = in.s[2 * blk + s][c];
-        herm_apply(h, v, w);
-#pragma unroll
-        for (int s = 0; s < 2; s++)
-#pragma unroll
-            for (int c = 0; c < 3; c++) out.s[2 * blk + s][c] = w[3 * s + c];
-    }
-}
-
-// ------------------------------------------------------- spin projection
-// h = psi_up + sgn * e_mu psi_lo, sgn = -1 for the forward (1-g) hop, +1 backward
-template <class R, int MU, int SGN>
-__device__ __forceinline__ void project(const Spinor<R> &p, cx<R> h[2][3])
-{
-#pragma unroll
-    for (int c = 0; c < 3; c++) {
-        cx<R> u0 = p.s[0][c], u1 = p.s[1][c], l0 = p.s[2][c], l1 = p.s[3][c];
-        if (MU == 0) {  // e = -1
-            h[0][c] = SGN < 0 ? u0 + l0 : u0 - l0;
-            h[1][c] = SGN < 0 ? u1 + l1 : u1 - l1;
-        } else if (MU == 1) {  // e = -i sigma_x: e l = (-i l1, -i l0)
-            h[0][c] = SGN < 0 ? u0 + timesI(l1) : u0 - timesI(l1);
-            h[1][c] = SGN < 0 ? u1 + timesI(l0) : u1 - timesI(l0);
-        } else if (MU == 2) {  // e = [[0,-1],[1,0]]: e l = (-l1, l0)
-            h[0][c] = SGN < 0 ? u0 + l1 : u0 - l1;
-            h[1][c] = SGN < 0 ? u1 - l0 : u1 + l0;
-        } else {  // e = diag(-i, i): e l = (-i l0, i l1)
-            h[0][c] = SGN < 0 ? u0 + timesI(l0) : u0 - timesI(l0);
-            h[1][c] = SGN < 0 ? u1 - timesI(l1) : u1 + timesI(l1);
-        }
-    }
-}
-// acc += (w ; sgn * e_mu^dag w)
-template <class R, int MU, int SGN>
-__device__ __forceinline__ void accumulate(Spinor<R> &acc, const cx<R> w[2][3])
-{
-#pragma unroll
-    for (int c = 0; c < 3; c++) {
-        acc.s[0][c] = acc.s[0][c] + w[0][c];
-        acc.s[1][c] = acc.s[1][c] + w[1][c];
-        cx<R> a, b;  // e^dag w
-        if (MU == 0) {  // e^dag = -1
-            a = -w[0][c];
-            b = -w[1][c];
-        } else if (MU == 1) {  // e^dag = i sigma_x
-            a = timesI(w[1][c]);
-            b = timesI(w[0][c]);
-        } else if (MU == 2) {  // e^dag = [[0,1],[-1,0]]
-            a = w[1][c];
-            b = -w[0][c];
-        } else {  // e^dag = diag(i, -i)
-            a = timesI(w[0][c]);
-            b = timesmI(w[1][c]);
-        }
-        if (SGN < 0) {
-            acc.s[2][c] = acc.s[2][c] - a;
-            acc.s[3][c] = acc.s[3][c] - b;
-        } else {
-            acc.s[2][c] = acc.s[2][c] + a;
-            acc.s[3][c] = acc.s[3][c] + b;
-        }
-    }
-}
-
-template <class R>
-__device__ __forceinline__ void su3_vec(const cx<R> u[3][3], const cx<R> h[3], cx<R> w[3], R sign)
-{
-#pragma unroll
-    for (int a = 0; a < 3; a++) {
-        cx<R> t = u[a][0] * h[0] + u[a][1] * h[1] + u[a][2] * h[2];
-        w[a] = sign * t;
-    }
-}
-template <class R>
-__device__ __forceinline__ void su3dag_vec(const cx<R> u[3][3], const cx<R> h[3], cx<R> w[3], R sign)
-{
-#pragma unroll
-    for (int a = 0; a < 3; a++) {
-        cx<R> t = cmulc(u[0][a], h[0]) + cmulc(u[1][a], h[1]) + cmulc(u[2][a], h[2]);
-        w[a] = sign * t;
-    }
-}
-
-template <class R, class SP, class LK, int MU>
-__device__ __forceinline__ void hop_dir(const Geom &g, int p_out, int r, const int x[4],
-                                        const SP *in, long Vh, const LK *U, Spinor<R> &acc)
-{
-    cx<R> h[2][3], w[2][3];
-    cx<R> u[3][3];
-    Spinor<R> psi;
-    // forward: (1 - g_mu) U_mu(x) psi(x + mu)
-    {
-        int ry = nbr_rank(g, x, MU, +1);
-        R sg = (MU == 0 && x[0] == g.L[0] - 1) ? R(g.bc_t) : R(1);
-        load_spinor(in, Vh, ry, psi);
-        project<R, MU, -1>(psi, h);
-        load_link(U, Vh, p_out, MU, r, u);
-        su3_vec(u, h[0], w[0], sg);
-        su3_vec(u, h[1], w[1], sg);
-        accumulate<R, MU, -1>(acc, w);
-    }
-    // backward: (1 + g_mu) U_mu(x - mu)^dag psi(x - mu)
-    {
-        int rz = nbr_rank(g, x, MU, -1);
-        R sg = (MU == 0 && x[0] == 0) ? R(g.bc_t) : R(1);
-        load_spinor(in, Vh, rz, psi);
-        project<R, MU, +1>(psi, h);
-        load_link(U, Vh, 1 - p_out, MU, rz, u);
-        su3dag_vec(u, h[0], w[0], sg);
-        su3dag_vec(u, h[1], w[1], sg);
-        accumulate<R, MU, +1>(acc, w);
-    }
-}
-
-enum { MODE_HOP = 0, MODE_DHAT1 = 1, MODE_DHAT2 = 2, MODE_D = 3 };
-
-template <class SP, class LK, class CL>
-struct HopArgs {
-    Geom g;
-    int p_out, nrhs;
-    const SP *in_other;
-    long in_rs;
-    const SP *in_same;
-    long same_rs;
-    SP *out;
-    long out_rs;
-    const LK *U;
-    const CL *clov;   // parity p_out: A^-1 (DHAT1) or A (DHAT2, D)
-};
+using namespace stencil;
 
 //   MODE_HOP  : out = -1/2 S
 //   MODE_DHAT1: out = A^-1 (-1/2 S)            (chi_o = A_oo^-1 H_oe psi_e)
@@ -446,6 +124,51 @@ std::vector<TuneChoice> hop_candidates(int nrhs)
     return v;
 }
 
+int hop_force_nr(bool has_mr, int nrhs)
+{
+    const char *e = getenv("LQCD_HOP_NR");
+    if (!e || !*e) return 0;
+    const int n = atoi(e);
+    if (n == 1) return 1;
+    if (n == 2 && has_mr && n <= nrhs) return n;
+    return 0;
+}
+
+// register-blocked shapes: nr fields per thread, tx sites x ty field groups
+std::vector<TuneChoice> hop_mr_candidates(int nrhs)
+{
+    std::vector<TuneChoice> v;
+    for (int nr : {2}) {
+        if (nr > nrhs) continue;
+        const int groups = (nrhs + nr - 1) / nr;
+        std::vector<int> tys;
+        for (int t : {1, 2, groups})
+            if (t >= 1 && t <= groups && std::find(tys.begin(), tys.end(), t) == tys.end()) tys.push_back(t);
+        for (int var = 0; var < NVAR_MR; var++)
+            for (int ty : tys)
+                for (int tx : {32, 64, 128, 256}) {
+                    const int n = tx * ty;
+                    if (n > var_mr_max_threads(var) || n < 64) continue;
+                    TuneChoice t;
+                    t.variant = var;
+                    t.tx = tx;
+                    t.ty = ty;
+                    t.nr = nr;
+                    v.push_back(t);
+                }
+    }
+    return v;
+}
+
+template <class R, class SP, class LK, class CL, int MODE>
+lqcd_status launch_choice(lqcd_ctx *c, const TuneChoice &t, const HopArgs<SP, LK, CL> &a)
+{
+    if constexpr (std::is_same<R, float>::value && MODE != MODE_HOP) {
+        if (t.nr > 1) return launch_hop_mr<R, SP, LK, CL, MODE>(c, t.nr, t.variant, dim3(t.tx, t.ty), a);
+    }
+    return launch_var<R, SP, LK, CL, MODE>(c, t.variant, dim3(t.tx, t.ty), a);
+}
+
 template <class R, class SP, class LK, class CL, int MODE>
 lqcd_status launch_hop(lqcd_ctx *c, int p_out, const SP *in_other, long in_rs, const SP *in_same,
                        long same_rs, SP *out, long out_rs, const LK *U, const CL *clov, int nrhs)
@@ -463,20 +186,36 @@ lqcd_status launch_hop(lqcd_ctx *c, int p_out, const SP *in_other, long in_rs, c
     a.U = U;
     a.clov = clov;
     const int prec = sizeof(R) == 8 ? 0 : (std::is_same<SP, h16s>::value ? 2 : 1);
-    std::string key = tune_key(c, "k_hop", MODE, prec, nrhs);
+    constexpr bool has_mr = std::is_same<R, float>::value && MODE != MODE_HOP;
+    // LQCD_HOP_NR = 1 or 2 restricts the search to that many fields per
+    // thread (test instrumentation; ignored where no such kernel exists)
+    const int force_nr = hop_force_nr(has_mr, nrhs);
+    std::string key = tune_key(c, force_nr ? (force_nr == 1 ? "k_hop2_nr1" : "k_hop2_nr2") : "k_hop2", MODE, prec, nrhs);
     TuneChoice tc;
     if (!tune_lookup(key, &tc)) {
         tc = TuneChoice();
         tc.tx = nrhs == 1 ? 128 : 32;
         tc.ty = nrhs == 1 ? 1 : std::min(nrhs, 8);
+        if (force_nr > 1) {
+            tc.nr = force_nr;
+            tc.tx = 64;
+            tc.ty = 1;
+        }
         if (tune_enabled()) {
             float best = 1e30f;
-            for (const TuneChoice &cand : hop_candidates(nrhs)) {
+            std::vector<TuneChoice> cands;
+            if (force_nr <= 1) cands = hop_candidates(nrhs);
+            if (has_mr) {
+                for (const TuneChoice &m : hop_mr_candidates(nrhs))
+                    if (!force_nr || m.nr == force_nr) cands.push_back(m);
+            }
+            for (const TuneChoice &cand : cands) {
                 float us;
-                lqcd_status s = tune_time(
-                    c, [&]() { return launch_var<R, SP, LK, CL, MODE>(c, cand.variant, dim3(cand.tx, cand.ty), a); },
-                    3, &us);
+                lqcd_status s = tune_time(c, [&]() { return launch_choice<R, SP, LK, CL, MODE>(c, cand, a); }, 3, &us);
                 if (s != LQCD_OK) return s;
+                if (tune_verbose())
+                    fprintf(stderr, "tune %s: nr=%d var=%d %dx%d %.1f us\n", key.c_str(), cand.nr, cand.variant,
+                            cand.tx, cand.ty, us);
                 if (us < best) {
                     best = us;
                     tc = cand;
@@ -486,7 +225,7 @@ lqcd_status launch_hop(lqcd_ctx *c, int p_out, const SP *in_other, long in_rs, c
             tune_store(key, tc);
         }
     }
-    return launch_var<R, SP, LK, CL, MODE>(c, tc.variant, dim3(tc.tx, tc.ty), a);
+    return launch_choice<R, SP, LK, CL, MODE>(c, tc, a);
 }
 
 }  // namespace

@@ -30,7 +30,7 @@ std::string cache_path()
     return std::string(h ? h : "/tmp") + "/.cache/lqcd_tune.json";
 }
 
-// file format: {"key": [variant, tx, ty, us], ...} one entry per line
+// file format: {"key": [variant, tx, ty, us, nr], ...} one entry per line
 void load_locked()
 {
     if (g_loaded) return;
@@ -45,7 +45,10 @@ void load_locked()
         std::stringstream ss(line.substr(l + 1, r - l - 1));
         TuneChoice t;
         char comma;
-        if (ss >> t.variant >> comma >> t.tx >> comma >> t.ty >> comma >> t.us) g_cache[key] = t;
+        if (ss >> t.variant >> comma >> t.tx >> comma >> t.ty >> comma >> t.us) {
+            if (!(ss >> comma >> t.nr)) t.nr = 1;
+            g_cache[key] = t;
+        }
     }
 }
 
@@ -65,7 +68,7 @@ void save_locked()
     size_t i = 0;
     for (auto &kv : g_cache) {
         f << "  \"" << kv.first << "\": [" << kv.second.variant << ", " << kv.second.tx << ", " << kv.second.ty
-          << ", " << kv.second.us << "]" << (++i < g_cache.size() ? "," : "") << "\n";
+          << ", " << kv.second.us << ", " << kv.second.nr << "]" << (++i < g_cache.size() ? "," : "") << "\n";
     }
     f << "}\n";
     f.close();
@@ -112,6 +115,12 @@ bool tune_enabled()
 {
     const char *p = getenv("LQCD_TUNE");
     return !(p && p[0] == '0');
+}
+
+bool tune_verbose()
+{
+    const char *p = getenv("LQCD_TUNE_VERBOSE");
+    return p && p[0] == '1';
 }
 
 // time a launch closure on the context's stream: median of reps
