@@ -305,6 +305,46 @@ LQCD_API lqcd_status lqcd_net_train(lqcd_ctx *ctx, const lqcd_net_train_params *
 LQCD_API lqcd_status lqcd_solve_D(lqcd_ctx *ctx, const lqcd_solver_params *p, const double *eta_dev,
                          double *psi_dev, int nrhs, lqcd_solve_info *info);
 
+/* ------------------------------------------------ batched multi-lattice solve */
+/* Several independent lattices (each its own context: gauge field, kappa,
+ * clover term) solved together with the SAP-preconditioned flexible GCR of
+ * Sec. 3-4, one right-hand side per lattice.  Every phase of a GCR step runs
+ * as ONE launch over a work list of (lattice, tile / SAP block / vector chunk)
+ * items of all lattices: the SAP block solves (precision sap.prec, F16S or
+ * F32), D phi in F32, the FP64 Gram-Schmidt (one cooperative persistent
+ * kernel whose grid barriers wait at most wait_timeout_s, then report
+ * LQCD_ERR_TIMEOUT), and the FP64 residual restart.  Per-lattice scalars and
+ * convergence flags stay on the device; converged lattices drop out of the
+ * work lists.  With use_graph the GCR cycle (nkv steps and the solution
+ * update) is captured once as a CUDA graph and replayed; the host waits once
+ * per cycle.  All contexts must share one SAP block shape; they must not be
+ * used by other calls while a batch solve runs. */
+typedef struct lqcd_batch lqcd_batch;
+typedef struct {
+    int nkv;                /* Krylov vectors per cycle, 1..32 */
+    int nmx;                /* GCR steps per lattice, at most */
+    double tol;             /* relative residual |eta - D psi| / |eta| per lattice */
+    lqcd_sap_params sap;    /* preconditioner; prec LQCD_F16S or LQCD_F32 */
+    int use_graph;          /* replay the GCR cycle from a captured CUDA graph */
+    double wait_timeout_s;  /* limit of each device-side wait */
+    int stall_test;         /* test aid: the first grid barrier waits for one CTA too many,
+                               so it can only end by its time limit; 0 in normal use */
+} lqcd_batch_params;
+/* ctxs: n contexts with gauge field and clover term.  stream: the caller's
+ * stream, ordered before and after each solve; the batch works on its own. */
+LQCD_API lqcd_status lqcd_batch_create(lqcd_ctx *const *ctxs, int n, const lqcd_batch_params *p, void *stream,
+                                       lqcd_batch **out);
+LQCD_API lqcd_status lqcd_batch_destroy(lqcd_batch *b);
+LQCD_API const char *lqcd_batch_last_error(const lqcd_batch *b);
+/* Solve Dhat_l psi_l = eta_l (Eq. 2, through Eq. 5) for every lattice l:
+ * eta_dev[l], psi_dev[l]: canonical FP64 even fields of lattice l (device).
+ * info: n entries.  Returns the worst per-lattice status. */
+LQCD_API lqcd_status lqcd_batch_solve_dhat(lqcd_batch *b, const double *const *eta_dev, double *const *psi_dev,
+                                           lqcd_solve_info *info);
+/* Statistics of the last solve: GCR cycles, cycles replayed from the graph,
+ * kernel launches issued by the host. */
+LQCD_API lqcd_status lqcd_batch_stats(const lqcd_batch *b, int *cycles, int *graph_replays, long *launches);
+
 #ifdef __cplusplus
 }
 #endif

@@ -42,13 +42,11 @@ struct Var<3> {
 constexpr int NVAR = 4;
 inline int var_max_threads(int v) { return v < 2 ? 384 : 256; }
 
-template <class R, class SP, class LK, class CL, int MODE, int VAR>
-__global__ void __launch_bounds__(Var<VAR>::T, Var<VAR>::B) k_hop(HopArgs<SP, LK, CL> a)
+// output site r (rank of parity p_out), right-hand side k
+template <class R, class SP, class LK, class CL, int MODE>
+__device__ __forceinline__ void hop_site(const HopArgs<SP, LK, CL> &a, int r, int k)
 {
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    const int k = blockIdx.y * blockDim.y + threadIdx.y;
     const long Vh = a.g.Vh;
-    if (r >= a.g.Vh || k >= a.nrhs) return;
     int x[4];
     rank_coords(a.g, a.p_out, r, x);
     const SP *in = a.in_other + k * a.in_rs;
@@ -86,6 +84,29 @@ __global__ void __launch_bounds__(Var<VAR>::T, Var<VAR>::B) k_hop(HopArgs<SP, LK
     } else {
         store_spinor(a.out + k * a.out_rs, Vh, r, acc);
     }
+}
+
+template <class R, class SP, class LK, class CL, int MODE, int VAR>
+__global__ void __launch_bounds__(Var<VAR>::T, Var<VAR>::B) k_hop(HopArgs<SP, LK, CL> a)
+{
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    const int k = blockIdx.y * blockDim.y + threadIdx.y;
+    if (r >= a.g.Vh || k >= a.nrhs) return;
+    hop_site<R, SP, LK, CL, MODE>(a, r, k);
+}
+
+// D on the full fields of several lattices in one launch.  items: (index of
+// the HopArgs of a lattice and output parity, first rank of the tile, sites in
+// the tile, lattice); tiles of lattices whose active flag is 0 are skipped.
+template <class R, class SP, class LK, class CL>
+__global__ void __launch_bounds__(256) k_hop_batch(const HopArgs<SP, LK, CL> *args, const int4 *items, const int *active)
+{
+    __shared__ HopArgs<SP, LK, CL> sa;
+    const int4 w = items[blockIdx.x];
+    if (active && !active[w.w]) return;
+    if (threadIdx.x == 0) sa = args[w.x];
+    __syncthreads();
+    if ((int)threadIdx.x < w.z) hop_site<R, SP, LK, CL, MODE_D>(sa, w.y + threadIdx.x, 0);
 }
 
 template <class R, class SP, class LK, class CL, int MODE>
@@ -320,4 +341,157 @@ lqcd_status dirac_hop_parity(lqcd_ctx *c, lqcd_prec p, int p_out, const void *in
             c, p_out, (const float4 *)in_other, in_rstride, nullptr, 0, (float4 *)out, out_rstride,
             c->U32, (const float4 *)nullptr, nrhs);
     return set_err(c, LQCD_ERR_ARG, "precision %d not supported for hop", (int)p);
+}
+
+// ------------------------------------------------------------------ batches
+struct DBatch {
+    lqcd_prec p = LQCD_F32;
+    int nlat = 0;
+    long sites = 0;
+    void *args = nullptr;                       // HopArgs[2 nlat]: (lattice, output parity)
+    int4 *items[3] = {nullptr, nullptr, nullptr};   // tiles of 64 / 128 / 256 sites
+    int nitems[3] = {0, 0, 0};
+    int choice = -1;                            // tuned tile size index
+};
+static const int kBatchTile[3] = {64, 128, 256};
+
+namespace {
+template <class SP, class LK, class CL>
+std::vector<HopArgs<SP, LK, CL>> batch_args(lqcd_ctx *const *ctx, int n, const SP *in, SP *out, const long *off,
+                                            long units_per_site, const LK *const *U, const CL *const *A0,
+                                            const CL *const *A1)
+{
+    std::vector<HopArgs<SP, LK, CL>> v;
+    for (int l = 0; l < n; l++)
+        for (int p = 0; p < 2; p++) {
+            HopArgs<SP, LK, CL> a;
+            const long half = units_per_site * ctx[l]->g.Vh;
+            a.g = ctx[l]->g;
+            a.p_out = p;
+            a.nrhs = 1;
+            a.in_other = in + off[l] + (1 - p) * half;
+            a.in_rs = 0;
+            a.in_same = in + off[l] + p * half;
+            a.same_rs = 0;
+            a.out = out + off[l] + p * half;
+            a.out_rs = 0;
+            a.U = U[l];
+            a.clov = p ? A1[l] : A0[l];
+            v.push_back(a);
+        }
+    return v;
+}
+}  // namespace
+
+lqcd_status dirac_batch_create(lqcd_ctx *hc, lqcd_ctx *const *ctx, int n, lqcd_prec p, const void *in, void *out,
+                               const long *off, DBatch **out_b)
+{
+    if (p != LQCD_F32 && p != LQCD_F64) return set_err(hc, LQCD_ERR_ARG, "batched D: precision %d", (int)p);
+    DBatch *b = new DBatch();
+    b->p = p;
+    b->nlat = n;
+    size_t argbytes;
+    std::vector<unsigned char> host;
+    if (p == LQCD_F32) {
+        std::vector<const float4 *> U(n), A0(n), A1(n);
+        for (int l = 0; l < n; l++) {
+            U[l] = ctx[l]->U32;
+            A0[l] = ctx[l]->A32[0];
+            A1[l] = ctx[l]->A32[1];
+        }
+        auto v = batch_args<float4, float4, float4>(ctx, n, (const float4 *)in, (float4 *)out, off, 6, U.data(),
+                                                    A0.data(), A1.data());
+        argbytes = v.size() * sizeof(v[0]);
+        host.assign((unsigned char *)v.data(), (unsigned char *)v.data() + argbytes);
+    } else {
+        std::vector<const double2 *> U(n), A0(n), A1(n);
+        for (int l = 0; l < n; l++) {
+            U[l] = ctx[l]->U64;
+            A0[l] = ctx[l]->A64[0];
+            A1[l] = ctx[l]->A64[1];
+        }
+        auto v = batch_args<double2, double2, double2>(ctx, n, (const double2 *)in, (double2 *)out, off, 12,
+                                                       U.data(), A0.data(), A1.data());
+        argbytes = v.size() * sizeof(v[0]);
+        host.assign((unsigned char *)v.data(), (unsigned char *)v.data() + argbytes);
+    }
+    if (cudaMalloc(&b->args, argbytes) != cudaSuccess) {
+        delete b;
+        cudaGetLastError();
+        return set_err(hc, LQCD_ERR_NOMEM, "batched D arguments");
+    }
+    cudaMemcpy(b->args, host.data(), argbytes, cudaMemcpyHostToDevice);
+    for (int t = 0; t < 3; t++) {
+        std::vector<int4> it;
+        for (int l = 0; l < n; l++)
+            for (int par = 0; par < 2; par++)
+                for (int r0 = 0; r0 < ctx[l]->g.Vh; r0 += kBatchTile[t])
+                    it.push_back(make_int4(2 * l + par, r0, std::min(kBatchTile[t], ctx[l]->g.Vh - r0), l));
+        b->nitems[t] = (int)it.size();
+        if (cudaMalloc(&b->items[t], it.size() * sizeof(int4)) != cudaSuccess) {
+            cudaGetLastError();
+            dirac_batch_free(b);
+            return set_err(hc, LQCD_ERR_NOMEM, "batched D work list");
+        }
+        cudaMemcpy(b->items[t], it.data(), it.size() * sizeof(int4), cudaMemcpyHostToDevice);
+    }
+    for (int l = 0; l < n; l++) b->sites += ctx[l]->g.V;
+    *out_b = b;
+    return LQCD_OK;
+}
+
+void dirac_batch_free(DBatch *b)
+{
+    if (!b) return;
+    cudaFree(b->args);
+    for (int t = 0; t < 3; t++) cudaFree(b->items[t]);
+    delete b;
+}
+
+namespace {
+lqcd_status batch_launch(lqcd_ctx *hc, DBatch *b, int t, const int *active)
+{
+    if (b->p == LQCD_F32)
+        k_hop_batch<float, float4, float4, float4><<<b->nitems[t], kBatchTile[t], 0, hc->stream>>>(
+            (const HopArgs<float4, float4, float4> *)b->args, b->items[t], active);
+    else
+        k_hop_batch<double, double2, double2, double2><<<b->nitems[t], kBatchTile[t], 0, hc->stream>>>(
+            (const HopArgs<double2, double2, double2> *)b->args, b->items[t], active);
+    hc->n_kernel_launches++;
+    LQCD_LAUNCH_CHECK(hc);
+    return LQCD_OK;
+}
+}  // namespace
+
+// out = D in on every lattice of the batch (tile size chosen by the autotuner
+// on the first call, which must not be inside a stream capture)
+lqcd_status dirac_batch_D(lqcd_ctx *hc, DBatch *b, const int *active)
+{
+    if (b->choice < 0) {
+        std::string key = "k_hop_batch/p" + std::to_string((int)b->p) + "/n" + std::to_string(b->nlat) + "/s" +
+                          std::to_string(b->sites);
+        TuneChoice tc;
+        if (tune_lookup(key, &tc)) {
+            b->choice = tc.variant;
+        } else {
+            b->choice = 1;
+            if (tune_enabled()) {
+                float best = 1e30f;
+                for (int t = 0; t < 3; t++) {
+                    float us;
+                    LQCD_TRY(tune_time(hc, [&]() { return batch_launch(hc, b, t, active); }, 3, &us));
+                    if (tune_verbose()) fprintf(stderr, "tune %s: tile %d %.1f us\n", key.c_str(), kBatchTile[t], us);
+                    if (us < best) {
+                        best = us;
+                        b->choice = t;
+                    }
+                }
+                tc.variant = b->choice;
+                tc.tx = kBatchTile[b->choice];
+                tc.us = best;
+                tune_store(key, tc);
+            }
+        }
+    }
+    return batch_launch(hc, b, b->choice, active);
 }

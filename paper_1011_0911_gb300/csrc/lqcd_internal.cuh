@@ -203,6 +203,19 @@ lqcd_status sap_axpby_native(lqcd_ctx *c, lqcd_prec p, const void *eta, void *r)
 void sap_free_plans(lqcd_ctx *c);
 lqcd_status sap_apply(lqcd_ctx *c, const lqcd_sap_params *sp, const void *eta_native,
                       void *psi_native, int nrhs = 1);
+// batched operators over several lattices; hc: the batch's own context (stream,
+// error text, launch counter); arenas hold the lattices' native full fields at
+// offsets off[l] (in native spinor units of the precision)
+struct DBatch;
+lqcd_status dirac_batch_create(lqcd_ctx *hc, lqcd_ctx *const *ctx, int n, lqcd_prec p, const void *in, void *out,
+                               const long *off, DBatch **out_b);
+lqcd_status dirac_batch_D(lqcd_ctx *hc, DBatch *b, const int *active_dev);
+void dirac_batch_free(DBatch *b);
+struct SapBatch;
+lqcd_status sap_batch_create(lqcd_ctx *hc, lqcd_ctx *const *ctx, int n, const lqcd_sap_params *sp, void *r,
+                             void *psi, void *delta, const long *off, SapBatch **out_b);
+lqcd_status sap_batch_apply(lqcd_ctx *hc, SapBatch *b, const void *eta, size_t bytes, const int *active_dev);
+void sap_batch_free(SapBatch *b);
 // learned preconditioner
 void net_free(lqcd_ctx *c);
 lqcd_status net_apply_native(lqcd_ctx *c, const double2 *rho, double2 *phi, int nrhs);

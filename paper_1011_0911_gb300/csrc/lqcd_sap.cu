@@ -12,6 +12,7 @@
 // H_blk keeps only hops whose both ends lie in the block (Dirichlet); a block
 // that spans a whole lattice direction keeps the wrapped hop of that direction.
 #include <algorithm>
+#include <vector>
 
 #include "lqcd_f16s.cuh"
 #include "lqcd_internal.cuh"
@@ -716,8 +717,9 @@ __device__ __forceinline__ void half_add(SP *f, long Vh, long r, int h, const cx
     half_store(f, Vh, r, h, t);
 }
 
+// block list entry bi of a.blocks, right-hand side rhs; blockDim.x = 2 nh
 template <int P>
-__global__ void __launch_bounds__(2 * SAPS_NH, 1) k_sap_block_s(SapArgs<P> a)
+__device__ __forceinline__ void sap_block_s_body(const SapArgs<P> &a, int bi, int rhs)
 {
     using SP = typename SapT<P>::SP;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -726,13 +728,13 @@ __global__ void __launch_bounds__(2 * SAPS_NH, 1) k_sap_block_s(SapArgs<P> a)
     const int nh = B.nh;
     const long Vh = a.g.Vh;
     const long half = SapT<P>::half(Vh);
-    const long foff = blockIdx.y * a.fstride;
+    const long foff = rhs * a.fstride;
     SP *r_e = a.r + foff, *r_o = a.r + foff + half;
     SP *psi_e = a.psi + foff, *psi_o = a.psi + foff + half;
     SP *d_e = a.delta + foff, *d_o = a.delta + foff + half;
     int org[4];
     {
-        int t = a.blocks[blockIdx.x];
+        int t = a.blocks[bi];
         int c3 = t % B.nb[3];
         t /= B.nb[3];
         int c2 = t % B.nb[2];
@@ -915,21 +917,27 @@ __global__ void __launch_bounds__(2 * SAPS_NH, 1) k_sap_block_s(SapArgs<P> a)
     }
 }
 
-// r(x) -= sum of the hops into x from neighbours y that lie in another block
-// of colour col (delta holds chi there).  One thread per (site, rhs).
 template <int P>
-__global__ void __launch_bounds__(128) k_sap_face(SapArgs<P> a, int col)
+__global__ void __launch_bounds__(2 * SAPS_NH, 1) k_sap_block_s(SapArgs<P> a)
+{
+    sap_block_s_body<P>(a, blockIdx.x, blockIdx.y);
+}
+
+// r(x) -= sum of the hops into x from neighbours y that lie in another block
+// of colour col (delta holds chi there).  One thread per (site, rhs); i is the
+// parity-major site index 0 .. V-1.
+template <int P>
+__device__ __forceinline__ void sap_face_body(const SapArgs<P> &a, int col, long i, int rhs)
 {
     using R = typename SapT<P>::R;
     using SP = typename SapT<P>::SP;
     const BlkGeom &B = a.B;
-    long i = blockIdx.x * (long)blockDim.x + threadIdx.x;   // 0 .. V-1: parity-major
     if (i >= 2L * a.g.Vh) return;
     const long Vh = a.g.Vh;
     const int par = i >= Vh;
     const long rk = par ? i - Vh : i;
     const long half = SapT<P>::half(Vh);
-    const long foff = blockIdx.y * a.fstride;
+    const long foff = rhs * a.fstride;
     int x[4];
     rank_coords(a.g, par, (int)rk, x);
     int bx[4];
@@ -967,6 +975,50 @@ __global__ void __launch_bounds__(128) k_sap_face(SapArgs<P> a, int col)
 #pragma unroll
     for (int c = 0; c < 12; c++) acc[c] = R(0.5) * acc[c];
     gadd(a.r + foff + par * half, Vh, rk, acc);
+}
+
+template <int P>
+__global__ void __launch_bounds__(128) k_sap_face(SapArgs<P> a, int col)
+{
+    sap_face_body<P>(a, col, blockIdx.x * (long)blockDim.x + threadIdx.x, blockIdx.y);
+}
+
+// ------------------------------------------------------------------ batches
+// Several lattices in one launch.  args[2 l + col]: the SAP arguments of
+// lattice l for the blocks of colour col.  Persistent CTAs take work items from
+// a device counter (*queue, zero before the launch) until the list is empty;
+// items of lattices whose active flag is 0 are skipped.
+template <int P>
+__global__ void __launch_bounds__(2 * SAPS_NH, 1)
+    k_sap_block_s_batch(const SapArgs<P> *args, int col, const int2 *items, int nitems, const int *active, int *queue)
+{
+    __shared__ int s_item;
+    __shared__ SapArgs<P> sa;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(queue, 1);
+        __syncthreads();
+        const int it = s_item;
+        if (it >= nitems) return;
+        const int2 w = items[it];   // (lattice, index in its list of colour col)
+        const bool on = !active || active[w.x];
+        if (on && threadIdx.x == 0) sa = args[2 * w.x + col];
+        __syncthreads();
+        if (on) sap_block_s_body<P>(sa, w.y, 0);
+        __syncthreads();
+    }
+}
+
+// face items: (lattice, first parity-major site of a 128-site tile)
+template <int P>
+__global__ void __launch_bounds__(128)
+    k_sap_face_batch(const SapArgs<P> *args, int col, const int2 *items, int nitems, const int *active)
+{
+    const int2 w = items[blockIdx.x];
+    if (active && !active[w.x]) return;
+    __shared__ SapArgs<P> sa;
+    if (threadIdx.x == 0) sa = args[2 * w.x + col];
+    __syncthreads();
+    sap_face_body<P>(sa, col, (long)w.y + threadIdx.x, 0);
 }
 
 // LQCD_SAP_GENERIC=1 selects the generic (L1-cached) FP32 block kernel
@@ -1158,6 +1210,148 @@ lqcd_status sap_apply(lqcd_ctx *c, const lqcd_sap_params *sp, const void *eta, v
     if (sp->prec == LQCD_F32) return sap_run<LQCD_F32>(c, *P, sp->ncy, sp->nmr, eta, psi, r, delta, nrhs);
     if (sp->prec == LQCD_F16S) return sap_run<LQCD_F16S>(c, *P, sp->ncy, sp->nmr, eta, psi, r, delta, nrhs);
     return set_err(c, LQCD_ERR_ARG, "SAP precision %d not supported", (int)sp->prec);
+}
+
+// ------------------------------------------------------------------ batches
+struct SapBatch {
+    lqcd_prec p = LQCD_F16S;
+    int ncy = 4, nmr = 5, nh = 0, nsm = 0;
+    void *args = nullptr;                  // SapArgs<p>[2 nlat]
+    int2 *blk[2] = {nullptr, nullptr};     // (lattice, index in its colour list)
+    int nblk[2] = {0, 0};
+    int2 *face = nullptr;                  // (lattice, first site of a 128-site tile)
+    int nface = 0;
+    int *queue = nullptr;                  // one work counter per block launch of an application
+    void *r = nullptr, *psi = nullptr, *delta = nullptr;
+};
+
+void sap_batch_free(SapBatch *b)
+{
+    if (!b) return;
+    cudaFree(b->args);
+    cudaFree(b->blk[0]);
+    cudaFree(b->blk[1]);
+    cudaFree(b->face);
+    cudaFree(b->queue);
+    delete b;
+}
+
+namespace {
+template <int P>
+lqcd_status sap_batch_args(lqcd_ctx *hc, lqcd_ctx *const *ctx, int n, const lqcd_sap_params *sp, SapBatch *b,
+                           const long *off)
+{
+    using SP = typename SapT<P>::SP;
+    std::vector<SapArgs<P>> v;
+    std::vector<int2> it[2], face;
+    for (int l = 0; l < n; l++) {
+        SapPlan *pl;
+        LQCD_TRY(get_plan(ctx[l], sp->bs, &pl));
+        if (b->nh == 0) b->nh = pl->B.nh;
+        if (pl->B.nh != b->nh || b->nh > SAPS_NH || (2 * b->nh) % 32)
+            return set_err(hc, LQCD_ERR_ARG, "batched SAP needs one block shape of <= %d sites per parity", SAPS_NH);
+        for (int col = 0; col < 2; col++) {
+            SapArgs<P> a;
+            a.g = ctx[l]->g;
+            a.B = pl->B;
+            a.blocks = pl->blocks_dev + (col == 0 ? 0 : pl->count[0]);
+            a.r = (SP *)b->r + off[l];
+            a.psi = (SP *)b->psi + off[l];
+            a.delta = (SP *)b->delta + off[l];
+            a.fstride = 0;
+            if constexpr (P == LQCD_F32) {
+                a.U = ctx[l]->U32;
+                a.Ae = ctx[l]->A32[0];
+                a.Aio = ctx[l]->Ai32[1];
+            } else {
+                a.U = ctx[l]->U16;
+                a.Ae = ctx[l]->A16[0];
+                a.Aio = ctx[l]->Ai16[1];
+            }
+            a.nmr = sp->nmr;
+            v.push_back(a);
+            for (int i = 0; i < pl->count[col]; i++) it[col].push_back(make_int2(l, i));
+        }
+        for (int s0 = 0; s0 < 2 * ctx[l]->g.Vh; s0 += 128) face.push_back(make_int2(l, s0));
+    }
+    LQCD_CUDA_CHECK(hc, cudaMalloc(&b->args, v.size() * sizeof(v[0])));
+    LQCD_CUDA_CHECK(hc, cudaMemcpy(b->args, v.data(), v.size() * sizeof(v[0]), cudaMemcpyHostToDevice));
+    for (int col = 0; col < 2; col++) {
+        b->nblk[col] = (int)it[col].size();
+        LQCD_CUDA_CHECK(hc, cudaMalloc(&b->blk[col], std::max<size_t>(1, it[col].size()) * sizeof(int2)));
+        LQCD_CUDA_CHECK(hc, cudaMemcpy(b->blk[col], it[col].data(), it[col].size() * sizeof(int2), cudaMemcpyHostToDevice));
+    }
+    b->nface = (int)face.size();
+    LQCD_CUDA_CHECK(hc, cudaMalloc(&b->face, face.size() * sizeof(int2)));
+    LQCD_CUDA_CHECK(hc, cudaMemcpy(b->face, face.data(), face.size() * sizeof(int2), cudaMemcpyHostToDevice));
+    return LQCD_OK;
+}
+
+template <int P>
+lqcd_status sap_batch_run(lqcd_ctx *hc, SapBatch *b, const int *active)
+{
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_sap_block_s_batch<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(SapSmem));
+        attr = true;
+    }
+    const auto *args = (const SapArgs<P> *)b->args;
+    const int last_col = b->nblk[1] > 0 ? 1 : 0;
+    for (int cyc = 0; cyc < b->ncy; cyc++)
+        for (int col = 0; col < 2; col++) {
+            if (b->nblk[col] == 0) continue;
+            const int grid = std::min(b->nblk[col], b->nsm);
+            k_sap_block_s_batch<P><<<grid, 2 * b->nh, sizeof(SapSmem), hc->stream>>>(
+                args, col, b->blk[col], b->nblk[col], active, b->queue + 2 * cyc + col);
+            hc->n_kernel_launches++;
+            LQCD_LAUNCH_CHECK(hc);
+            if (cyc == b->ncy - 1 && col == last_col) continue;
+            k_sap_face_batch<P><<<b->nface, 128, 0, hc->stream>>>(args, col, b->face, b->nface, active);
+            hc->n_kernel_launches++;
+            LQCD_LAUNCH_CHECK(hc);
+        }
+    return LQCD_OK;
+}
+}  // namespace
+
+lqcd_status sap_batch_create(lqcd_ctx *hc, lqcd_ctx *const *ctx, int n, const lqcd_sap_params *sp, void *r,
+                             void *psi, void *delta, const long *off, SapBatch **out_b)
+{
+    if (sp->prec != LQCD_F32 && sp->prec != LQCD_F16S)
+        return set_err(hc, LQCD_ERR_ARG, "batched SAP runs in F32 or F16S");
+    if (sp->ncy < 1 || sp->nmr < 0) return set_err(hc, LQCD_ERR_ARG, "bad SAP cycle counts");
+    SapBatch *b = new SapBatch();
+    b->p = sp->prec;
+    b->ncy = sp->ncy;
+    b->nmr = sp->nmr;
+    b->r = r;
+    b->psi = psi;
+    b->delta = delta;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&b->nsm, cudaDevAttrMultiProcessorCount, dev);
+    lqcd_status st = sp->prec == LQCD_F32 ? sap_batch_args<LQCD_F32>(hc, ctx, n, sp, b, off)
+                                          : sap_batch_args<LQCD_F16S>(hc, ctx, n, sp, b, off);
+    if (st == LQCD_OK && cudaMalloc(&b->queue, 2 * sp->ncy * sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        st = set_err(hc, LQCD_ERR_NOMEM, "batched SAP work counters");
+    }
+    if (st != LQCD_OK) {
+        sap_batch_free(b);
+        return st;
+    }
+    *out_b = b;
+    return LQCD_OK;
+}
+
+// psi = M_sap eta on every lattice whose active flag is set (the arenas given
+// at creation; eta: an arena of the same layout, bytes long)
+lqcd_status sap_batch_apply(lqcd_ctx *hc, SapBatch *b, const void *eta, size_t bytes, const int *active)
+{
+    LQCD_CUDA_CHECK(hc, cudaMemsetAsync(b->psi, 0, bytes, hc->stream));
+    LQCD_CUDA_CHECK(hc, cudaMemcpyAsync(b->r, eta, bytes, cudaMemcpyDeviceToDevice, hc->stream));
+    LQCD_CUDA_CHECK(hc, cudaMemsetAsync(b->queue, 0, 2 * b->ncy * sizeof(int), hc->stream));
+    return b->p == LQCD_F32 ? sap_batch_run<LQCD_F32>(hc, b, active) : sap_batch_run<LQCD_F16S>(hc, b, active);
 }
 
 void sap_free_plans(lqcd_ctx *c)

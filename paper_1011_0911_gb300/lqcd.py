@@ -60,6 +60,11 @@ class SolveInfo(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class BatchParams(C.Structure):
+    _fields_ = [("nkv", C.c_int), ("nmx", C.c_int), ("tol", C.c_double), ("sap", SapParams),
+                ("use_graph", C.c_int), ("wait_timeout_s", C.c_double), ("stall_test", C.c_int)]
+
+
 class NetDesc(C.Structure):
     _fields_ = [("nlayers", C.c_int), ("chans", C.c_int * 5), ("act", C.c_int)]
 
@@ -127,6 +132,16 @@ def lib():
         L.lqcd_kernel_launches.restype = C.c_long
         L.lqcd_dfl_stats.argtypes = [P, C.POINTER(C.c_long), C.POINTER(C.c_long)]
         L.lqcd_dfl_stats.restype = C.c_int
+        L.lqcd_batch_create.argtypes = [P, I, C.POINTER(BatchParams), P, C.POINTER(P)]
+        L.lqcd_batch_create.restype = C.c_int
+        L.lqcd_batch_destroy.argtypes = [P]
+        L.lqcd_batch_destroy.restype = C.c_int
+        L.lqcd_batch_last_error.argtypes = [P]
+        L.lqcd_batch_last_error.restype = C.c_char_p
+        L.lqcd_batch_solve_dhat.argtypes = [P, P, P, C.POINTER(SolveInfo)]
+        L.lqcd_batch_solve_dhat.restype = C.c_int
+        L.lqcd_batch_stats.argtypes = [P, C.POINTER(I), C.POINTER(I), C.POINTER(C.c_long)]
+        L.lqcd_batch_stats.restype = C.c_int
         _lib = L
     return _lib
 
@@ -387,3 +402,54 @@ class Context:
                 sap_prec=F64, inner=F64, check=True):
         return self._solve(lib().lqcd_solve_D, eta, self.V, solver, tol, nkv, nmx, bs, ncy, nmr, sap_prec, inner,
                            check)
+
+
+class Batch:
+    """Several lattices (Contexts with clover terms) solved together by the
+    batched SAP-GCR: one launch per phase over all lattices' work items."""
+
+    def __init__(self, ctxs, nkv=16, nmx=4096, tol=1e-10, bs=(4, 4, 4, 4), ncy=4, nmr=5, sap_prec=F16S,
+                 use_graph=True, wait_timeout_s=2.0, stall_test=False, stream=None):
+        self.ctxs = list(ctxs)
+        n = len(self.ctxs)
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        p = BatchParams(nkv, nmx, tol, sap_params(bs, ncy, nmr, sap_prec), 1 if use_graph else 0,
+                        wait_timeout_s, 1 if stall_test else 0)
+        arr = (C.c_void_p * n)(*[c._h for c in self.ctxs])
+        h = C.c_void_p()
+        st = lib().lqcd_batch_create(arr, n, C.byref(p), C.c_void_p(stream.cuda_stream), C.byref(h))
+        if st != 0:
+            msg = lib().lqcd_last_error(self.ctxs[0]._h)
+            raise LqcdError(st, f"lqcd_batch_create: {msg.decode() if msg else ''}")
+        self._h = h
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.lqcd_batch_destroy(self._h)
+            self._h = None
+
+    def solve_dhat(self, etas, check=False):
+        """etas: one canonical even FP64 field per lattice; returns (psis, infos, status)."""
+        etas = [e.to(torch.complex128).contiguous() for e in etas]
+        psis = [torch.empty_like(e) for e in etas]
+        n = len(etas)
+        assert n == len(self.ctxs)
+        ea = (C.c_void_p * n)(*[e.data_ptr() for e in etas])
+        pa = (C.c_void_p * n)(*[x.data_ptr() for x in psis])
+        info = (SolveInfo * n)()
+        st = lib().lqcd_batch_solve_dhat(self._h, ea, pa, info)
+        if check and st != 0:
+            msg = lib().lqcd_batch_last_error(self._h)
+            raise LqcdError(st, f"batch solve: {msg.decode() if msg else ''}")
+        return psis, [i.as_dict() for i in info], st
+
+    def last_error(self) -> str:
+        msg = lib().lqcd_batch_last_error(self._h)
+        return msg.decode() if msg else ""
+
+    def stats(self):
+        cy, rp, ln = C.c_int(), C.c_int(), C.c_long()
+        lib().lqcd_batch_stats(self._h, C.byref(cy), C.byref(rp), C.byref(ln))
+        return {"cycles": cy.value, "graph_replays": rp.value, "launches": ln.value}
