@@ -278,6 +278,75 @@ def run_batch(args):
     print(json.dumps(res))
 
 
+def run_net(args):
+    """Learned preconditioner workload: a 3-layer parallel-transport network
+    (1 -> 2 -> 2 -> 1 spinor fields, BF16, FP32 accumulation) trained on the GPU
+    at 32x16^3 on 10 gauge fields x 200 sources (2000 pairs; targets M_sap
+    source made by the library's SAP), then used at 64x32^3 (kappa = 0.1363)
+    as the smoother of the deflated GCR, deflated SAP where its step fails.
+    Reported beside the same deflated GCR with SAP, and plain SAP-GCR."""
+    import numpy as np
+    import torch
+    from paper_1011_0911_gb300 import lqcd, synth
+    kappa, chans = 0.1363, (1, 2, 2, 1)
+    nw = lqcd.Context.net_weight_count(chans)
+    g = synth.gaussians(7, synth.STREAM_NET, 2 * nw)
+    W = 0.02 * (g[0::2] + 1j * g[1::2])
+    off = 0
+    for l in range(len(chans) - 1):
+        W[off:off + chans[l + 1] * chans[l] * 144].reshape(chans[l + 1], chans[l], 9, 4, 4)[0, 0, 0] += 0.7 * np.eye(4)
+        off += chans[l + 1] * chans[l] * 144
+    W = W.astype(np.complex64)
+    tdims = (32, 16, 16, 16)
+    hist, train_s, gen_s = [], 0.0, 0.0
+    for f in range(args.nfields):
+        t0 = time.perf_counter()
+        c = lqcd.Context(tdims)
+        c.set_gauge(torch.from_numpy(synth.su3_links(tdims, 100 + f)).cuda())
+        c.clover_invert(kappa, CSW)
+        gen = torch.Generator(device="cuda").manual_seed(1000 + f)
+        src = torch.randn((args.npairs, c.V, 4, 3), dtype=torch.complex128, device="cuda", generator=gen)
+        torch.cuda.synchronize()
+        gen_s += time.perf_counter() - t0
+        t0 = time.perf_counter()
+        c.net_set(chans, W, act=lqcd.BF16)
+        h = c.net_train(src, steps=args.train_steps, batch=8, lr=2e-3, sap_prec=lqcd.F32)
+        torch.cuda.synchronize()
+        train_s += time.perf_counter() - t0
+        W = c.net_get()
+        hist += [float(x) for x in h]
+        del src, c
+    dims = (64, 32, 32, 32)
+    ctx = lqcd.Context(dims)
+    ctx.set_gauge(torch.from_numpy(synth.su3_links(dims, 0)).cuda())
+    ctx.clover_invert(kappa, CSW)
+    ctx.net_set(chans, W, act=lqcd.BF16)
+    eta = torch.from_numpy(synth.gaussian_spinor(ctx.Vh, 1)).cuda()
+    Ns = 20
+    v0 = torch.from_numpy(synth.gaussian_spinor(Ns * ctx.V, 100, synth.STREAM_SUBSPACE).reshape(Ns, ctx.V, 4, 3)).cuda()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ctx.dfl_build(v0, bs=(4, 4, 4, 4), ninv=8, ncy=4, nmr=4, prec=lqcd.F32, coarse_tol=1e-2, coarse_nmx=64,
+                  coarse_prec=lqcd.F32)
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t0
+    out = {"mode": "net", "train_lattice": "32x16x16x16", "train_fields": args.nfields, "pairs": args.nfields * args.npairs,
+           "train_steps": args.nfields * args.train_steps, "train_s": round(train_s, 3),
+           "loss_first": round(float(np.mean(hist[:5])), 4), "loss_last": round(float(np.mean(hist[-5:])), 4),
+           "lattice": "64x32x32x32", "kappa": kappa, "subspace_build_s": round(build_s, 3)}
+    forms = [("dfl_net", lqcd.SOLVER_DFL_NET_GCR), ("dfl_sap", lqcd.SOLVER_DFL_SAP_GCR), ("sap", lqcd.SOLVER_SAP_GCR)]
+    for name, sid in forms:
+        ctx.solve_dhat(eta, solver=sid, tol=1e-10, sap_prec=lqcd.F32, inner=lqcd.F32, check=False)   # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, info, st = ctx.solve_dhat(eta, solver=sid, tol=1e-10, sap_prec=lqcd.F32, inner=lqcd.F32, check=False)
+        torch.cuda.synchronize()
+        out[name] = {"seconds": round(time.perf_counter() - t0, 4), "iters": info[0]["iters"],
+                     "net_fallbacks": info[0]["net_fallbacks"], "relres_dhat": info[0]["relres_dhat"], "status": st}
+    out["gain_dfl_net_vs_dfl_sap"] = round(out["dfl_sap"]["seconds"] / out["dfl_net"]["seconds"], 3)
+    print(json.dumps(out))
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -304,9 +373,12 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
     ap.add_argument("--no-solve", action="store_true", help="skip the time-to-solution comparison")
     ap.add_argument("--lattice", default="48x24x24x24", help="TxL1xL2xL3 (profiling runs use smaller ones)")
-    ap.add_argument("--mode", default="dhat", choices=["dhat", "solve", "batch"],
+    ap.add_argument("--mode", default="dhat", choices=["dhat", "solve", "batch", "net"],
                     help="solve: one time-to-solution run; batch: the uneven multi-lattice batch")
     ap.add_argument("--nlat", type=int, default=16, help="lattices of the batch mode")
+    ap.add_argument("--nfields", type=int, default=10, help="net mode: training gauge fields")
+    ap.add_argument("--npairs", type=int, default=200, help="net mode: sources per training field")
+    ap.add_argument("--train-steps", type=int, default=50, help="net mode: Adam steps per training field")
     ap.add_argument("--no-graph", action="store_true", help="batch mode: eager launches instead of graph replay")
     ap.add_argument("--solver", default="dfl", choices=["cgnr", "sap", "dfl"])
     ap.add_argument("--kappa", type=float, default=None)
@@ -324,6 +396,8 @@ def main():
         return run_solve(args)
     if args.mode == "batch":
         return run_batch(args)
+    if args.mode == "net":
+        return run_net(args)
 
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))

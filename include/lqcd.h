@@ -230,7 +230,10 @@ typedef enum {
     LQCD_SOLVER_CGNR = 0,     /* even-odd CG on Dhat^dag Dhat (FP64) */
     LQCD_SOLVER_SAP_GCR = 1,  /* flexible GCR, SAP preconditioner */
     LQCD_SOLVER_DFL_SAP_GCR = 2, /* flexible GCR, deflated SAP preconditioner */
-    LQCD_SOLVER_NET_GCR = 3   /* flexible GCR, network preconditioner, SAP where it fails */
+    LQCD_SOLVER_NET_GCR = 3,  /* flexible GCR, network preconditioner, SAP where it fails */
+    LQCD_SOLVER_DFL_NET_GCR = 4  /* flexible GCR, deflated preconditioner with the network in place of
+                                    SAP (N(rho - D Pi A^-1 Pi^dag rho) + Pi A^-1 Pi^dag rho), the
+                                    deflated SAP preconditioner where the network's step fails */
 } lqcd_solver;
 
 typedef struct {

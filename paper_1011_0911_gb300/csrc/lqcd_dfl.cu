@@ -900,7 +900,8 @@ lqcd_status precond_sap(lqcd_ctx *c, const lqcd_sap_params *sp, const double2 *r
 }  // namespace
 
 // phi_r = M_dfl rho_r for nrhs native full FP64 fields
-lqcd_status dfl_precond_native(lqcd_ctx *c, const lqcd_sap_params *sp, const double2 *rho, double2 *phi, int nrhs)
+lqcd_status dfl_precond_native(lqcd_ctx *c, const lqcd_sap_params *sp, const double2 *rho, double2 *phi, int nrhs,
+                               bool net)
 {
     DflState *d = c->dfl;
     if (!d) return set_err(c, LQCD_ERR_STATE, "deflation subspace not built");
@@ -928,7 +929,10 @@ lqcd_status dfl_precond_native(lqcd_ctx *c, const lqcd_sap_params *sp, const dou
         LQCD_TRY(convert_native(c, sp->prec, LQCD_F64, b2, w, 2 * nrhs));
     }
     LQCD_TRY(blas_sub(c, 2 * nf * nrhs, (const double *)rho, (const double *)w, (double *)w));
-    LQCD_TRY(precond_sap(c, sp, w, phi, nrhs));
+    if (net)
+        LQCD_TRY(net_apply_native(c, w, phi, nrhs));
+    else
+        LQCD_TRY(precond_sap(c, sp, w, phi, nrhs));
     return blas_axpy(c, 2 * nf * nrhs, 1.0, 0, (const double *)u, (double *)phi);
 }
 

@@ -221,5 +221,6 @@ void net_free(lqcd_ctx *c);
 lqcd_status net_apply_native(lqcd_ctx *c, const double2 *rho, double2 *phi, int nrhs);
 // deflation
 void dfl_free(lqcd_ctx *c);
+// smoother: SAP (net = false) or the network (net = true) after the deflation step
 lqcd_status dfl_precond_native(lqcd_ctx *c, const lqcd_sap_params *sp, const double2 *rho,
-                               double2 *phi, int nrhs);
+                               double2 *phi, int nrhs, bool net = false);

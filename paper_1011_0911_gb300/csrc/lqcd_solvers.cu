@@ -126,6 +126,7 @@ lqcd_status precond(lqcd_ctx *c, const lqcd_solver_params *sp, const double2 *rh
     const lqcd_sap_params &sap = sp->sap;
     if (sp->solver == LQCD_SOLVER_DFL_SAP_GCR) return dfl_precond_native(c, &sap, rho, phi, nrhs);
     if (sp->solver == LQCD_SOLVER_NET_GCR) return net_apply_native(c, rho, phi, nrhs);
+    if (sp->solver == LQCD_SOLVER_DFL_NET_GCR) return dfl_precond_native(c, &sap, rho, phi, nrhs, true);
     if (sap.prec == LQCD_F64) return sap_apply(c, &sap, rho, phi, nrhs);
     void *a, *b;
     size_t fb = 2 * native_half_bytes(c, sap.prec) * nrhs;
@@ -285,7 +286,7 @@ lqcd_status gcr_native(lqcd_ctx *c, const lqcd_solver_params *sp, const std::vec
                                  dots.data());
             };
             LQCD_TRY(orth());
-            if (sp->solver == LQCD_SOLVER_NET_GCR) {
+            if (sp->solver == LQCD_SOLVER_NET_GCR || sp->solver == LQCD_SOLVER_DFL_NET_GCR) {
                 // the network's direction must cut |rho| to 0.95 |rho| at least, i.e.
                 // |c_k|^2 >= (1 - 0.95^2) |rho|^2; where it does not, SAP replaces it
                 std::vector<int> reject;
@@ -301,7 +302,8 @@ lqcd_status gcr_native(lqcd_ctx *c, const lqcd_solver_params *sp, const std::vec
                     void *fb;
                     LQCD_TRY(ws_get(c, WS_NET_FALLBACK, (size_t)bf * sizeof(double2), &fb));
                     lqcd_solver_params sap_only = *sp;
-                    sap_only.solver = LQCD_SOLVER_SAP_GCR;
+                    sap_only.solver = sp->solver == LQCD_SOLVER_DFL_NET_GCR ? LQCD_SOLVER_DFL_SAP_GCR
+                                                                            : LQCD_SOLVER_SAP_GCR;
                     LQCD_TRY(precond(c, &sap_only, rho, (double2 *)fb, nrhs));
                     for (int r : reject) {
                         LQCD_CUDA_CHECK(c, cudaMemcpyAsync(ph + r * nf, (double2 *)fb + r * nf, nf * sizeof(double2),
@@ -420,10 +422,11 @@ lqcd_status check_params(lqcd_ctx *c, const lqcd_solver_params *p, int nrhs)
     if (!p || nrhs < 1) return set_err(c, LQCD_ERR_ARG, "bad solver arguments");
     if (!(p->tol > 0)) return set_err(c, LQCD_ERR_ARG, "tol must be > 0");
     if (!c->have_clover) return set_err(c, LQCD_ERR_STATE, "clover term not built");
-    if (p->solver == LQCD_SOLVER_DFL_SAP_GCR && !c->dfl)
+    if ((p->solver == LQCD_SOLVER_DFL_SAP_GCR || p->solver == LQCD_SOLVER_DFL_NET_GCR) && !c->dfl)
         return set_err(c, LQCD_ERR_STATE, "deflation subspace not built");
-    if (p->solver == LQCD_SOLVER_NET_GCR && !c->net) return set_err(c, LQCD_ERR_STATE, "network not set");
-    if (p->solver < LQCD_SOLVER_CGNR || p->solver > LQCD_SOLVER_NET_GCR)
+    if ((p->solver == LQCD_SOLVER_NET_GCR || p->solver == LQCD_SOLVER_DFL_NET_GCR) && !c->net)
+        return set_err(c, LQCD_ERR_STATE, "network not set");
+    if (p->solver < LQCD_SOLVER_CGNR || p->solver > LQCD_SOLVER_DFL_NET_GCR)
         return set_err(c, LQCD_ERR_ARG, "solver %d", (int)p->solver);
     if (p->solver != LQCD_SOLVER_CGNR && (p->inner != LQCD_F64 && p->inner != LQCD_F32))
         return set_err(c, LQCD_ERR_ARG, "inner precision %d", (int)p->inner);

@@ -18,7 +18,7 @@ import torch
 from . import build_lib
 
 F64, F32, F16S, BF16 = 0, 1, 2, 3
-SOLVER_CGNR, SOLVER_SAP_GCR, SOLVER_DFL_SAP_GCR, SOLVER_NET_GCR = 0, 1, 2, 3
+SOLVER_CGNR, SOLVER_SAP_GCR, SOLVER_DFL_SAP_GCR, SOLVER_NET_GCR, SOLVER_DFL_NET_GCR = 0, 1, 2, 3, 4
 
 STATUS = {
     0: "OK", 1: "ERR_ARG", 2: "ERR_CUDA", 3: "ERR_NOMEM", 4: "ERR_SINGULAR_CLOVER",

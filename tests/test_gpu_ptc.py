@@ -177,3 +177,22 @@ def test_net_gcr_solve(trained):
         assert 0 <= inf["net_fallbacks"] <= inf["iters"]
         r = eta[k] - P.ctx.apply_D(psi[k][None])[0]
         assert (torch.linalg.vector_norm(r) / torch.linalg.vector_norm(eta[k])).item() <= 1.5e-10
+
+
+def test_deflated_net_gcr_solve(trained):
+    """The network as the smoother of the deflated preconditioner
+    (N(rho - D Pi A^-1 Pi^dag rho) + Pi A^-1 Pi^dag rho), deflated SAP where
+    its step fails: FP64 true residual at 1e-10."""
+    P, _ = trained
+    Ns = 8
+    v0 = torch.from_numpy(synth.gaussian_spinor(Ns * P.V, 3, synth.STREAM_SUBSPACE).reshape(Ns, P.V, 4, 3)).cuda()
+    P.ctx.dfl_build(v0, ninv=4, prec=lqcd.F32)
+    eta = torch.from_numpy(sources(P.V, 2, 650)).cuda()
+    psi, infos, st = P.ctx.solve_D(eta, solver=lqcd.SOLVER_DFL_NET_GCR, tol=1e-10, nkv=16, nmx=2000,
+                                   sap_prec=lqcd.F32)
+    assert st == 0
+    for k, inf in enumerate(infos):
+        assert inf["true_relres"] <= 1e-10
+        assert 0 <= inf["net_fallbacks"] <= inf["iters"]
+        r = eta[k] - P.ctx.apply_D(psi[k][None])[0]
+        assert (torch.linalg.vector_norm(r) / torch.linalg.vector_norm(eta[k])).item() <= 1.5e-10
