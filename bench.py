@@ -47,6 +47,20 @@ def dhat_bytes_per_site(prec: str, nrhs: int) -> int:
     return word * (link_words + 144 + 120 * nrhs)
 
 
+# ncu DRAM bytes (read + write) of one Dhat application per even site, FP32 with
+# 12 fields, from the 32x16^3 capture summarised in profiles/; valid for the
+# kernels as they were captured (k_hop DHAT1 + k_hop_mr DHAT2, NR = 2)
+TRAFFIC_F32_12_PER_SITE = 565.6e6 / 65536
+TRAFFIC_NOTE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of k_hop<DHAT1> + k_hop_mr<DHAT2> at "
+                "32x16^3 x 12 fields (565.6 MB), scaled by the even-site count")
+
+
+def traffic_of(prec, nrhs, Vh):
+    if prec == "f32" and nrhs == 12:
+        return int(TRAFFIC_F32_12_PER_SITE * Vh)
+    return None
+
+
 def load_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -160,23 +174,68 @@ def solve_once(ctx, lqcd, eta, solver, inner, Ns=20, ninv=8, ctol=1e-2, seed=100
     return res, psi
 
 
-def time_to_solve(ctx, lqcd, eta):
+def time_to_solve(ctx, lqcd, eta, net=None):
     """Time-to-solution of Dhat psi = eta for the 12 sources to a true relative
-    residual <= 1e-10 (checked in FP64), subspace build included:
+    residual <= 1e-10 (checked in FP64), subspace builds included:
       plain_f64 : deflated SAP-GCR, FP64 everywhere, one source at a time
       dfl_mixed : deflated SAP-GCR, FP32 SAP / subspace / little operator,
                   FP64 outer GCR, the 12 sources in one batched solve
+      learned   : dfl_mixed with the trained network as the smoother (deflated
+                  SAP where its step fails); training at 32x16^3 reported apart
+      sap_f16s  : SAP-GCR, FP16 (per-site scale) SAP, FP32 stencil, 12 batched
       chosen    : SAP-GCR, FP32 SAP and stencil, FP64 outer GCR, the 12
-                  sources in one batched solve (fastest measured form)"""
+                  sources in one batched solve (fastest measured form)
+    Every form is first run for two steps (and its subspace built once) so
+    that launch-shape tuning and workspace growth stay out of the timings."""
     import torch
+    from paper_1011_0911_gb300 import synth
     out = {}
+    one = eta[:1].contiguous()
+    for spr, inner in ((lqcd.F32, lqcd.F32), (lqcd.F16S, lqcd.F32), (lqcd.F64, lqcd.F64)):
+        ctx.solve_dhat(eta, solver=lqcd.SOLVER_SAP_GCR, tol=1e-10, nmx=2, sap_prec=spr, inner=inner, check=False)
+    v0 = torch.from_numpy(synth.gaussian_spinor(20 * ctx.V, 100, synth.STREAM_SUBSPACE).reshape(20, ctx.V, 4, 3)).cuda()
+    for prec in (lqcd.F64, lqcd.F32):
+        ctx.dfl_build(v0, bs=(4, 4, 4, 4), ninv=1, ncy=4, nmr=4, prec=prec, coarse_tol=1e-2, coarse_nmx=64,
+                      coarse_prec=prec)
+        e = one if prec == lqcd.F64 else eta
+        ctx.solve_dhat(e, solver=lqcd.SOLVER_DFL_SAP_GCR, tol=1e-10, nmx=2, sap_prec=prec, inner=prec, check=False)
+        if prec == lqcd.F32 and net is not None:
+            ctx.net_set(NET_CHANS, net["W"], act=lqcd.BF16)
+            ctx.solve_dhat(eta, solver=lqcd.SOLVER_DFL_NET_GCR, tol=1e-10, nmx=2, sap_prec=prec, inner=prec,
+                           check=False)
+    del v0
+    torch.cuda.synchronize()
     r, _ = solve_once(ctx, lqcd, eta, "sap", "f32")
     out["chosen"] = {"form": "SAP-GCR, FP32 SAP/stencil, FP64 GCR, 12 RHS batched", "seconds": r["total_s"],
                      "iters": max(r["iters"]), "max_relres_dhat": r["max_relres_dhat"], "status": r["status"]}
+    t0 = time.perf_counter()
+    _, info, st = ctx.solve_dhat(eta, solver=lqcd.SOLVER_SAP_GCR, tol=1e-10, sap_prec=lqcd.F16S, inner=lqcd.F32,
+                                 check=False)
+    torch.cuda.synchronize()
+    out["sap_f16s"] = {"form": "SAP-GCR, FP16 (per-site scale) SAP, FP32 stencil, FP64 GCR, 12 RHS batched",
+                       "seconds": round(time.perf_counter() - t0, 4), "iters": max(i["iters"] for i in info),
+                       "max_relres_dhat": max(i["relres_dhat"] for i in info), "status": st}
     r, _ = solve_once(ctx, lqcd, eta, "dfl", "f32", Ns=20, ninv=8, ctol=1e-2, cnmx=64, cprec="f32")
     out["dfl_mixed"] = {"form": "deflated SAP-GCR (Ns=20, 4^4 blocks), FP32 SAP/subspace/little operator, FP64 GCR, "
                                 "12 RHS batched", "seconds": r["total_s"], "build_s": r["build_s"],
                         "iters": max(r["iters"]), "max_relres_dhat": r["max_relres_dhat"], "status": r["status"]}
+    if net is not None:
+        # the same subspace, the network in place of the SAP smoother
+        ctx.net_set(NET_CHANS, net["W"], act=lqcd.BF16)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, info, st = ctx.solve_dhat(eta, solver=lqcd.SOLVER_DFL_NET_GCR, tol=1e-10, sap_prec=lqcd.F32,
+                                     inner=lqcd.F32, check=False)
+        torch.cuda.synchronize()
+        solve_s = time.perf_counter() - t0
+        out["learned"] = {"form": "deflated GCR (Ns=20), trained BF16 network as smoother, deflated FP32 SAP as "
+                                  "fallback, FP64 GCR, 12 RHS batched",
+                          "seconds": round(solve_s + r["build_s"], 4), "build_s": r["build_s"],
+                          "iters": max(i["iters"] for i in info),
+                          "net_fallbacks": sum(i["net_fallbacks"] for i in info),
+                          "max_relres_dhat": max(i["relres_dhat"] for i in info), "status": st,
+                          "training": {"lattice": "32x16x16x16", "pairs": net["pairs"], "seconds": net["train_s"],
+                                       "loss_first": net["loss_first"], "loss_last": net["loss_last"]}}
     total, build, iters, worst, st = 0.0, 0.0, 0, 0.0, 0
     for k in range(eta.shape[0]):
         if k == 0:
@@ -199,8 +258,9 @@ def time_to_solve(ctx, lqcd, eta):
     out["plain_f64"] = {"form": "deflated SAP-GCR (Ns=20, 4^4 blocks), FP64 throughout, one source at a time",
                         "seconds": round(total, 4), "build_s": build, "iters": iters, "max_relres_dhat": worst,
                         "status": st}
-    out["speedup_chosen_vs_plain_f64"] = round(out["plain_f64"]["seconds"] / out["chosen"]["seconds"], 2)
-    out["speedup_dfl_mixed_vs_plain_f64"] = round(out["plain_f64"]["seconds"] / out["dfl_mixed"]["seconds"], 2)
+    for k in ("chosen", "sap_f16s", "dfl_mixed", "learned"):
+        if k in out:
+            out["speedup_%s_vs_plain_f64" % k] = round(out["plain_f64"]["seconds"] / out[k]["seconds"], 2)
     out["tolerance"] = 1e-10
     return out
 
@@ -278,6 +338,44 @@ def run_batch(args):
     print(json.dumps(res))
 
 
+NET_CHANS = (1, 2, 2, 1)
+
+
+def train_net(lqcd, synth, kappa, nfields=10, npairs=200, steps=50):
+    """The network trained on the GPU at 32x16^3: nfields gauge fields x npairs
+    sources (drawn on the device), targets M_sap source made by the library's
+    SAP; weights carried from field to field.  Returns (W, loss history, s)."""
+    import numpy as np
+    import torch
+    chans = NET_CHANS
+    nw = lqcd.Context.net_weight_count(chans)
+    g = synth.gaussians(7, synth.STREAM_NET, 2 * nw)
+    W = 0.02 * (g[0::2] + 1j * g[1::2])
+    off = 0
+    for l in range(len(chans) - 1):
+        W[off:off + chans[l + 1] * chans[l] * 144].reshape(chans[l + 1], chans[l], 9, 4, 4)[0, 0, 0] += 0.7 * np.eye(4)
+        off += chans[l + 1] * chans[l] * 144
+    W = W.astype(np.complex64)
+    tdims = (32, 16, 16, 16)
+    hist, train_s = [], 0.0
+    for f in range(nfields):
+        c = lqcd.Context(tdims)
+        c.set_gauge(torch.from_numpy(synth.su3_links(tdims, 100 + f)).cuda())
+        c.clover_invert(kappa, CSW)
+        gen = torch.Generator(device="cuda").manual_seed(1000 + f)
+        src = torch.randn((npairs, c.V, 4, 3), dtype=torch.complex128, device="cuda", generator=gen)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        c.net_set(chans, W, act=lqcd.BF16)
+        h = c.net_train(src, steps=steps, batch=8, lr=2e-3, sap_prec=lqcd.F32)
+        torch.cuda.synchronize()
+        train_s += time.perf_counter() - t0
+        W = c.net_get()
+        hist += [float(x) for x in h]
+        del src, c
+    return W, hist, train_s
+
+
 def run_net(args):
     """Learned preconditioner workload: a 3-layer parallel-transport network
     (1 -> 2 -> 2 -> 1 spinor fields, BF16, FP32 accumulation) trained on the GPU
@@ -289,33 +387,7 @@ def run_net(args):
     import torch
     from paper_1011_0911_gb300 import lqcd, synth
     kappa, chans = 0.1363, (1, 2, 2, 1)
-    nw = lqcd.Context.net_weight_count(chans)
-    g = synth.gaussians(7, synth.STREAM_NET, 2 * nw)
-    W = 0.02 * (g[0::2] + 1j * g[1::2])
-    off = 0
-    for l in range(len(chans) - 1):
-        W[off:off + chans[l + 1] * chans[l] * 144].reshape(chans[l + 1], chans[l], 9, 4, 4)[0, 0, 0] += 0.7 * np.eye(4)
-        off += chans[l + 1] * chans[l] * 144
-    W = W.astype(np.complex64)
-    tdims = (32, 16, 16, 16)
-    hist, train_s, gen_s = [], 0.0, 0.0
-    for f in range(args.nfields):
-        t0 = time.perf_counter()
-        c = lqcd.Context(tdims)
-        c.set_gauge(torch.from_numpy(synth.su3_links(tdims, 100 + f)).cuda())
-        c.clover_invert(kappa, CSW)
-        gen = torch.Generator(device="cuda").manual_seed(1000 + f)
-        src = torch.randn((args.npairs, c.V, 4, 3), dtype=torch.complex128, device="cuda", generator=gen)
-        torch.cuda.synchronize()
-        gen_s += time.perf_counter() - t0
-        t0 = time.perf_counter()
-        c.net_set(chans, W, act=lqcd.BF16)
-        h = c.net_train(src, steps=args.train_steps, batch=8, lr=2e-3, sap_prec=lqcd.F32)
-        torch.cuda.synchronize()
-        train_s += time.perf_counter() - t0
-        W = c.net_get()
-        hist += [float(x) for x in h]
-        del src, c
+    W, hist, train_s = train_net(lqcd, synth, kappa, args.nfields, args.npairs, args.train_steps)
     dims = (64, 32, 32, 32)
     ctx = lqcd.Context(dims)
     ctx.set_gauge(torch.from_numpy(synth.su3_links(dims, 0)).cuda())
@@ -347,6 +419,90 @@ def run_net(args):
     print(json.dumps(out))
 
 
+def run_configs(args):
+    """The small configurations: Dhat per precision (one field, native
+    resident, CUDA events) at 8^4 and 32x16^3, the 8^4 FP64 CGNR solve and the
+    32x16^3 FP64 SAP-GCR solve to 1e-10 (plus the mixed forms), and the CPU
+    oracle on the host cores: Dhat at both sizes, the 8^4 CGNR solve, and the
+    32x16^3 SAP-GCR solve extrapolated from one SAP and one D application."""
+    import torch
+    import oracle as orc
+    from paper_1011_0911_gb300 import lqcd, synth
+    peak, peak_kind = load_peaks()
+    out = {"mode": "configs", "hbm_peak_gbs": peak, "peak_kind": peak_kind, "oracle_threads": orc.num_threads()}
+    for dims in ((8, 8, 8, 8), (32, 16, 16, 16)):
+        kappa = KAPPA_OF[dims]
+        U = synth.su3_links(dims, 0)
+        ctx = lqcd.Context(dims)
+        ctx.set_gauge(torch.from_numpy(U).cuda())
+        ctx.clover_invert(kappa, CSW)
+        tag = "x".join(map(str, dims))
+        res = {"kappa": kappa, "dhat": {}}
+        pe = synth.gaussian_spinor(ctx.Vh, 1)
+        for name, prec in (("f64", lqcd.F64), ("f32", lqcd.F32), ("f16s", lqcd.F16S)):
+            cdt = torch.complex128 if prec == lqcd.F64 else torch.complex64
+            nin = ctx.pack(torch.from_numpy(pe).to(cdt).cuda(), prec, 1)
+            nout = ctx.native_empty(prec, 1, 1)
+            for _ in range(20):
+                ctx.apply_Dhat_native(nin, nout, prec, 1)
+            steps = 200
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(ctx.stream)
+            for _ in range(steps):
+                ctx.apply_Dhat_native(nin, nout, prec, 1)
+            e1.record(ctx.stream)
+            torch.cuda.synchronize()
+            t = e0.elapsed_time(e1) / steps * 1e-3
+            b = dhat_bytes_per_site(name, 1) * ctx.Vh
+            res["dhat"][name] = {"us": round(t * 1e6, 2), "gflops": round(FLOP_PER_SITE * ctx.Vh / t / 1e9, 1),
+                                 "hbm_frac_algorithmic": round(b / t / 1e9 / peak, 3),
+                                 "note": "working set fits L2" if b < 100e6 else "working set exceeds L2"}
+        o = orc.Oracle(dims, U, kappa, CSW)
+        o.Dhat(pe)
+        t0 = time.perf_counter()
+        for _ in range(3):
+            o.Dhat(pe)
+        tc = (time.perf_counter() - t0) / 3
+        res["oracle_dhat"] = {"seconds": round(tc, 5), "gflops": round(FLOP_PER_SITE * ctx.Vh / tc / 1e9, 3)}
+        eta = torch.from_numpy(pe).cuda()
+        if dims == (8, 8, 8, 8):
+            ctx.solve_dhat(eta, solver=lqcd.SOLVER_CGNR, tol=1e-10, nmx=20000, check=False)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            _, info, st = ctx.solve_dhat(eta, solver=lqcd.SOLVER_CGNR, tol=1e-10, nmx=20000, check=False)
+            torch.cuda.synchronize()
+            res["cgnr_f64"] = {"seconds": round(time.perf_counter() - t0, 4), "iters": info[0]["iters"],
+                               "relres_dhat": info[0]["relres_dhat"], "status": st}
+            t0 = time.perf_counter()
+            _, st, it = o.cgnr(pe, tol=1e-10)
+            res["oracle_cgnr"] = {"seconds": round(time.perf_counter() - t0, 4), "iters": it, "status": st}
+        forms = [("sap_gcr_f64", lqcd.F64, lqcd.F64), ("sap_gcr_f32", lqcd.F32, lqcd.F32),
+                 ("sap_gcr_f16s", lqcd.F16S, lqcd.F32)]
+        for name, sp, inner in forms:
+            ctx.solve_dhat(eta, solver=lqcd.SOLVER_SAP_GCR, tol=1e-10, nmx=2, sap_prec=sp, inner=inner, check=False)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            _, info, st = ctx.solve_dhat(eta, solver=lqcd.SOLVER_SAP_GCR, tol=1e-10, sap_prec=sp, inner=inner,
+                                         check=False)
+            torch.cuda.synchronize()
+            res[name] = {"seconds": round(time.perf_counter() - t0, 4), "iters": info[0]["iters"],
+                         "relres_dhat": info[0]["relres_dhat"], "status": st}
+        full = synth.gaussian_spinor(ctx.V, 2)
+        t0 = time.perf_counter()
+        o.sap(full)
+        t_sap = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        o.D(full)
+        t_d = time.perf_counter() - t0
+        it = res["sap_gcr_f64"]["iters"]
+        res["oracle_sap_gcr_estimate"] = {"seconds": round(it * (t_sap + t_d), 2), "sap_s": round(t_sap, 4),
+                                          "d_s": round(t_d, 4),
+                                          "sample": f"1 SAP + 1 D application, times the GPU's {it} GCR steps"}
+        out[tag] = res
+    print(json.dumps(out))
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -372,8 +528,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
     ap.add_argument("--no-solve", action="store_true", help="skip the time-to-solution comparison")
+    ap.add_argument("--no-net", action="store_true", help="time-to-solution without the learned form")
     ap.add_argument("--lattice", default="48x24x24x24", help="TxL1xL2xL3 (profiling runs use smaller ones)")
-    ap.add_argument("--mode", default="dhat", choices=["dhat", "solve", "batch", "net"],
+    ap.add_argument("--mode", default="dhat", choices=["dhat", "solve", "batch", "net", "configs"],
                     help="solve: one time-to-solution run; batch: the uneven multi-lattice batch")
     ap.add_argument("--nlat", type=int, default=16, help="lattices of the batch mode")
     ap.add_argument("--nfields", type=int, default=10, help="net mode: training gauge fields")
@@ -398,6 +555,8 @@ def main():
         return run_batch(args)
     if args.mode == "net":
         return run_net(args)
+    if args.mode == "configs":
+        return run_configs(args)
 
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -483,7 +642,12 @@ def main():
 
     tts = None
     if not args.no_solve and rank == 0 and DIMS == (48, 24, 24, 24):
-        tts = time_to_solve(ctx, lqcd, eta_dev.to(torch.complex128))
+        net = None
+        if not args.no_net:
+            W, hist, train_s = train_net(lqcd, synth, KAPPA, args.nfields, args.npairs, args.train_steps)
+            net = {"W": W, "pairs": args.nfields * args.npairs, "train_s": round(train_s, 3),
+                   "loss_first": round(sum(hist[:5]) / 5, 4), "loss_last": round(sum(hist[-5:]) / 5, 4)}
+        tts = time_to_solve(ctx, lqcd, eta_dev.to(torch.complex128), net)
 
     if rank == 0:
         cb = None
@@ -506,7 +670,9 @@ def main():
             "roofline": {"kernel": "Dhat = k_hop<DHAT1> + k_hop<DHAT2>", "bound": "hbm",
                          "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
-                         "traffic": None, "algorithmic_bytes_per_launch": bytes_app},
+                         "traffic": traffic_of(args.prec, nrhs, Vh),
+                         "traffic_source": TRAFFIC_NOTE if traffic_of(args.prec, nrhs, Vh) else None,
+                         "algorithmic_bytes_per_launch": bytes_app},
             "gpu_launches": launches,
             "clocks": clk,
             "cpu_baseline": cb,
