@@ -145,14 +145,39 @@ std::vector<TuneChoice> hop_candidates(int nrhs)
     return v;
 }
 
-int hop_force_nr(bool has_mr, int nrhs)
+// LQCD_HOP_KIND = hop | mr | sm restricts the search to one kernel form
+// (test instrumentation; ignored where that form does not exist)
+int hop_force_kind(bool has_alt, int nrhs)
 {
-    const char *e = getenv("LQCD_HOP_NR");
-    if (!e || !*e) return 0;
-    const int n = atoi(e);
-    if (n == 1) return 1;
-    if (n == 2 && has_mr && n <= nrhs) return n;
-    return 0;
+    const char *e = getenv("LQCD_HOP_KIND");
+    if (!e || !*e) return -1;
+    const std::string k(e);
+    if (k == "hop") return KIND_HOP;
+    if (k == "mr" && has_alt && nrhs >= 2) return KIND_MR;
+    if (k == "sm" && has_alt) return KIND_SM;
+    return -1;
+}
+
+// staged shapes: tx sites (16 or 32) x ty fields per CTA
+std::vector<TuneChoice> hop_sm_candidates(int nrhs)
+{
+    std::vector<TuneChoice> v;
+    std::vector<int> tys;
+    for (int t : {nrhs, (nrhs + 1) / 2, (nrhs + 2) / 3, 4, 2, 1})
+        if (t >= 1 && t <= nrhs && std::find(tys.begin(), tys.end(), t) == tys.end()) tys.push_back(t);
+    for (int var = 0; var < NVAR_SM; var++)
+        for (int ty : tys)
+            for (int tx : {16, 32}) {
+                const int n = tx * ty;
+                if (n > var_sm_max_threads(var) || n < 32) continue;
+                TuneChoice t;
+                t.kind = KIND_SM;
+                t.variant = var;
+                t.tx = tx;
+                t.ty = ty;
+                v.push_back(t);
+            }
+    return v;
 }
 
 // register-blocked shapes: nr fields per thread, tx sites x ty field groups
@@ -175,6 +200,7 @@ std::vector<TuneChoice> hop_mr_candidates(int nrhs)
                     t.tx = tx;
                     t.ty = ty;
                     t.nr = nr;
+                    t.kind = KIND_MR;
                     v.push_back(t);
                 }
     }
@@ -185,7 +211,8 @@ template <class R, class SP, class LK, class CL, int MODE>
 lqcd_status launch_choice(lqcd_ctx *c, const TuneChoice &t, const HopArgs<SP, LK, CL> &a)
 {
     if constexpr (std::is_same<R, float>::value && MODE != MODE_HOP) {
-        if (t.nr > 1) return launch_hop_mr<R, SP, LK, CL, MODE>(c, t.nr, t.variant, dim3(t.tx, t.ty), a);
+        if (t.kind == KIND_MR) return launch_hop_mr<R, SP, LK, CL, MODE>(c, t.nr, t.variant, dim3(t.tx, t.ty), a);
+        if (t.kind == KIND_SM) return launch_hop_sm<R, SP, LK, CL, MODE>(c, t.variant, dim3(t.tx, t.ty), a);
     }
     return launch_var<R, SP, LK, CL, MODE>(c, t.variant, dim3(t.tx, t.ty), a);
 }
@@ -207,36 +234,40 @@ lqcd_status launch_hop(lqcd_ctx *c, int p_out, const SP *in_other, long in_rs, c
     a.U = U;
     a.clov = clov;
     const int prec = sizeof(R) == 8 ? 0 : (std::is_same<SP, h16s>::value ? 2 : 1);
-    constexpr bool has_mr = std::is_same<R, float>::value && MODE != MODE_HOP;
-    // LQCD_HOP_NR = 1 or 2 restricts the search to that many fields per
-    // thread (test instrumentation; ignored where no such kernel exists)
-    const int force_nr = hop_force_nr(has_mr, nrhs);
-    std::string key = tune_key(c, force_nr ? (force_nr == 1 ? "k_hop2_nr1" : "k_hop2_nr2") : "k_hop2", MODE, prec, nrhs);
+    constexpr bool has_alt = std::is_same<R, float>::value && MODE != MODE_HOP;
+    const int force = hop_force_kind(has_alt, nrhs);
+    static const char *kname[3] = {"k_hop3_hop", "k_hop3_mr", "k_hop3_sm"};
+    std::string key = tune_key(c, force >= 0 ? kname[force] : "k_hop3", MODE, prec, nrhs);
     TuneChoice tc;
     if (!tune_lookup(key, &tc)) {
         tc = TuneChoice();
         tc.tx = nrhs == 1 ? 128 : 32;
         tc.ty = nrhs == 1 ? 1 : std::min(nrhs, 8);
-        if (force_nr > 1) {
-            tc.nr = force_nr;
+        if (force == KIND_MR) {
+            tc.kind = KIND_MR;
+            tc.nr = 2;
             tc.tx = 64;
             tc.ty = 1;
+        } else if (force == KIND_SM) {
+            tc.kind = KIND_SM;
+            tc.tx = 32;
+            tc.ty = std::min(nrhs, 8);
         }
         if (tune_enabled()) {
             float best = 1e30f;
             std::vector<TuneChoice> cands;
-            if (force_nr <= 1) cands = hop_candidates(nrhs);
-            if (has_mr) {
-                for (const TuneChoice &m : hop_mr_candidates(nrhs))
-                    if (!force_nr || m.nr == force_nr) cands.push_back(m);
-            }
+            if (force < 0 || force == KIND_HOP) cands = hop_candidates(nrhs);
+            if (has_alt && (force < 0 || force == KIND_MR))
+                for (const TuneChoice &m : hop_mr_candidates(nrhs)) cands.push_back(m);
+            if (has_alt && (force < 0 || force == KIND_SM))
+                for (const TuneChoice &m : hop_sm_candidates(nrhs)) cands.push_back(m);
             for (const TuneChoice &cand : cands) {
                 float us;
                 lqcd_status s = tune_time(c, [&]() { return launch_choice<R, SP, LK, CL, MODE>(c, cand, a); }, 3, &us);
                 if (s != LQCD_OK) return s;
                 if (tune_verbose())
-                    fprintf(stderr, "tune %s: nr=%d var=%d %dx%d %.1f us\n", key.c_str(), cand.nr, cand.variant,
-                            cand.tx, cand.ty, us);
+                    fprintf(stderr, "tune %s: kind=%d nr=%d var=%d %dx%d %.1f us\n", key.c_str(), cand.kind, cand.nr,
+                            cand.variant, cand.tx, cand.ty, us);
                 if (us < best) {
                     best = us;
                     tc = cand;

@@ -338,5 +338,13 @@ template <class R, class SP, class LK, class CL, int MODE>
 lqcd_status launch_hop_mr(lqcd_ctx *c, int nr, int var, dim3 b, const HopArgs<SP, LK, CL> &a);
 constexpr int NVAR_MR = 3;
 inline int var_mr_max_threads(int v) { return v == 1 ? 128 : 256; }
+// staged form (lqcd_dirac_sm.cu): tile of b.x = 16 or 32 sites x b.y fields,
+// occupancy variant var (0..2); float arithmetic, modes DHAT1 / DHAT2 / D
+template <class R, class SP, class LK, class CL, int MODE>
+lqcd_status launch_hop_sm(lqcd_ctx *c, int var, dim3 b, const HopArgs<SP, LK, CL> &a);
+constexpr int NVAR_SM = 3;
+inline int var_sm_max_threads(int v) { return v == 2 ? 256 : 384; }
+// kernel forms known to the autotuner
+enum { KIND_HOP = 0, KIND_MR = 1, KIND_SM = 2 };
 
 }  // namespace stencil

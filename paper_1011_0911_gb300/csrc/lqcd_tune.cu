@@ -30,7 +30,7 @@ std::string cache_path()
     return std::string(h ? h : "/tmp") + "/.cache/lqcd_tune.json";
 }
 
-// file format: {"key": [variant, tx, ty, us, nr], ...} one entry per line
+// file format: {"key": [variant, tx, ty, us, nr, kind], ...} one entry per line
 void load_locked()
 {
     if (g_loaded) return;
@@ -47,6 +47,7 @@ void load_locked()
         char comma;
         if (ss >> t.variant >> comma >> t.tx >> comma >> t.ty >> comma >> t.us) {
             if (!(ss >> comma >> t.nr)) t.nr = 1;
+            if (!(ss >> comma >> t.kind)) t.kind = 0;
             g_cache[key] = t;
         }
     }
@@ -68,7 +69,8 @@ void save_locked()
     size_t i = 0;
     for (auto &kv : g_cache) {
         f << "  \"" << kv.first << "\": [" << kv.second.variant << ", " << kv.second.tx << ", " << kv.second.ty
-          << ", " << kv.second.us << ", " << kv.second.nr << "]" << (++i < g_cache.size() ? "," : "") << "\n";
+          << ", " << kv.second.us << ", " << kv.second.nr << ", " << kv.second.kind << "]"
+          << (++i < g_cache.size() ? "," : "") << "\n";
     }
     f << "}\n";
     f.close();

@@ -13,6 +13,7 @@ struct TuneChoice {
     int tx = 128, ty = 1;
     float us = 0;      // measured time of the choice
     int nr = 1;        // fields per thread (register-blocked kernels)
+    int kind = 0;      // kernel form (family specific)
 };
 
 std::string tune_key(const lqcd_ctx *c, const char *kernel, int mode, int prec, int nrhs);

@@ -51,13 +51,14 @@ def test_Dhat(pair, prec):
 
 @pytest.mark.parametrize("prec", [lqcd.F64, lqcd.F32, lqcd.F16S], ids=["f64", "f32", "f16s"])
 @pytest.mark.parametrize("nrhs", [3, 12])
-@pytest.mark.parametrize("nr", ["1", "2"])
-def test_multi_rhs_matches_single(pair, prec, nrhs, nr, monkeypatch):
-    """The multi-RHS launch shapes (one field per thread, or 2 fields per
-    thread in registers, with a partial last group for 3 fields) compute each
-    field exactly as the single-field launch."""
+@pytest.mark.parametrize("kind", ["hop", "mr", "sm"])
+def test_multi_rhs_matches_single(pair, prec, nrhs, kind, monkeypatch):
+    """The multi-RHS kernel forms (one field per thread; two fields per thread
+    in registers, with a partial last group for 3 fields; the operator staged
+    in shared memory per tile of sites) compute each field exactly as the
+    single-field launch."""
     P = pair
-    monkeypatch.setenv("LQCD_HOP_NR", nr)
+    monkeypatch.setenv("LQCD_HOP_KIND", kind)
     pe = rounded(synth.gaussian_spinor(nrhs * P.Vh, 5).reshape(nrhs, P.Vh, 4, 3), prec)
     g = to_gpu(pe, prec)
     many = P.ctx.apply_Dhat(g, prec)
