@@ -61,6 +61,21 @@ def traffic_of(prec, nrhs, Vh):
     return None
 
 
+def max_over_ranks(ms: float, dist=None, device="cuda") -> float:
+    """The slowest rank's duration of the timed region (every rank returns it);
+    one process per GPU, replicas only: this is the only collective."""
+    import torch
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank_step: float, steps: int, world: int, max_ms: float) -> float:
+    """Units processed by all ranks per second of the slowest rank's timed region."""
+    return units_per_rank_step * steps * world / (max_ms * 1e-3)
+
+
 def load_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -605,13 +620,9 @@ def main():
     launches = ctx.kernel_launches - launches0
     clk = clocks.stop()
     per = [evs[i].elapsed_time(evs[i + 1]) for i in range(args.steps)]
-    total_ms = evs[0].elapsed_time(evs[-1])
-    t_tensor = torch.tensor([total_ms], device="cuda")
-    if dist:
-        dist.all_reduce(t_tensor, op=dist.ReduceOp.MAX)
-    total_ms = t_tensor.item()
+    total_ms = max_over_ranks(evs[0].elapsed_time(evs[-1]), dist)
     ms_step = total_ms / args.steps
-    value = flops_step * args.steps * world / (total_ms * 1e-3) / 1e9
+    value = whole_job_rate(flops_step, args.steps, world, total_ms) / 1e9
     avg_launch_ms = statistics.mean(per)
     bytes_app = dhat_bytes_per_site(args.prec, nrhs) * Vh
     peak, peak_kind = load_peaks()
@@ -636,8 +647,8 @@ def main():
             out_host.copy_(o, non_blocking=True)
         e1.record(stream)
         torch.cuda.synchronize()
-        e2e_ms = e0.elapsed_time(e1) / e2e_steps
-        e2e_val = round(flops_step * world / (e2e_ms * 1e-3) / 1e9, 2)
+        e2e_ms = max_over_ranks(e0.elapsed_time(e1), dist) / e2e_steps
+        e2e_val = round(whole_job_rate(flops_step, 1, world, e2e_ms) / 1e9, 2)
         e2e_ms = round(e2e_ms, 4)
 
     tts = None
