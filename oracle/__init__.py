@@ -43,6 +43,7 @@ def lib():
             "or_apply_clover": (None, [P, I, P, P]),
             "or_apply_D": (None, [P, P, P]),
             "or_apply_Dhat": (None, [P, P, P]),
+            "or_apply_W": (None, [P, C.c_double, P, P]),
             "or_apply_Dhat_dag": (None, [P, P, P]),
             "or_apply_gamma5": (None, [LG, P, P]),
             "or_dhat_site": (None, [P, P, LG, P]),
@@ -144,6 +145,13 @@ class Oracle:
 
     def Dhat(self, x):
         return self._apply(lib().or_apply_Dhat, x, self.Vh)
+
+    def W(self, x, dm):
+        """Hasenbusch operator W(dm) = Q_S + dm on an even field (Eq. 3)."""
+        x = _c(x).reshape(self.Vh, 4, 3)
+        out = np.empty_like(x)
+        lib().or_apply_W(self._o, float(dm), _p(x), _p(out))
+        return out
 
     def Dhat_dag(self, x):
         return self._apply(lib().or_apply_Dhat_dag, x, self.Vh)

@@ -77,6 +77,8 @@ void or_hop(const oracle *o, const double *in, double *out);
 void or_apply_clover(const oracle *o, int inverse, const double *in, double *out);
 void or_apply_D(const oracle *o, const double *in, double *out);
 void or_apply_Dhat(const oracle *o, const double *in_e, double *out_e);
+/* W(dm) = Q_S + dm, Q_S = 1 - A_ee^-1 H_eo A_oo^-1 H_oe (Eq. 2-3); even fields */
+void or_apply_W(const oracle *o, double dm, const double *in_e, double *out_e);
 void or_apply_Dhat_dag(const oracle *o, const double *in_e, double *out_e);
 void or_apply_gamma5(long n, const double *in, double *out);
 void or_dhat_site(const oracle *o, const double *in_e, long xe, double *out12);

@@ -493,6 +493,36 @@ void or_apply_Dhat(const oracle *o, const double *in_e_, double *out_e_)
     free(tmp);
 }
 
+/* Hasenbusch's mass-preconditioned operator (Eq. 3): W(dm) = Q_S + dm with
+ * Q_S = 1 - Q_ee^-1 Q_eo Q_oo^-1 Q_oe (Eq. 2), Q = gamma5 D.  gamma5 is diagonal
+ * on sites, so the gamma5 factors cancel pairwise and
+ * Q_S = 1 - A_ee^-1 H_eo A_oo^-1 H_oe, with H the hopping term of D. */
+void or_apply_W(const oracle *o, double dm, const double *in_e_, double *out_e_)
+{
+    const ocplx *in_e = (const ocplx *)in_e_;
+    ocplx *out_e = (ocplx *)out_e_;
+    size_t n = 12 * (size_t)o->V;
+    ocplx *full = calloc(n, sizeof(ocplx));
+    ocplx *tmp = calloc(n, sizeof(ocplx));
+    for (long r = 0; r < o->Vh; r++)
+        for (int i = 0; i < 12; i++) full[12 * o->site_of[0][r] + i] = in_e[12 * r + i];
+    or_hop(o, (double *)full, (double *)tmp); /* H_oe psi_e */
+    for (size_t i = 0; i < n; i++) full[i] = 0;
+    for (long r = 0; r < o->Vh; r++) {
+        long x = o->site_of[1][r];
+        mat12_vec(o->Ainv + 144 * x, tmp + 12 * x, full + 12 * x); /* A_oo^-1 H_oe psi_e */
+    }
+    or_hop(o, (double *)full, (double *)tmp); /* H_eo A_oo^-1 H_oe psi_e */
+    for (long r = 0; r < o->Vh; r++) {
+        long x = o->site_of[0][r];
+        ocplx v[12];
+        mat12_vec(o->Ainv + 144 * x, tmp + 12 * x, v); /* A_ee^-1 ... */
+        for (int i = 0; i < 12; i++) out_e[12 * r + i] = (1.0 + dm) * in_e[12 * r + i] - v[i];
+    }
+    free(full);
+    free(tmp);
+}
+
 /* Dhat^dag = gamma5 Dhat gamma5 (gamma5-hermiticity of D carries over to Dhat) */
 void or_apply_Dhat_dag(const oracle *o, const double *in_e, double *out_e)
 {
