@@ -308,6 +308,22 @@ LQCD_API lqcd_status lqcd_net_train(lqcd_ctx *ctx, const lqcd_net_train_params *
 LQCD_API lqcd_status lqcd_solve_D(lqcd_ctx *ctx, const lqcd_solver_params *p, const double *eta_dev,
                          double *psi_dev, int nrhs, lqcd_solve_info *info);
 
+/* ------------------------------------------- Hasenbusch mass preconditioning */
+/* W(dm) = Q_S + dm (Eq. 3) with Q_S = 1 - Q_ee^-1 Q_eo Q_oo^-1 Q_oe (Eq. 2),
+ * Q = gamma5 D; the gamma5 factors cancel, so W(dm) = A_ee^-1 Dhat + dm.
+ * out = W(dm) in: nrhs canonical even fields of precision prec (F64 or F32). */
+LQCD_API lqcd_status lqcd_apply_W(lqcd_ctx *ctx, lqcd_prec prec, double dm, const void *in_dev, void *out_dev,
+                                  int nrhs);
+/* Solve W(dm) psi = eta (the pseudofermion solve of Eq. 4) for nrhs canonical
+ * FP64 even fields, as Dhat' psi = A_ee eta where Dhat' is the Schur
+ * complement of D with its even-site clover blocks scaled by 1 + dm (built
+ * for the solve, then the clover term of D is rebuilt).  p->solver: CGNR or
+ * SAP-GCR (a deflation subspace or network belongs to D, not to D').
+ * info[k].relres_dhat holds the FP64 residual |eta - W psi| / |eta|.
+ * dm > -1. */
+LQCD_API lqcd_status lqcd_solve_W(lqcd_ctx *ctx, const lqcd_solver_params *p, double dm, const double *eta_dev,
+                                  double *psi_dev, int nrhs, lqcd_solve_info *info);
+
 /* ------------------------------------------------ batched multi-lattice solve */
 /* Several independent lattices (each its own context: gauge field, kappa,
  * clover term) solved together with the SAP-preconditioned flexible GCR of

@@ -185,6 +185,7 @@ struct CloverArgs {
     uint2 *A16[2], *Ai16[2];
     double *logdet;   // [2][Vh]
     int *singular;    // count of singular blocks
+    double even_scale;   // A on even sites multiplied by this (1 for D itself)
 };
 
 __global__ void __launch_bounds__(128) k_clover(CloverArgs a)
@@ -214,6 +215,9 @@ __global__ void __launch_bounds__(128) k_clover(CloverArgs a)
                 A[3 + i][3 + j] = -(f * z);
             }
         for (int i = 0; i < 6; i++) A[i][i].re += 4.0 + a.m0;
+        if (p == 0 && a.even_scale != 1.0)
+            for (int i = 0; i < 6; i++)
+                for (int j = 0; j < 6; j++) A[i][j] = a.even_scale * A[i][j];
         store_herm(A, blk, r, a.g.Vh, a.A64[p], a.A32[p], a.A16[p]);
         double ld = 0;
         if (lu_inv6(A, Ai, &ld)) {
@@ -280,7 +284,7 @@ __global__ void k_clover_apply64(Geom g, const double2 *A, const double2 *in, do
 
 }  // namespace
 
-lqcd_status clover_build(lqcd_ctx *c, double kappa, double csw, double *ld_e, double *ld_o)
+lqcd_status clover_build(lqcd_ctx *c, double kappa, double csw, double *ld_e, double *ld_o, double even_scale)
 {
     if (!c->have_gauge) return set_err(c, LQCD_ERR_STATE, "gauge field not set");
     if (!(kappa > 0)) return set_err(c, LQCD_ERR_ARG, "kappa must be > 0");
@@ -316,6 +320,7 @@ lqcd_status clover_build(lqcd_ctx *c, double kappa, double csw, double *ld_e, do
     }
     a.logdet = logdet;
     a.singular = sing;
+    a.even_scale = even_scale;
     k_clover<<<dim3(div_up(Vh, 128), 2), 128, 0, c->stream>>>(a);
     c->n_kernel_launches++;
     LQCD_LAUNCH_CHECK(c);

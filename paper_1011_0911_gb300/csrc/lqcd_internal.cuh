@@ -151,6 +151,7 @@ enum {
     WS_NET_TGT,
     WS_NET_BATCH_T,
     WS_NET_FALLBACK,
+    WS_HASEN,
 };
 lqcd_status ws_get(lqcd_ctx *c, int slot, size_t bytes, void **out);
 
@@ -172,7 +173,9 @@ lqcd_status convert_native(lqcd_ctx *c, lqcd_prec from, lqcd_prec to, const void
                            long nhalf);
 lqcd_status pack_field(lqcd_ctx *c, lqcd_prec p, int nsub, const void *canon, void *native,
                        int nrhs, bool unpack);
-lqcd_status clover_build(lqcd_ctx *c, double kappa, double csw, double *ld_e, double *ld_o);
+// even_scale != 1: the even-site blocks of A (and so of A^-1) belong to
+// even_scale * A_ee (the shifted operator of the Hasenbusch solve)
+lqcd_status clover_build(lqcd_ctx *c, double kappa, double csw, double *ld_e, double *ld_o, double even_scale = 1.0);
 lqcd_status clover_apply_native64(lqcd_ctx *c, int parity, int inverse, const double2 *in,
                                   double2 *out);
 

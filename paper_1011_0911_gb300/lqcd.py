@@ -119,6 +119,8 @@ def lib():
             "lqcd_net_train": [P, C.POINTER(NetTrainParams), P, I, P],
             "lqcd_solve_dhat": [P, C.POINTER(SolverParams), P, P, I, C.POINTER(SolveInfo)],
             "lqcd_solve_D": [P, C.POINTER(SolverParams), P, P, I, C.POINTER(SolveInfo)],
+            "lqcd_apply_W": [P, I, D, P, P, I],
+            "lqcd_solve_W": [P, C.POINTER(SolverParams), D, P, P, I, C.POINTER(SolveInfo)],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -397,6 +399,26 @@ class Context:
                    sap_prec=F64, inner=F64, check=True):
         return self._solve(lib().lqcd_solve_dhat, eta, self.Vh, solver, tol, nkv, nmx, bs, ncy, nmr, sap_prec,
                            inner, check)
+
+    def apply_W(self, x: torch.Tensor, dm: float, prec=F64) -> torch.Tensor:
+        """Hasenbusch operator W(dm) = Q_S + dm on even fields (Eq. 3)."""
+        x = x.to(_dtype(prec)).contiguous()
+        out = torch.empty_like(x)
+        self._check(lib().lqcd_apply_W(self._h, prec, float(dm), _ptr(x), _ptr(out), self._nrhs(x, self.Vh)),
+                    "apply_W")
+        return out
+
+    def solve_W(self, eta, dm, solver=SOLVER_SAP_GCR, tol=1e-10, nkv=16, nmx=4096, bs=(4, 4, 4, 4), ncy=4, nmr=5,
+                sap_prec=F64, inner=F64, check=True):
+        eta = eta.to(torch.complex128).contiguous()
+        nrhs = self._nrhs(eta, self.Vh)
+        psi = torch.empty_like(eta)
+        p = SolverParams(solver, nkv, nmx, tol, sap_params(bs, ncy, nmr, sap_prec), inner)
+        info = (SolveInfo * nrhs)()
+        st = lib().lqcd_solve_W(self._h, C.byref(p), float(dm), _ptr(eta), _ptr(psi), nrhs, info)
+        if check:
+            self._check(st, "solve_W")
+        return psi, [i.as_dict() for i in info], st
 
     def solve_D(self, eta, solver=SOLVER_SAP_GCR, tol=1e-10, nkv=16, nmx=4096, bs=(4, 4, 4, 4), ncy=4, nmr=5,
                 sap_prec=F64, inner=F64, check=True):
