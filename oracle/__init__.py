@@ -275,6 +275,18 @@ class Oracle:
         return out
 
 
+def chrono_guess(o: Oracle, xs, eta):
+    """Chronological initial guess (Sec. 2, the method of Brower et al.):
+    x0 = sum_i c_i x_i over the stored solutions x_i with c minimising
+    |eta - Dhat x0|, solved here by a least-squares routine on the dense
+    columns Dhat x_i.  Returns (x0, c)."""
+    xs = [np.asarray(x, dtype=np.complex128).reshape(o.Vh, 4, 3) for x in xs]
+    Y = np.stack([o.Dhat(x).ravel() for x in xs], axis=1)
+    c = np.linalg.lstsq(Y, np.asarray(eta, dtype=np.complex128).ravel(), rcond=None)[0]
+    x0 = sum(ci * x for ci, x in zip(c, xs))
+    return x0, c
+
+
 def ptc_weight_count(chans) -> int:
     """complex weights of a network with channel counts chans[0..nl]"""
     return sum(chans[l] * chans[l + 1] * 9 * 16 for l in range(len(chans) - 1))
