@@ -503,6 +503,16 @@ def run_configs(args):
             torch.cuda.synchronize()
             res[name] = {"seconds": round(time.perf_counter() - t0, 4), "iters": info[0]["iters"],
                          "relres_dhat": info[0]["relres_dhat"], "status": st}
+        if dims == (32, 16, 16, 16):
+            # Hasenbusch solve W(0.09) psi = eta (Eq. 3-4) beside the Dhat solve
+            for name, sp, inner in (("hasenbusch_W_f64", lqcd.F64, lqcd.F64), ("hasenbusch_W_f32", lqcd.F32, lqcd.F32)):
+                ctx.solve_W(eta, 0.09, tol=1e-10, nmx=2, sap_prec=sp, inner=inner, check=False)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                _, info, st = ctx.solve_W(eta, 0.09, tol=1e-10, sap_prec=sp, inner=inner, check=False)
+                torch.cuda.synchronize()
+                res[name] = {"dm": 0.09, "seconds": round(time.perf_counter() - t0, 4), "iters": info[0]["iters"],
+                             "relres_W": info[0]["relres_dhat"], "status": st}
         full = synth.gaussian_spinor(ctx.V, 2)
         t0 = time.perf_counter()
         o.sap(full)

@@ -308,6 +308,23 @@ LQCD_API lqcd_status lqcd_net_train(lqcd_ctx *ctx, const lqcd_net_train_params *
 LQCD_API lqcd_status lqcd_solve_D(lqcd_ctx *ctx, const lqcd_solver_params *p, const double *eta_dev,
                          double *psi_dev, int nrhs, lqcd_solve_info *info);
 
+/* As lqcd_solve_dhat (GCR solvers), starting from the guess that psi_dev
+ * holds on entry instead of from zero. */
+LQCD_API lqcd_status lqcd_solve_dhat_guess(lqcd_ctx *ctx, const lqcd_solver_params *p, const double *eta_dev,
+                                           double *psi_dev, int nrhs, lqcd_solve_info *info);
+
+/* ---------------------------------------------- chronological initial guess */
+/* Sec. 2: each inversion starts from a prediction built from earlier
+ * solutions (the chronological method of Brower et al.).  The context keeps
+ * the last nkeep (0..16; 0 drops the store) solutions added; the guess for a
+ * source eta is x0 = sum_i c_i x_i with c minimising |eta - Dhat x0|
+ * (normal equations in FP64, nearly dependent solutions dropped).  Fields are
+ * canonical FP64 even fields (device).  nused (may be NULL) receives the
+ * number of stored solutions the guess uses; with none stored x0 = 0. */
+LQCD_API lqcd_status lqcd_chrono_reset(lqcd_ctx *ctx, int nkeep);
+LQCD_API lqcd_status lqcd_chrono_add(lqcd_ctx *ctx, const double *psi_dev);
+LQCD_API lqcd_status lqcd_chrono_guess(lqcd_ctx *ctx, const double *eta_dev, double *x0_dev, int *nused);
+
 /* ------------------------------------------- Hasenbusch mass preconditioning */
 /* W(dm) = Q_S + dm (Eq. 3) with Q_S = 1 - Q_ee^-1 Q_eo Q_oo^-1 Q_oe (Eq. 2),
  * Q = gamma5 D; the gamma5 factors cancel, so W(dm) = A_ee^-1 Dhat + dm.

@@ -313,6 +313,7 @@ lqcd_status lqcd_destroy(lqcd_ctx *c)
     if (!c) return LQCD_OK;
     dfl_free(c);
     net_free(c);
+    chrono_free(c);
     sap_free_plans(c);
     cudaFree(c->U64);
     cudaFree(c->U32);

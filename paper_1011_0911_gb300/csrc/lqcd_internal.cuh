@@ -87,6 +87,7 @@ struct Workspace {
 
 struct DflState;   // deflation subspace (lqcd_dfl.cu)
 struct NetState;   // learned preconditioner (lqcd_ptc.cu)
+struct ChronoState;   // stored solutions for initial guesses (lqcd_chrono.cu)
 
 struct lqcd_ctx {
     lqcd_geom geom;
@@ -112,6 +113,7 @@ struct lqcd_ctx {
     Workspace ws[24];
     DflState *dfl = nullptr;
     NetState *net = nullptr;
+    ChronoState *chrono = nullptr;
     long n_kernel_launches = 0;
 };
 
@@ -219,6 +221,7 @@ lqcd_status sap_batch_create(lqcd_ctx *hc, lqcd_ctx *const *ctx, int n, const lq
                              void *psi, void *delta, const long *off, SapBatch **out_b);
 lqcd_status sap_batch_apply(lqcd_ctx *hc, SapBatch *b, const void *eta, size_t bytes, const int *active_dev);
 void sap_batch_free(SapBatch *b);
+void chrono_free(lqcd_ctx *c);
 // learned preconditioner
 void net_free(lqcd_ctx *c);
 lqcd_status net_apply_native(lqcd_ctx *c, const double2 *rho, double2 *phi, int nrhs);

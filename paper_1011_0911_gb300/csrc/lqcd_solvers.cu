@@ -435,15 +435,15 @@ lqcd_status check_params(lqcd_ctx *c, const lqcd_solver_params *p, int nrhs)
 
 lqcd_status worst(lqcd_status a, lqcd_status b) { return a != LQCD_OK ? a : b; }
 
-}  // namespace
-
-extern "C" {
-
-lqcd_status lqcd_solve_dhat(lqcd_ctx *c, const lqcd_solver_params *p, const double *eta, double *psi, int nrhs,
-                            lqcd_solve_info *info)
+// guess: psi holds the initial even-site guess x0 on entry (GCR solvers); the
+// odd part of the full-lattice start is -A_oo^-1 H_oe x0, so that the full
+// residual starts as (eta_e - Dhat x0, 0)
+lqcd_status solve_dhat_impl(lqcd_ctx *c, const lqcd_solver_params *p, const double *eta, double *psi, int nrhs,
+                            lqcd_solve_info *info, bool guess)
 {
     if (!c || !eta || !psi) return set_err(c, LQCD_ERR_ARG, "null argument");
     LQCD_TRY(check_params(c, p, nrhs));
+    if (guess && p->solver == LQCD_SOLVER_CGNR) return set_err(c, LQCD_ERR_ARG, "initial guesses are for the GCR solvers");
     const long Vh = c->g.Vh;
     const long nf = 24 * Vh;
     const size_t hb = native_half_bytes(c, LQCD_F64);
@@ -470,6 +470,17 @@ lqcd_status lqcd_solve_dhat(lqcd_ctx *c, const lqcd_solver_params *p, const doub
         LQCD_TRY(blas_zero(c, 4 * hb * nrhs, io));
         for (int k = 0; k < nrhs; k++)
             LQCD_TRY(pack_field(c, LQCD_F64, 1, eta + (size_t)k * 24 * Vh, eta_f + k * nf, 1, false));
+        if (guess) {
+            const long hh = 12 * Vh;   // double2 in one half field
+            for (int k = 0; k < nrhs; k++)
+                LQCD_TRY(pack_field(c, LQCD_F64, 1, psi + (size_t)k * 24 * Vh, psi_f + k * nf, 1, false));
+            LQCD_TRY(dirac_hop_parity(c, LQCD_F64, 1, psi_f, psi_f + hh, nf, nf, nrhs));
+            for (int k = 0; k < nrhs; k++) {
+                double2 *po = psi_f + k * nf + hh;
+                LQCD_TRY(clover_apply_native64(c, 1, 1, po, po));
+                LQCD_TRY(blas_scal(c, 2 * hh, -1.0, 0.0, (double *)po));
+            }
+        }
         GcrState S(nrhs);
         std::vector<double> tol(nrhs, p->tol), rh(nrhs, 0);
         for (int attempt = 0; attempt < 4; attempt++) {
@@ -504,6 +515,22 @@ lqcd_status lqcd_solve_dhat(lqcd_ctx *c, const lqcd_solver_params *p, const doub
     }
     if (all != LQCD_OK && all != LQCD_ERR_CUDA) set_err(c, all, "solve did not converge (status %d)", (int)all);
     return all;
+}
+
+}  // namespace
+
+extern "C" {
+
+lqcd_status lqcd_solve_dhat(lqcd_ctx *c, const lqcd_solver_params *p, const double *eta, double *psi, int nrhs,
+                            lqcd_solve_info *info)
+{
+    return solve_dhat_impl(c, p, eta, psi, nrhs, info, false);
+}
+
+lqcd_status lqcd_solve_dhat_guess(lqcd_ctx *c, const lqcd_solver_params *p, const double *eta, double *psi,
+                                  int nrhs, lqcd_solve_info *info)
+{
+    return solve_dhat_impl(c, p, eta, psi, nrhs, info, true);
 }
 
 lqcd_status lqcd_solve_D(lqcd_ctx *c, const lqcd_solver_params *p, const double *eta, double *psi, int nrhs,

@@ -120,6 +120,10 @@ def lib():
             "lqcd_solve_dhat": [P, C.POINTER(SolverParams), P, P, I, C.POINTER(SolveInfo)],
             "lqcd_solve_D": [P, C.POINTER(SolverParams), P, P, I, C.POINTER(SolveInfo)],
             "lqcd_apply_W": [P, I, D, P, P, I],
+            "lqcd_solve_dhat_guess": [P, C.POINTER(SolverParams), P, P, I, C.POINTER(SolveInfo)],
+            "lqcd_chrono_reset": [P, I],
+            "lqcd_chrono_add": [P, P],
+            "lqcd_chrono_guess": [P, P, P, C.POINTER(I)],
             "lqcd_solve_W": [P, C.POINTER(SolverParams), D, P, P, I, C.POINTER(SolveInfo)],
         }
         for name, args in sig.items():
@@ -399,6 +403,33 @@ class Context:
                    sap_prec=F64, inner=F64, check=True):
         return self._solve(lib().lqcd_solve_dhat, eta, self.Vh, solver, tol, nkv, nmx, bs, ncy, nmr, sap_prec,
                            inner, check)
+
+    def solve_dhat_guess(self, eta, x0, solver=SOLVER_SAP_GCR, tol=1e-10, nkv=16, nmx=4096, bs=(4, 4, 4, 4),
+                         ncy=4, nmr=5, sap_prec=F64, inner=F64, check=True):
+        """As solve_dhat, starting from the guess x0 (even fields)."""
+        eta = eta.to(torch.complex128).contiguous()
+        nrhs = self._nrhs(eta, self.Vh)
+        psi = x0.to(torch.complex128).contiguous().clone()
+        p = SolverParams(solver, nkv, nmx, tol, sap_params(bs, ncy, nmr, sap_prec), inner)
+        info = (SolveInfo * nrhs)()
+        st = lib().lqcd_solve_dhat_guess(self._h, C.byref(p), _ptr(eta), _ptr(psi), nrhs, info)
+        if check:
+            self._check(st, "solve_dhat_guess")
+        return psi, [i.as_dict() for i in info], st
+
+    def chrono_reset(self, nkeep: int):
+        self._check(lib().lqcd_chrono_reset(self._h, nkeep), "chrono_reset")
+
+    def chrono_add(self, psi: torch.Tensor):
+        psi = psi.to(torch.complex128).contiguous()
+        self._check(lib().lqcd_chrono_add(self._h, _ptr(psi)), "chrono_add")
+
+    def chrono_guess(self, eta: torch.Tensor):
+        eta = eta.to(torch.complex128).contiguous()
+        x0 = torch.empty_like(eta)
+        n = C.c_int()
+        self._check(lib().lqcd_chrono_guess(self._h, _ptr(eta), _ptr(x0), C.byref(n)), "chrono_guess")
+        return x0, n.value
 
     def apply_W(self, x: torch.Tensor, dm: float, prec=F64) -> torch.Tensor:
         """Hasenbusch operator W(dm) = Q_S + dm on even fields (Eq. 3)."""
