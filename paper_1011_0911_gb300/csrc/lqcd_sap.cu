@@ -523,9 +523,30 @@ __global__ void __launch_bounds__(128) k_sap_block(SapArgs<P> a)
 // as k_sap_block, different summation order.
 constexpr int SAPS_NH = 128;   // sites of one parity per block (4^4 blocks)
 
-struct SapSmem {
+// SA: the clover term of the block is staged in shared memory (184 KB, one
+// CTA per SM); without it (110 KB) two CTAs fit on an SM and every clover
+// application reads its 6x6 block through L1/L2 instead (same values).
+// staging loads of the resident kernel: one 4-real word of a link row pair or
+// of the clover term, and one site of a residual field
+__device__ __forceinline__ float4 stage4(const float4 *p) { return __ldg(p); }
+__device__ __forceinline__ float4 stage4(const uint2 *p)
+{
+    uint2 t = __ldg(p);
+    cx<float> a = f16s_h2c(t.x, 1.f), b = f16s_h2c(t.y, 1.f);
+    return make_float4(a.re, a.im, b.re, b.im);
+}
+template <bool SA>
+struct SapSmemT;
+template <>
+struct SapSmemT<true> {
     float4 U[4][3][2 * SAPS_NH];   // forward links, two rows, local lexicographic site
     float4 A[18][2 * SAPS_NH];     // A (even sites) or A^-1 (odd sites), local lexicographic site
+    float4 rho[6][SAPS_NH], chi[6][SAPS_NH], p[6][SAPS_NH], to[6][SAPS_NH], ro[6][SAPS_NH];
+    float red[3][8];
+};
+template <>
+struct SapSmemT<false> {
+    float4 U[4][3][2 * SAPS_NH];
     float4 rho[6][SAPS_NH], chi[6][SAPS_NH], p[6][SAPS_NH], to[6][SAPS_NH], ro[6][SAPS_NH];
     float red[3][8];
 };
@@ -557,7 +578,8 @@ __device__ __forceinline__ void s_spinor(const float4 (*f)[SAPS_NH], int t, cx<f
         v[2 * q + 1] = mk(a.z, a.w);
     }
 }
-__device__ __forceinline__ void s_link(const SapSmem &S, int mu, int ls, cx<float> u[3][3])
+template <class SM>
+__device__ __forceinline__ void s_link(const SM &S, int mu, int ls, cx<float> u[3][3])
 {
 #pragma unroll
     for (int q = 0; q < 3; q++) {
@@ -569,13 +591,20 @@ __device__ __forceinline__ void s_link(const SapSmem &S, int mu, int ls, cx<floa
     u[2][1] = conjx(u[0][2] * u[1][0] - u[0][0] * u[1][2]);
     u[2][2] = conjx(u[0][0] * u[1][1] - u[0][1] * u[1][0]);
 }
-// one chirality block h of the clover matrix at local site ls applied to v[6]
-__device__ __forceinline__ void s_clover_half(const SapSmem &S, int ls, int h, const cx<float> v[6], cx<float> w[6])
+// one chirality block h of the clover matrix applied to v[6]; the block is
+// read from shared memory (local site ls) or from global memory (rank grank)
+template <bool SA, class CL>
+__device__ __forceinline__ void s_clover_half(const SapSmemT<SA> &S, int ls, const CL *A, long Vh, long grank, int h,
+                                              const cx<float> v[6], cx<float> w[6])
 {
     float a[36];
 #pragma unroll
     for (int q = 0; q < 9; q++) {
-        float4 t = S.A[9 * h + q][ls];
+        float4 t;
+        if constexpr (SA)
+            t = S.A[9 * h + q][ls];
+        else
+            t = stage4(A + (9 * h + q) * Vh + grank);
         a[4 * q] = t.x;
         a[4 * q + 1] = t.y;
         a[4 * q + 2] = t.z;
@@ -598,7 +627,8 @@ __device__ __forceinline__ void s_clover_half(const SapSmem &S, int ls, int h, c
 // half of the in-block hop sum at site (l, x, ls) from the smem field src of the
 // other parity: h = 0 forward hops, h = 1 backward hops; then the pair's halves
 // are added so both threads hold the full sum S (before the -1/2).
-__device__ __forceinline__ void s_hopsum(const Geom &g, const BlkGeom &B, const SapSmem &S, int h, const int l[4],
+template <class SM>
+__device__ __forceinline__ void s_hopsum(const Geom &g, const BlkGeom &B, const SM &S, int h, const int l[4],
                                          const int x[4], int ls, const float4 (*src)[SAPS_NH], cx<float> acc[12])
 {
 #pragma unroll
@@ -638,15 +668,6 @@ __device__ __forceinline__ void s_half(const cx<float> acc[12], int h, cx<float>
     for (int i = 0; i < 6; i++) out[i] = h ? acc[6 + i] : acc[i];
 }
 
-// staging loads of the resident kernel: one 4-real word of a link row pair or
-// of the clover term, and one site of a residual field
-__device__ __forceinline__ float4 stage4(const float4 *p) { return __ldg(p); }
-__device__ __forceinline__ float4 stage4(const uint2 *p)
-{
-    uint2 t = __ldg(p);
-    cx<float> a = f16s_h2c(t.x, 1.f), b = f16s_h2c(t.y, 1.f);
-    return make_float4(a.re, a.im, b.re, b.im);
-}
 __device__ __forceinline__ void stage_site(const float4 *f, long Vh, long r, float4 o[6])
 {
 #pragma unroll
@@ -718,12 +739,12 @@ __device__ __forceinline__ void half_add(SP *f, long Vh, long r, int h, const cx
 }
 
 // block list entry bi of a.blocks, right-hand side rhs; blockDim.x = 2 nh
-template <int P>
+template <int P, bool SA>
 __device__ __forceinline__ void sap_block_s_body(const SapArgs<P> &a, int bi, int rhs)
 {
     using SP = typename SapT<P>::SP;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    SapSmem &S = *reinterpret_cast<SapSmem *>(smem_raw);
+    SapSmemT<SA> &S = *reinterpret_cast<SapSmemT<SA> *>(smem_raw);
     const BlkGeom &B = a.B;
     const int nh = B.nh;
     const long Vh = a.g.Vh;
@@ -757,9 +778,11 @@ __device__ __forceinline__ void sap_block_s_body(const SapArgs<P> &a, int bi, in
         for (int mu = 0; mu < 4; mu++)
 #pragma unroll
             for (int q = 0; q < 3; q++) S.U[mu][q][ls] = stage4(a.U + ((long)(par * 4 + mu) * 3 + q) * Vh + s.grank);
-        const typename SapT<P>::CL *A = par ? a.Aio : a.Ae;
+        if constexpr (SA) {
+            const typename SapT<P>::CL *A = par ? a.Aio : a.Ae;
 #pragma unroll
-        for (int q = 0; q < 18; q++) S.A[q][ls] = stage4(A + q * Vh + s.grank);
+            for (int q = 0; q < 18; q++) S.A[q][ls] = stage4(A + q * Vh + s.grank);
+        }
         float4 site[6];
         stage_site(par ? r_o : r_e, Vh, s.grank, site);
         if (par) {
@@ -793,7 +816,7 @@ __device__ __forceinline__ void sap_block_s_body(const SapArgs<P> &a, int bi, in
             v[2 * q] = mk(x.x, x.y);
             v[2 * q + 1] = mk(x.z, x.w);
         }
-        s_clover_half(S, lso, h, v, w);
+        s_clover_half<SA>(S, lso, a.Aio, Vh, so.grank, h, v, w);
 #pragma unroll
         for (int q = 0; q < 3; q++) S.to[3 * h + q][t] = make_float4(w[2 * q].re, w[2 * q].im, w[2 * q + 1].re, w[2 * q + 1].im);
     }
@@ -818,7 +841,7 @@ __device__ __forceinline__ void sap_block_s_body(const SapArgs<P> &a, int bi, in
             s_half(acc, h, v);
 #pragma unroll
             for (int i = 0; i < 6; i++) v[i] = -0.5f * v[i];
-            s_clover_half(S, lso, h, v, w);
+            s_clover_half<SA>(S, lso, a.Aio, Vh, so.grank, h, v, w);
 #pragma unroll
             for (int q = 0; q < 3; q++) S.to[3 * h + q][t] = make_float4(w[2 * q].re, w[2 * q].im, w[2 * q + 1].re, w[2 * q + 1].im);
         }
@@ -834,7 +857,7 @@ __device__ __forceinline__ void sap_block_s_body(const SapArgs<P> &a, int bi, in
                 x[2 * q] = mk(y.x, y.y);
                 x[2 * q + 1] = mk(y.z, y.w);
             }
-            s_clover_half(S, lse, h, x, w);
+            s_clover_half<SA>(S, lse, a.Ae, Vh, se.grank, h, x, w);
             cx<float> ah[6];
             s_half(acc, h, ah);
 #pragma unroll
@@ -897,7 +920,7 @@ __device__ __forceinline__ void sap_block_s_body(const SapArgs<P> &a, int bi, in
             v[2 * q] = mk(x.x + 0.5f * ah[2 * q].re, x.y + 0.5f * ah[2 * q].im);
             v[2 * q + 1] = mk(x.z + 0.5f * ah[2 * q + 1].re, x.w + 0.5f * ah[2 * q + 1].im);
         }
-        s_clover_half(S, lso, h, v, w);
+        s_clover_half<SA>(S, lso, a.Aio, Vh, so.grank, h, v, w);
         cx<float> ce[6], re[6], zero[6];
 #pragma unroll
         for (int q = 0; q < 3; q++) {
@@ -917,10 +940,17 @@ __device__ __forceinline__ void sap_block_s_body(const SapArgs<P> &a, int bi, in
     }
 }
 
-template <int P>
-__global__ void __launch_bounds__(2 * SAPS_NH, 1) k_sap_block_s(SapArgs<P> a)
+template <int P, bool SA>
+__global__ void __launch_bounds__(2 * SAPS_NH, SA ? 1 : 2) k_sap_block_s(SapArgs<P> a)
 {
-    sap_block_s_body<P>(a, blockIdx.x, blockIdx.y);
+    sap_block_s_body<P, SA>(a, blockIdx.x, blockIdx.y);
+}
+
+// LQCD_SAP_STAGE_A=1 stages the clover term in shared memory (one CTA per SM)
+bool sap_stage_clover()
+{
+    const char *e = getenv("LQCD_SAP_STAGE_A");
+    return e && e[0] == '1';
 }
 
 // r(x) -= sum of the hops into x from neighbours y that lie in another block
@@ -988,8 +1018,8 @@ __global__ void __launch_bounds__(128) k_sap_face(SapArgs<P> a, int col)
 // lattice l for the blocks of colour col.  Persistent CTAs take work items from
 // a device counter (*queue, zero before the launch) until the list is empty;
 // items of lattices whose active flag is 0 are skipped.
-template <int P>
-__global__ void __launch_bounds__(2 * SAPS_NH, 1)
+template <int P, bool SA>
+__global__ void __launch_bounds__(2 * SAPS_NH, SA ? 1 : 2)
     k_sap_block_s_batch(const SapArgs<P> *args, int col, const int2 *items, int nitems, const int *active, int *queue)
 {
     __shared__ int s_item;
@@ -1003,7 +1033,7 @@ __global__ void __launch_bounds__(2 * SAPS_NH, 1)
         const bool on = !active || active[w.x];
         if (on && threadIdx.x == 0) sa = args[2 * w.x + col];
         __syncthreads();
-        if (on) sap_block_s_body<P>(sa, w.y, 0);
+        if (on) sap_block_s_body<P, SA>(sa, w.y, 0);
         __syncthreads();
     }
 }
@@ -1130,7 +1160,10 @@ lqcd_status sap_run(lqcd_ctx *c, const SapPlan &P_, int ncy, int nmr, const void
     if constexpr (P != LQCD_F64) {
         static bool attr_s = false;
         if (!attr_s) {
-            cudaFuncSetAttribute(k_sap_block_s<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(SapSmem));
+            cudaFuncSetAttribute(k_sap_block_s<P, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)sizeof(SapSmemT<true>));
+            cudaFuncSetAttribute(k_sap_block_s<P, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)sizeof(SapSmemT<false>));
             attr_s = true;
         }
         resident = Pl.B.nh <= SAPS_NH && (2 * Pl.B.nh) % 32 == 0 && !sap_force_generic();
@@ -1142,8 +1175,12 @@ lqcd_status sap_run(lqcd_ctx *c, const SapPlan &P_, int ncy, int nmr, const void
             if (Pl.count[col] == 0) continue;
             a.blocks = Pl.blocks_dev + (col == 0 ? 0 : Pl.count[0]);
             if constexpr (P != LQCD_F64) {
-                if (resident)
-                    k_sap_block_s<P><<<dim3(Pl.count[col], nrhs), 2 * Pl.B.nh, sizeof(SapSmem), c->stream>>>(a);
+                if (resident && sap_stage_clover())
+                    k_sap_block_s<P, true>
+                        <<<dim3(Pl.count[col], nrhs), 2 * Pl.B.nh, sizeof(SapSmemT<true>), c->stream>>>(a);
+                else if (resident)
+                    k_sap_block_s<P, false>
+                        <<<dim3(Pl.count[col], nrhs), 2 * Pl.B.nh, sizeof(SapSmemT<false>), c->stream>>>(a);
                 else
                     k_sap_block<P><<<dim3(Pl.count[col], nrhs), threads, smem, c->stream>>>(a);
             } else {
@@ -1292,17 +1329,26 @@ lqcd_status sap_batch_run(lqcd_ctx *hc, SapBatch *b, const int *active)
 {
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(k_sap_block_s_batch<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(SapSmem));
+        cudaFuncSetAttribute(k_sap_block_s_batch<P, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sizeof(SapSmemT<true>));
+        cudaFuncSetAttribute(k_sap_block_s_batch<P, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sizeof(SapSmemT<false>));
         attr = true;
     }
+    const bool sa = sap_stage_clover();
     const auto *args = (const SapArgs<P> *)b->args;
     const int last_col = b->nblk[1] > 0 ? 1 : 0;
     for (int cyc = 0; cyc < b->ncy; cyc++)
         for (int col = 0; col < 2; col++) {
             if (b->nblk[col] == 0) continue;
-            const int grid = std::min(b->nblk[col], b->nsm);
-            k_sap_block_s_batch<P><<<grid, 2 * b->nh, sizeof(SapSmem), hc->stream>>>(
-                args, col, b->blk[col], b->nblk[col], active, b->queue + 2 * cyc + col);
+            if (sa)
+                k_sap_block_s_batch<P, true><<<std::min(b->nblk[col], b->nsm), 2 * b->nh, sizeof(SapSmemT<true>),
+                                               hc->stream>>>(args, col, b->blk[col], b->nblk[col], active,
+                                                             b->queue + 2 * cyc + col);
+            else
+                k_sap_block_s_batch<P, false><<<std::min(b->nblk[col], 2 * b->nsm), 2 * b->nh,
+                                                sizeof(SapSmemT<false>), hc->stream>>>(
+                    args, col, b->blk[col], b->nblk[col], active, b->queue + 2 * cyc + col);
             hc->n_kernel_launches++;
             LQCD_LAUNCH_CHECK(hc);
             if (cyc == b->ncy - 1 && col == last_col) continue;

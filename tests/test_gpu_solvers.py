@@ -91,3 +91,17 @@ def test_not_converged_reported(p8):
     bad[3, 1, 2] = np.nan
     psi, info, st = P.ctx.solve_dhat(to_gpu(bad), solver=lqcd.SOLVER_CGNR, tol=1e-10, nmx=10, check=False)
     assert st == 7
+
+
+@pytest.mark.parametrize("prec", [lqcd.F32, lqcd.F16S], ids=["f32", "f16s"])
+def test_sap_clover_staging_is_bitwise_neutral(prec, monkeypatch):
+    """The resident SAP kernel reads the clover blocks from shared memory
+    (staged, one CTA per SM) or through L1/L2 (two CTAs per SM): same values,
+    same arithmetic order, identical results."""
+    P = Pair((8, 8, 8, 8), kappa=0.1355)
+    eta = to_gpu(synth.gaussian_spinor(P.V, 5))
+    out = {}
+    for stage in ("0", "1"):
+        monkeypatch.setenv("LQCD_SAP_STAGE_A", stage)
+        out[stage] = P.ctx.sap(eta, ncy=4, nmr=5, prec=prec)
+    assert torch.equal(out["0"], out["1"])
