@@ -521,24 +521,31 @@ __global__ void k_block_jacobi(int nblk, int Ns, long N, int nrhs, const double2
     }
 }
 
-// FP32 operator variants: matrices stored as float2, products and the row sums
-// in float, FP64 vectors in and out (the coarse GCR itself stays FP64)
+// FP32 operator variants: matrices stored as float2, the input vector given in
+// float (converted once per application by k_to_float2), products and the row
+// sums in float; FP64 vectors out (the coarse GCR itself stays FP64)
+__device__ __forceinline__ void warp_sum2f(float &re, float &im)
+{
+    for (int o = 16; o > 0; o >>= 1) {
+        re += __shfl_down_sync(0xffffffffu, re, o);
+        im += __shfl_down_sync(0xffffffffu, im, o);
+    }
+}
 __global__ void k_block_jacobi32(int nblk, int Ns, long N, int nrhs, const float2 *__restrict__ Dinv,
-                                 const double2 *__restrict__ in, double2 *out)
+                                 const float2 *__restrict__ in, double2 *out)
 {
     const int b = blockIdx.x, k = threadIdx.x >> 5, l = threadIdx.x & 31;
     if (b >= nblk || k >= Ns) return;
     float2 a = l < Ns ? Dinv[((size_t)b * Ns + k) * Ns + l] : make_float2(0, 0);
     for (int r = 0; r < nrhs; r++) {
-        double2 yd = l < Ns ? in[r * N + (long)b * Ns + l] : make_double2(0, 0);
-        float yx = (float)yd.x, yy = (float)yd.y;
-        double re = a.x * yx - a.y * yy, im = a.x * yy + a.y * yx;
-        warp_sum2(re, im);
+        const float2 y = l < Ns ? in[r * N + (long)b * Ns + l] : make_float2(0, 0);
+        float re = a.x * y.x - a.y * y.y, im = a.x * y.y + a.y * y.x;
+        warp_sum2f(re, im);
         if (l == 0) out[r * N + (long)b * Ns + k] = make_double2(re, im);
     }
 }
 __global__ void k_little_apply_b32(int nblk, int Ns, long N, int nrhs, const int *nbr,
-                                   const float2 *__restrict__ Aint, const double2 *__restrict__ c, double2 *out)
+                                   const float2 *__restrict__ Aint, const float2 *__restrict__ c, double2 *out)
 {
     const int b = blockIdx.x, k = threadIdx.x >> 5, l = threadIdx.x & 31;
     if (b >= nblk || k >= Ns) return;
@@ -552,18 +559,16 @@ __global__ void k_little_apply_b32(int nblk, int Ns, long N, int nrhs, const int
     for (int r = 0; r < nrhs; r++) {
         float re = 0, im = 0;
         if (l < Ns) {
-            const double2 *cr = c + r * N + l;
+            const float2 *cr = c + r * N + l;
 #pragma unroll
             for (int j = 0; j < 9; j++) {
-                double2 yd = cr[(long)nb[j] * Ns];
-                float yx = (float)yd.x, yy = (float)yd.y;
-                re += a[j].x * yx - a[j].y * yy;
-                im += a[j].x * yy + a[j].y * yx;
+                const float2 y = cr[(long)nb[j] * Ns];
+                re += a[j].x * y.x - a[j].y * y.y;
+                im += a[j].x * y.y + a[j].y * y.x;
             }
         }
-        double dre = re, dim = im;
-        warp_sum2(dre, dim);
-        if (l == 0) out[r * N + (long)b * Ns + k] = make_double2(dre, dim);
+        warp_sum2f(re, im);
+        if (l == 0) out[r * N + (long)b * Ns + k] = make_double2(re, im);
     }
 }
 __global__ void k_to_float2(long n, const double2 *in, float2 *out)
@@ -691,14 +696,27 @@ lqcd_status expand(lqcd_ctx *c, const double2 *cv, double2 *out)
 {
     return c->dfl->prec == LQCD_F64 ? launch_expand<double2>(c, cv, out) : launch_expand<float4>(c, cv, out);
 }
+// float copy of coarse vectors for the FP32 operator (grown on demand)
+lqcd_status coarse_f32(lqcd_ctx *c, long n, float2 **out)
+{
+    void *p;
+    LQCD_TRY(ws_get(c, WS_COARSE_F32, n * sizeof(float2), &p));
+    *out = (float2 *)p;
+    return LQCD_OK;
+}
+
 lqcd_status little_apply_b(lqcd_ctx *c, const double2 *cv, double2 *out, int nrhs)
 {
     DflState *d = c->dfl;
     long N = (long)d->B.nblk * d->Ns;
-    if (d->Aint32)
-        k_little_apply_b32<<<d->B.nblk, 32 * d->Ns, 0, c->stream>>>(d->B.nblk, d->Ns, N, nrhs, d->nbr, d->Aint32, cv,
+    if (d->Aint32) {
+        float2 *cf;
+        LQCD_TRY(coarse_f32(c, N * nrhs, &cf));
+        k_to_float2<<<div_up(N * nrhs, 256), 256, 0, c->stream>>>(N * nrhs, cv, cf);
+        k_little_apply_b32<<<d->B.nblk, 32 * d->Ns, 0, c->stream>>>(d->B.nblk, d->Ns, N, nrhs, d->nbr, d->Aint32, cf,
                                                                     out);
-    else
+        c->n_kernel_launches++;
+    } else
         k_little_apply_b<<<d->B.nblk, 32 * d->Ns, 0, c->stream>>>(d->B.nblk, d->Ns, N, nrhs, d->nbr, d->Aint, cv, out);
     c->n_kernel_launches++;
     LQCD_LAUNCH_CHECK(c);
@@ -710,9 +728,13 @@ lqcd_status block_jacobi(lqcd_ctx *c, const double2 *in, double2 *out, int nrhs)
 {
     DflState *d = c->dfl;
     long N = (long)d->B.nblk * d->Ns;
-    if (d->Dinv32)
-        k_block_jacobi32<<<d->B.nblk, 32 * d->Ns, 0, c->stream>>>(d->B.nblk, d->Ns, N, nrhs, d->Dinv32, in, out);
-    else
+    if (d->Dinv32) {
+        float2 *cf;
+        LQCD_TRY(coarse_f32(c, N * nrhs, &cf));
+        k_to_float2<<<div_up(N * nrhs, 256), 256, 0, c->stream>>>(N * nrhs, in, cf);
+        k_block_jacobi32<<<d->B.nblk, 32 * d->Ns, 0, c->stream>>>(d->B.nblk, d->Ns, N, nrhs, d->Dinv32, cf, out);
+        c->n_kernel_launches++;
+    } else
         k_block_jacobi<<<d->B.nblk, 32 * d->Ns, 0, c->stream>>>(d->B.nblk, d->Ns, N, nrhs, d->Dinv, in, out);
     c->n_kernel_launches++;
     LQCD_LAUNCH_CHECK(c);

@@ -154,6 +154,7 @@ enum {
     WS_NET_BATCH_T,
     WS_NET_FALLBACK,
     WS_HASEN,
+    WS_COARSE_F32,
 };
 lqcd_status ws_get(lqcd_ctx *c, int slot, size_t bytes, void **out);
 

@@ -29,9 +29,9 @@
 
 namespace {
 
-constexpr int PT_SITES = 32;
+constexpr int PT_SITES = 64;
 constexpr int PT_ROWS = 3 * PT_SITES;   // (site, colour) rows per CTA
-constexpr int PT_THREADS = 192;         // 6 warps x 16 rows
+constexpr int PT_THREADS = 192;         // 6 warps x 32 rows (two m16 tiles each)
 constexpr int PT_CMAX = 2;
 
 using bf16 = __nv_bfloat16;
@@ -83,53 +83,101 @@ __device__ __forceinline__ long lex_index(const Geom &g, const int c[4])
 {
     return c[3] + (long)g.L[3] * (c[2] + (long)g.L[2] * (c[1] + (long)g.L[1] * c[0]));
 }
-__device__ __forceinline__ void link32(const Geom &g, const float4 *U, long s, const int c[4], int mu, cx<float> u[3][3])
+// ------------------------------------------------------------ gather
+// Per CTA, once per site of its tile and path d: the neighbour site, the
+// first float4 of the path's link (two stored rows) and the hop's boundary sign.
+struct PtStage {
+    long lnk[9][PT_SITES];
+    int nbr[9][PT_SITES];
+    float sg[9][PT_SITES];
+};
+
+__device__ void pt_stage_sites(const Geom &g, long x0, PtStage &S)
 {
-    const int p = (c[0] + c[1] + c[2] + c[3]) & 1;
-    const float4 *b = U + (long)((p * 4 + mu) * 3) * g.Vh + (s >> 1);
-#pragma unroll
-    for (int q = 0; q < 3; q++) {
-        float4 t = __ldg(b + q * (long)g.Vh);
-        u[(2 * q) / 3][(2 * q) % 3] = mk(t.x, t.y);
-        u[(2 * q + 1) / 3][(2 * q + 1) % 3] = mk(t.z, t.w);
+    for (int it = threadIdx.x; it < 9 * PT_SITES; it += blockDim.x) {
+        const int s = it % PT_SITES, d = it / PT_SITES;
+        const long x = x0 + s;
+        if (x >= g.V) continue;
+        int c[4];
+        lex_coords(g, x, c);
+        if (d == 0) {
+            S.nbr[0][s] = (int)x;
+            S.lnk[0][s] = -1;
+            S.sg[0][s] = 1.f;
+            continue;
+        }
+        const int mu = (d - 1) >> 1;
+        const bool fwd = d & 1;
+        int yc[4] = {c[0], c[1], c[2], c[3]};
+        const int v = yc[mu] + (fwd ? 1 : -1);
+        yc[mu] = v < 0 ? v + g.L[mu] : (v >= g.L[mu] ? v - g.L[mu] : v);
+        const long y = lex_index(g, yc);
+        float sgn = 1.f;
+        if (mu == 0 && ((fwd && c[0] == g.L[0] - 1) || (!fwd && c[0] == 0))) sgn = (float)g.bc_t;
+        // forward: U_mu(x) (parity of x); backward: U_mu(y) (parity of y), daggered
+        const int *lc = fwd ? c : yc;
+        const long ls = fwd ? x : y;
+        const int p = (lc[0] + lc[1] + lc[2] + lc[3]) & 1;
+        S.nbr[d][s] = (int)y;
+        S.lnk[d][s] = (long)((p * 4 + mu) * 3) * g.Vh + (ls >> 1);
+        S.sg[d][s] = sgn;
     }
-    u[2][0] = conjx(u[0][1] * u[1][2] - u[0][2] * u[1][1]);
-    u[2][1] = conjx(u[0][2] * u[1][0] - u[0][0] * u[1][2]);
-    u[2][2] = conjx(u[0][0] * u[1][1] - u[0][1] * u[1][0]);
 }
 
-// z = (T_d f)(x)
-template <class ACT>
-__device__ __forceinline__ void transport(const Geom &g, const float4 *U, const ACT *f, long x, const int c[4], int d,
-                                          cx<float> z[12])
+// The transported inputs (T_d y_i)(x) of the tile: one item per (site, path);
+// the path's link is loaded and its third row rebuilt once and applied to every
+// input channel.  sink(s, i, d, z) receives the 12 spin-colour components.
+template <class ACT, class SINK>
+__device__ __forceinline__ void pt_gather(const Geom &g, const float4 *U, const ACT *in, int cin, long x0,
+                                          const PtStage &S, SINK sink)
 {
-    if (d == 0) {
-        act_load(f, x, z);
-        return;
-    }
-    const int mu = (d - 1) >> 1;
-    const bool fwd = d & 1;
-    int yc[4] = {c[0], c[1], c[2], c[3]};
-    int v = yc[mu] + (fwd ? 1 : -1);
-    yc[mu] = v < 0 ? v + g.L[mu] : (v >= g.L[mu] ? v - g.L[mu] : v);
-    const long y = lex_index(g, yc);
-    float s = 1.f;
-    if (mu == 0 && ((fwd && c[0] == g.L[0] - 1) || (!fwd && c[0] == 0))) s = (float)g.bc_t;
-    cx<float> in[12], u[3][3];
-    act_load(f, y, in);
-    if (fwd)
-        link32(g, U, x, c, mu, u);
-    else
-        link32(g, U, y, yc, mu, u);
+    const long V = g.V;
+    for (int it = threadIdx.x; it < 9 * PT_SITES; it += blockDim.x) {
+        const int s = it % PT_SITES, d = it / PT_SITES;
+        const bool ok = x0 + s < V;
+        cx<float> u[3][3];
+        if (ok && d > 0) {
+            const float4 *b = U + S.lnk[d][s];
 #pragma unroll
-    for (int sp = 0; sp < 4; sp++)
-#pragma unroll
-        for (int a = 0; a < 3; a++) {
-            cx<float> acc = mk(0.f, 0.f);
-#pragma unroll
-            for (int b = 0; b < 3; b++) acc = acc + (fwd ? u[a][b] * in[3 * sp + b] : cmulc(u[b][a], in[3 * sp + b]));
-            z[3 * sp + a] = s * acc;
+            for (int q = 0; q < 3; q++) {
+                const float4 t = __ldg(b + q * (long)g.Vh);
+                u[(2 * q) / 3][(2 * q) % 3] = mk(t.x, t.y);
+                u[(2 * q + 1) / 3][(2 * q + 1) % 3] = mk(t.z, t.w);
+            }
+            u[2][0] = conjx(u[0][1] * u[1][2] - u[0][2] * u[1][1]);
+            u[2][1] = conjx(u[0][2] * u[1][0] - u[0][0] * u[1][2]);
+            u[2][2] = conjx(u[0][0] * u[1][1] - u[0][1] * u[1][0]);
         }
+        const bool fwd = d & 1;
+        const int y = ok ? S.nbr[d][s] : 0;
+        const float sgn = ok ? S.sg[d][s] : 1.f;
+        for (int i = 0; i < cin; i++) {
+            cx<float> z[12];
+            if (!ok) {
+#pragma unroll
+                for (int k = 0; k < 12; k++) z[k] = mk(0.f, 0.f);
+            } else {
+                cx<float> v[12];
+                act_load(in + (long)i * 12 * V, y, v);
+                if (d == 0) {
+#pragma unroll
+                    for (int k = 0; k < 12; k++) z[k] = v[k];
+                } else {
+#pragma unroll
+                    for (int sp = 0; sp < 4; sp++)
+#pragma unroll
+                        for (int a = 0; a < 3; a++) {
+                            cx<float> acc = mk(0.f, 0.f);
+#pragma unroll
+                            for (int b = 0; b < 3; b++)
+                                acc = acc + (fwd ? u[a][b] * v[3 * sp + b] : cmulc(u[b][a], v[3 * sp + b]));
+                            z[3 * sp + a] = sgn * acc;
+                        }
+                }
+            }
+            sink(s, i, d, z);
+        }
+    }
 }
 
 // ------------------------------------------------------------ layer
@@ -146,6 +194,16 @@ struct LayerArgs {
 
 __device__ __forceinline__ unsigned ld_b32(const bf16 *p) { return *reinterpret_cast<const unsigned *>(p); }
 
+// row pitch (bf16) of the A tile: room for Kp columns, even, and an odd
+// number of 4-byte words per 3 rows, so that the stride-3-row stores of the
+// gather and the fragment loads of the MMA both spread over the banks
+__host__ __device__ inline int pt_ld(int Kp)
+{
+    int ld = Kp + 8;
+    if (((3 * ld / 2) & 1) == 0) ld += 2;
+    return ld;
+}
+
 template <class ACT>
 __global__ void __launch_bounds__(PT_THREADS) k_ptc_layer(LayerArgs a)
 {
@@ -155,11 +213,13 @@ __global__ void __launch_bounds__(PT_THREADS) k_ptc_layer(LayerArgs a)
     const long x0 = (long)blockIdx.x * PT_SITES;
     const long V = a.g.V;
     const int cin = a.cin, cout = a.cout, tid = threadIdx.x;
-    const int K = 72 * cin, Kp = (K + 15) / 16 * 16, ld = Kp + 8;
+    const int K = 72 * cin, Kp = (K + 15) / 16 * 16, ld = pt_ld(Kp);
     constexpr bool BF = sizeof(ACT) == 4;
-    bf16 *A = (bf16 *)smraw;                                   // [rows][ld]
+    PtStage &S = *reinterpret_cast<PtStage *>(smraw);
+    unsigned char *tile = smraw + sizeof(PtStage);
+    bf16 *A = (bf16 *)tile;                                    // [rows][ld]
     bf16 *Bs = A + PT_ROWS * ld;                               // [8 cout][ld]
-    cx<float> *Z = (cx<float> *)smraw;                         // [rows][36 cin]
+    cx<float> *Z = (cx<float> *)tile;                          // [rows][36 cin]
     cx<float> *Ws = Z + PT_ROWS * 36 * cin;                    // [cout*cin*144]
     if (BF) {
         for (int e = tid; e < 8 * cout * Kp; e += blockDim.x) Bs[(e / Kp) * ld + e % Kp] = a.Bt[e];
@@ -171,60 +231,58 @@ __global__ void __launch_bounds__(PT_THREADS) k_ptc_layer(LayerArgs a)
             Ws[e] = mk(w.x, w.y);
         }
     }
-    // gather the transported inputs
-    for (int it = tid; it < PT_SITES * cin * 9; it += blockDim.x) {
-        const int sl = it / (cin * 9), rem = it % (cin * 9), i = rem / 9, d = rem % 9;
-        const long x = x0 + sl;
-        cx<float> z[12];
-        if (x < V) {
-            int c[4];
-            lex_coords(a.g, x, c);
-            transport(a.g, a.U, in + (long)i * 12 * V, x, c, d, z);
-        } else {
+    pt_stage_sites(a.g, x0, S);
+    __syncthreads();
+    if (BF) {
+        pt_gather(a.g, a.U, in, cin, x0, S, [&](int s, int i, int d, const cx<float> z[12]) {
 #pragma unroll
-            for (int k = 0; k < 12; k++) z[k] = mk(0.f, 0.f);
-        }
+            for (int sp = 0; sp < 4; sp++)
 #pragma unroll
-        for (int sp = 0; sp < 4; sp++)
-#pragma unroll
-            for (int cc = 0; cc < 3; cc++) {
-                const int kk = (i * 9 + d) * 4 + sp, row = 3 * sl + cc;
-                if (BF) {
-                    A[row * ld + 2 * kk] = __float2bfloat16(z[3 * sp + cc].re);
-                    A[row * ld + 2 * kk + 1] = __float2bfloat16(z[3 * sp + cc].im);
-                } else {
-                    Z[row * 36 * cin + kk] = z[3 * sp + cc];
+                for (int cc = 0; cc < 3; cc++) {
+                    const int kk = (i * 9 + d) * 4 + sp, row = 3 * s + cc;
+                    *reinterpret_cast<bf162 *>(A + row * ld + 2 * kk) =
+                        __floats2bfloat162_rn(z[3 * sp + cc].re, z[3 * sp + cc].im);
                 }
-            }
+        });
+    } else {
+        pt_gather(a.g, a.U, in, cin, x0, S, [&](int s, int i, int d, const cx<float> z[12]) {
+#pragma unroll
+            for (int sp = 0; sp < 4; sp++)
+#pragma unroll
+                for (int cc = 0; cc < 3; cc++) Z[(3 * s + cc) * 36 * cin + (i * 9 + d) * 4 + sp] = z[3 * sp + cc];
+        });
     }
     __syncthreads();
     if (BF) {
-        // tensor-core contraction: warp w owns rows 16w..16w+15
+        // tensor-core contraction: warp w owns rows 32w .. 32w+31 (two m16 tiles)
         const int w = tid >> 5, lane = tid & 31, gq = lane >> 2, tq = lane & 3;
-        const bf16 *Ar = A + (16 * w) * ld;
         for (int nt = 0; nt < cout; nt++) {
-            float d0 = 0.f, d1 = 0.f, d2 = 0.f, d3 = 0.f;
             const bf16 *Br = Bs + (8 * nt + gq) * ld;
-            for (int k0 = 0; k0 < Kp; k0 += 16) {
-                unsigned a0 = ld_b32(Ar + gq * ld + k0 + 2 * tq);
-                unsigned a1 = ld_b32(Ar + (gq + 8) * ld + k0 + 2 * tq);
-                unsigned a2 = ld_b32(Ar + gq * ld + k0 + 8 + 2 * tq);
-                unsigned a3 = ld_b32(Ar + (gq + 8) * ld + k0 + 8 + 2 * tq);
-                unsigned b0 = ld_b32(Br + k0 + 2 * tq);
-                unsigned b1 = ld_b32(Br + k0 + 8 + 2 * tq);
-                asm volatile(
-                    "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-                    "{%0,%1,%2,%3};\n"
-                    : "+f"(d0), "+f"(d1), "+f"(d2), "+f"(d3)
-                    : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
-            }
-            // columns 2tq, 2tq+1 of n-tile nt are (re, im) of output channel nt, spin tq
 #pragma unroll
-            for (int h = 0; h < 2; h++) {
-                const int row = 16 * w + gq + 8 * h;
-                const int sl = row / 3, cc = row % 3;
-                const long x = x0 + sl;
-                if (x < V) act_store1(out, (long)nt * 12 * V + 12 * x + 3 * tq + cc, h ? d2 : d0, h ? d3 : d1);
+            for (int mi = 0; mi < 2; mi++) {
+                const bf16 *Ar = A + (32 * w + 16 * mi) * ld;
+                float d0 = 0.f, d1 = 0.f, d2 = 0.f, d3 = 0.f;
+                for (int k0 = 0; k0 < Kp; k0 += 16) {
+                    unsigned a0 = ld_b32(Ar + gq * ld + k0 + 2 * tq);
+                    unsigned a1 = ld_b32(Ar + (gq + 8) * ld + k0 + 2 * tq);
+                    unsigned a2 = ld_b32(Ar + gq * ld + k0 + 8 + 2 * tq);
+                    unsigned a3 = ld_b32(Ar + (gq + 8) * ld + k0 + 8 + 2 * tq);
+                    unsigned b0 = ld_b32(Br + k0 + 2 * tq);
+                    unsigned b1 = ld_b32(Br + k0 + 8 + 2 * tq);
+                    asm volatile(
+                        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+                        "{%0,%1,%2,%3};\n"
+                        : "+f"(d0), "+f"(d1), "+f"(d2), "+f"(d3)
+                        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+                }
+                // columns 2tq, 2tq+1 of n-tile nt are (re, im) of output channel nt, spin tq
+#pragma unroll
+                for (int h = 0; h < 2; h++) {
+                    const int row = 32 * w + 16 * mi + gq + 8 * h;
+                    const int sl = row / 3, cc = row % 3;
+                    const long x = x0 + sl;
+                    if (x < V) act_store1(out, (long)nt * 12 * V + 12 * x + 3 * tq + cc, h ? d2 : d0, h ? d3 : d1);
+                }
             }
         }
     } else {
@@ -264,27 +322,19 @@ __global__ void __launch_bounds__(PT_THREADS) k_ptc_wgrad(WgradArgs a)
     const long x0 = (long)blockIdx.x * PT_SITES;
     const long V = a.g.V;
     const int cin = a.cin, cout = a.cout, tid = threadIdx.x;
-    cx<float> *Z = (cx<float> *)smraw;                 // [rows][36 cin]
-    cx<float> *Dt = Z + PT_ROWS * 36 * cin;            // [rows][4 cout]
-    for (int it = tid; it < PT_SITES * cin * 9; it += blockDim.x) {
-        const int sl = it / (cin * 9), rem = it % (cin * 9), i = rem / 9, d = rem % 9;
-        const long x = x0 + sl;
-        cx<float> z[12];
-        if (x < V) {
-            int c[4];
-            lex_coords(a.g, x, c);
-            transport(a.g, a.U, y + (long)i * 12 * V, x, c, d, z);
-        } else {
-#pragma unroll
-            for (int k = 0; k < 12; k++) z[k] = mk(0.f, 0.f);
-        }
+    PtStage &S = *reinterpret_cast<PtStage *>(smraw);
+    cx<float> *Z = (cx<float> *)(smraw + sizeof(PtStage));   // [rows][36 cin]
+    cx<float> *Dt = Z + PT_ROWS * 36 * cin;                   // [rows][4 cout]
+    pt_stage_sites(a.g, x0, S);
+    __syncthreads();
+    pt_gather(a.g, a.U, y, cin, x0, S, [&](int s, int i, int d, const cx<float> z[12]) {
 #pragma unroll
         for (int sp = 0; sp < 4; sp++)
 #pragma unroll
-            for (int cc = 0; cc < 3; cc++) Z[(3 * sl + cc) * 36 * cin + (i * 9 + d) * 4 + sp] = z[3 * sp + cc];
-    }
+            for (int cc = 0; cc < 3; cc++) Z[(3 * s + cc) * 36 * cin + (i * 9 + d) * 4 + sp] = z[3 * sp + cc];
+    });
     for (int it = tid; it < PT_SITES * cout; it += blockDim.x) {
-        const int sl = it / cout, o = it % cout;
+        const int sl = it % PT_SITES, o = it / PT_SITES;
         const long x = x0 + sl;
         cx<float> v[12];
         if (x < V)
@@ -570,12 +620,14 @@ lqcd_status net_rebuild(lqcd_ctx *c)
 
 size_t layer_smem(lqcd_prec act, int cin, int cout)
 {
-    if (act == LQCD_BF16) return (size_t)(PT_ROWS + 8 * cout) * (kpad(cin) + 8) * sizeof(bf16);
-    return (size_t)PT_ROWS * 36 * cin * sizeof(cx<float>) + (size_t)cout * cin * 144 * sizeof(cx<float>);
+    if (act == LQCD_BF16) return sizeof(PtStage) + (size_t)(PT_ROWS + 8 * cout) * pt_ld(kpad(cin)) * sizeof(bf16);
+    return sizeof(PtStage) + (size_t)PT_ROWS * 36 * cin * sizeof(cx<float>) +
+           (size_t)cout * cin * 144 * sizeof(cx<float>);
 }
 size_t wgrad_smem(int cin, int cout)
 {
-    return (size_t)PT_ROWS * 36 * cin * sizeof(cx<float>) + (size_t)PT_ROWS * 4 * cout * sizeof(cx<float>);
+    return sizeof(PtStage) + (size_t)PT_ROWS * 36 * cin * sizeof(cx<float>) +
+           (size_t)PT_ROWS * 4 * cout * sizeof(cx<float>);
 }
 
 template <class ACT>
@@ -584,7 +636,7 @@ lqcd_status launch_layer(lqcd_ctx *c, const void *in, void *out, int cin, int co
 {
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(k_ptc_layer<ACT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
+        cudaFuncSetAttribute(k_ptc_layer<ACT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         attr = true;
     }
     LayerArgs a;
@@ -625,7 +677,7 @@ lqcd_status wgrad_t(lqcd_ctx *c, int l, const void *y, const void *delta, int nb
 {
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(k_ptc_wgrad<ACT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
+        cudaFuncSetAttribute(k_ptc_wgrad<ACT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         attr = true;
     }
     NetState *n = c->net;
