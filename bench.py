@@ -154,7 +154,8 @@ def cpu_baseline(steps: int = 2):
 KAPPA_OF = {(8, 8, 8, 8): 0.1355, (32, 16, 16, 16): 0.1357, (48, 24, 24, 24): 0.13625, (64, 32, 32, 32): 0.1363}
 
 
-def solve_once(ctx, lqcd, eta, solver, inner, Ns=20, ninv=8, ctol=1e-2, seed=100, cnmx=4096, cnkv=16, cprec=None):
+def solve_once(ctx, lqcd, eta, solver, inner, Ns=20, ninv=8, ctol=1e-2, seed=100, cnmx=4096, cnkv=16, cprec=None,
+               nkv=16, sap_prec=None):
     """Time-to-solution of Dhat psi = eta (all fields of eta) to 1e-10 with the
     given solver; the subspace build is timed separately and included in total."""
     import torch
@@ -177,8 +178,9 @@ def solve_once(ctx, lqcd, eta, solver, inner, Ns=20, ninv=8, ctol=1e-2, seed=100
                     "coarse_prec": "f32" if cp == lqcd.F32 else "f64", "build_s": round(build_s, 4)})
     sid = {"cgnr": lqcd.SOLVER_CGNR, "sap": lqcd.SOLVER_SAP_GCR, "dfl": lqcd.SOLVER_DFL_SAP_GCR}[solver]
     t0 = time.perf_counter()
+    sp = prec if sap_prec is None else sap_prec
     psi, info, st = ctx.solve_dhat(eta, solver=sid, tol=1e-10, nmx=20000 if solver == "cgnr" else 4096,
-                                   sap_prec=prec, inner=prec, check=False)
+                                   nkv=nkv, sap_prec=sp, inner=prec, check=False)
     torch.cuda.synchronize()
     solve_s = time.perf_counter() - t0
     res.update({"status": st, "solve_s": round(solve_s, 4), "total_s": round(solve_s + build_s, 4),
@@ -193,13 +195,14 @@ def time_to_solve(ctx, lqcd, eta, net=None):
     """Time-to-solution of Dhat psi = eta for the 12 sources to a true relative
     residual <= 1e-10 (checked in FP64), subspace builds included:
       plain_f64 : deflated SAP-GCR, FP64 everywhere, one source at a time
-      dfl_mixed : deflated SAP-GCR, FP32 SAP / subspace / little operator,
-                  FP64 outer GCR, the 12 sources in one batched solve
-      learned   : dfl_mixed with the trained network as the smoother (deflated
-                  SAP where its step fails); training at 32x16^3 reported apart
-      sap_f16s  : SAP-GCR, FP16 (per-site scale) SAP, FP32 stencil, 12 batched
-      chosen    : SAP-GCR, FP32 SAP and stencil, FP64 outer GCR, the 12
-                  sources in one batched solve (fastest measured form)
+      chosen    : deflated SAP-GCR, FP16 (per-site scale) SAP, FP32 subspace /
+                  little operator / stencil, FP64 outer GCR, the 12 sources in
+                  one batched solve (fastest measured form)
+      dfl_mixed : the same with FP32 SAP
+      learned   : the same subspace with the trained network as the smoother
+                  (deflated SAP where its step fails); training at 32x16^3
+                  reported apart
+      sap_f32, sap_f16s : SAP-GCR without deflation, FP32 / FP16 SAP
     Every form is first run for two steps (and its subspace built once) so
     that launch-shape tuning and workspace growth stay out of the timings."""
     import torch
@@ -214,6 +217,9 @@ def time_to_solve(ctx, lqcd, eta, net=None):
                       coarse_prec=prec)
         e = one if prec == lqcd.F64 else eta
         ctx.solve_dhat(e, solver=lqcd.SOLVER_DFL_SAP_GCR, tol=1e-10, nmx=2, sap_prec=prec, inner=prec, check=False)
+        if prec == lqcd.F32:
+            ctx.solve_dhat(eta, solver=lqcd.SOLVER_DFL_SAP_GCR, tol=1e-10, nmx=2, sap_prec=lqcd.F16S, inner=prec,
+                           check=False)
         if prec == lqcd.F32 and net is not None:
             ctx.net_set(NET_CHANS, net["W"], act=lqcd.BF16)
             ctx.solve_dhat(eta, solver=lqcd.SOLVER_DFL_NET_GCR, tol=1e-10, nmx=2, sap_prec=prec, inner=prec,
@@ -221,8 +227,8 @@ def time_to_solve(ctx, lqcd, eta, net=None):
     del v0
     torch.cuda.synchronize()
     r, _ = solve_once(ctx, lqcd, eta, "sap", "f32")
-    out["chosen"] = {"form": "SAP-GCR, FP32 SAP/stencil, FP64 GCR, 12 RHS batched", "seconds": r["total_s"],
-                     "iters": max(r["iters"]), "max_relres_dhat": r["max_relres_dhat"], "status": r["status"]}
+    out["sap_f32"] = {"form": "SAP-GCR, FP32 SAP/stencil, FP64 GCR, 12 RHS batched", "seconds": r["total_s"],
+                      "iters": max(r["iters"]), "max_relres_dhat": r["max_relres_dhat"], "status": r["status"]}
     t0 = time.perf_counter()
     _, info, st = ctx.solve_dhat(eta, solver=lqcd.SOLVER_SAP_GCR, tol=1e-10, sap_prec=lqcd.F16S, inner=lqcd.F32,
                                  check=False)
@@ -230,25 +236,30 @@ def time_to_solve(ctx, lqcd, eta, net=None):
     out["sap_f16s"] = {"form": "SAP-GCR, FP16 (per-site scale) SAP, FP32 stencil, FP64 GCR, 12 RHS batched",
                        "seconds": round(time.perf_counter() - t0, 4), "iters": max(i["iters"] for i in info),
                        "max_relres_dhat": max(i["relres_dhat"] for i in info), "status": st}
+    # one subspace build (timed, included in every deflated form) and three smoothers on it
     r, _ = solve_once(ctx, lqcd, eta, "dfl", "f32", Ns=20, ninv=8, ctol=1e-2, cnmx=64, cprec="f32")
+    build = r["build_s"]
     out["dfl_mixed"] = {"form": "deflated SAP-GCR (Ns=20, 4^4 blocks), FP32 SAP/subspace/little operator, FP64 GCR, "
-                                "12 RHS batched", "seconds": r["total_s"], "build_s": r["build_s"],
+                                "12 RHS batched", "seconds": r["total_s"], "build_s": build,
                         "iters": max(r["iters"]), "max_relres_dhat": r["max_relres_dhat"], "status": r["status"]}
+
+    def deflated(sid, sap_prec):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, info, st = ctx.solve_dhat(eta, solver=sid, tol=1e-10, sap_prec=sap_prec, inner=lqcd.F32, check=False)
+        torch.cuda.synchronize()
+        return {"seconds": round(time.perf_counter() - t0 + build, 4), "build_s": build,
+                "iters": max(i["iters"] for i in info), "net_fallbacks": sum(i["net_fallbacks"] for i in info),
+                "max_relres_dhat": max(i["relres_dhat"] for i in info), "status": st}
+    out["chosen"] = {"form": "deflated SAP-GCR (Ns=20, 4^4 blocks), FP16 (per-site scale) SAP, FP32 subspace, "
+                             "little operator and stencil, FP64 GCR, 12 RHS batched",
+                     **deflated(lqcd.SOLVER_DFL_SAP_GCR, lqcd.F16S)}
     if net is not None:
         # the same subspace, the network in place of the SAP smoother
         ctx.net_set(NET_CHANS, net["W"], act=lqcd.BF16)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        _, info, st = ctx.solve_dhat(eta, solver=lqcd.SOLVER_DFL_NET_GCR, tol=1e-10, sap_prec=lqcd.F32,
-                                     inner=lqcd.F32, check=False)
-        torch.cuda.synchronize()
-        solve_s = time.perf_counter() - t0
         out["learned"] = {"form": "deflated GCR (Ns=20), trained BF16 network as smoother, deflated FP32 SAP as "
                                   "fallback, FP64 GCR, 12 RHS batched",
-                          "seconds": round(solve_s + r["build_s"], 4), "build_s": r["build_s"],
-                          "iters": max(i["iters"] for i in info),
-                          "net_fallbacks": sum(i["net_fallbacks"] for i in info),
-                          "max_relres_dhat": max(i["relres_dhat"] for i in info), "status": st,
+                          **deflated(lqcd.SOLVER_DFL_NET_GCR, lqcd.F32),
                           "training": {"lattice": "32x16x16x16", "pairs": net["pairs"], "seconds": net["train_s"],
                                        "loss_first": net["loss_first"], "loss_last": net["loss_last"]}}
     total, build, iters, worst, st = 0.0, 0.0, 0, 0.0, 0
@@ -273,7 +284,7 @@ def time_to_solve(ctx, lqcd, eta, net=None):
     out["plain_f64"] = {"form": "deflated SAP-GCR (Ns=20, 4^4 blocks), FP64 throughout, one source at a time",
                         "seconds": round(total, 4), "build_s": build, "iters": iters, "max_relres_dhat": worst,
                         "status": st}
-    for k in ("chosen", "sap_f16s", "dfl_mixed", "learned"):
+    for k in ("chosen", "sap_f32", "sap_f16s", "dfl_mixed", "learned"):
         if k in out:
             out["speedup_%s_vs_plain_f64" % k] = round(out["plain_f64"]["seconds"] / out[k]["seconds"], 2)
     out["tolerance"] = 1e-10
@@ -289,7 +300,10 @@ def run_solve(args):
     ctx.clover_invert(kappa, CSW)
     eta = torch.from_numpy(synth.gaussian_spinor(args.nrhs * ctx.Vh, 1).reshape(args.nrhs, ctx.Vh, 4, 3)).cuda()
     res, _ = solve_once(ctx, lqcd, eta, args.solver, args.prec, Ns=args.Ns, ninv=args.ninv, ctol=args.ctol,
-                        cnmx=args.cnmx, cprec=args.cprec)
+                        cnmx=args.cnmx, cprec=args.cprec, nkv=args.nkv,
+                        sap_prec={"f16s": lqcd.F16S, "f32": lqcd.F32, "f64": lqcd.F64}.get(args.sap_prec))
+    res["nkv"] = args.nkv
+    res["sap_prec"] = args.sap_prec or args.prec
     res.update({"mode": "solve", "lattice": args.lattice, "kappa": kappa})
     print(json.dumps(res))
 
@@ -569,6 +583,8 @@ def main():
     ap.add_argument("--ctol", type=float, default=1e-2)
     ap.add_argument("--cnmx", type=int, default=4096, help="iteration budget of each little-Dirac solve")
     ap.add_argument("--cprec", default=None, choices=["f32", "f64"], help="little-Dirac operator precision")
+    ap.add_argument("--nkv", type=int, default=16, help="solve mode: GCR Krylov vectors per cycle")
+    ap.add_argument("--sap-prec", default=None, choices=["f16s", "f32", "f64"], help="solve mode: SAP precision")
     args = ap.parse_args()
     global DIMS
     DIMS = tuple(int(v) for v in args.lattice.split("x"))
