@@ -195,9 +195,11 @@ typedef struct {
     double coarse_tol;/* relative residual of the little-Dirac solve */
     int coarse_nkv;   /* GCR Krylov length of the little-Dirac solve */
     int coarse_nmx;   /* iteration limit of the little-Dirac solve */
-    lqcd_prec coarse_prec; /* arithmetic of the little-Dirac operator: LQCD_F64, or LQCD_F32
-                              (operator stored and applied in float; the GCR around it,
-                              its vectors and inner products stay FP64) */
+    lqcd_prec coarse_prec; /* arithmetic of the little-Dirac solve: LQCD_F64, or LQCD_F32
+                              (operator, block-Jacobi inverse, Krylov vectors and
+                              Gram-Schmidt in float; GCR scalars and the sums of the
+                              per-CTA partial inner products in FP64).  With LQCD_F32
+                              coarse_tol must be >= 1e-6, else LQCD_ERR_ARG */
 } lqcd_dfl_params;
 
 /* Build the deflation subspace ("locally deflated" solver, Sec. 3-4,

@@ -531,8 +531,11 @@ __device__ __forceinline__ void warp_sum2f(float &re, float &im)
         im += __shfl_down_sync(0xffffffffu, im, o);
     }
 }
+__device__ __forceinline__ void put2(double2 *p, float re, float im) { *p = make_double2(re, im); }
+__device__ __forceinline__ void put2(float2 *p, float re, float im) { *p = make_float2(re, im); }
+template <class OT>
 __global__ void k_block_jacobi32(int nblk, int Ns, long N, int nrhs, const float2 *__restrict__ Dinv,
-                                 const float2 *__restrict__ in, double2 *out)
+                                 const float2 *__restrict__ in, OT *out)
 {
     const int b = blockIdx.x, k = threadIdx.x >> 5, l = threadIdx.x & 31;
     if (b >= nblk || k >= Ns) return;
@@ -541,11 +544,12 @@ __global__ void k_block_jacobi32(int nblk, int Ns, long N, int nrhs, const float
         const float2 y = l < Ns ? in[r * N + (long)b * Ns + l] : make_float2(0, 0);
         float re = a.x * y.x - a.y * y.y, im = a.x * y.y + a.y * y.x;
         warp_sum2f(re, im);
-        if (l == 0) out[r * N + (long)b * Ns + k] = make_double2(re, im);
+        if (l == 0) put2(out + r * N + (long)b * Ns + k, re, im);
     }
 }
+template <class OT>
 __global__ void k_little_apply_b32(int nblk, int Ns, long N, int nrhs, const int *nbr,
-                                   const float2 *__restrict__ Aint, const float2 *__restrict__ c, double2 *out)
+                                   const float2 *__restrict__ Aint, const float2 *__restrict__ c, OT *out)
 {
     const int b = blockIdx.x, k = threadIdx.x >> 5, l = threadIdx.x & 31;
     if (b >= nblk || k >= Ns) return;
@@ -568,13 +572,113 @@ __global__ void k_little_apply_b32(int nblk, int Ns, long N, int nrhs, const int
             }
         }
         warp_sum2f(re, im);
-        if (l == 0) out[r * N + (long)b * Ns + k] = make_double2(re, im);
+        if (l == 0) put2(out + r * N + (long)b * Ns + k, re, im);
     }
 }
 __global__ void k_to_float2(long n, const double2 *in, float2 *out)
 {
     long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
     if (i < n) out[i] = make_float2((float)in[i].x, (float)in[i].y);
+}
+__global__ void k_to_double2(long n, const float2 *in, double2 *out)
+{
+    long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (i < n) out[i] = make_double2(in[i].x, in[i].y);
+}
+
+// FP32 coarse-vector BLAS (the coarse solve with the FP32 operator): per-CTA
+// partial dots accumulated in float, partials and their fixed-order sum in
+// double.  partial[(r*nb + b)*32 + i] for vector i of rhs r.
+constexpr int FDOT_K = 8;
+__global__ void __launch_bounds__(256) k_fdot_partial(long n, const float2 *__restrict__ A, long sa, long fa,
+                                                      const float2 *__restrict__ B, long fb, int k0, int kn,
+                                                      double2 *partial)
+{
+    const int r = blockIdx.y;
+    const float2 *Br = B + r * fb, *Ar = A + r * fa;
+    float re[FDOT_K], im[FDOT_K];
+#pragma unroll
+    for (int i = 0; i < FDOT_K; i++) re[i] = im[i] = 0.f;
+    for (long j = blockIdx.x * (long)blockDim.x + threadIdx.x; j < n; j += (long)gridDim.x * blockDim.x) {
+        const float2 bv = Br[j];
+#pragma unroll
+        for (int i = 0; i < FDOT_K; i++)
+            if (i < kn) {
+                const float2 a = Ar[(k0 + i) * sa + j];
+                re[i] += a.x * bv.x + a.y * bv.y;
+                im[i] += a.x * bv.y - a.y * bv.x;
+            }
+    }
+    __shared__ double sh[8][FDOT_K][2];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int i = 0; i < FDOT_K; i++) {
+        float x = re[i], m = im[i];
+        for (int o = 16; o > 0; o >>= 1) {
+            x += __shfl_down_sync(0xffffffffu, x, o);
+            m += __shfl_down_sync(0xffffffffu, m, o);
+        }
+        if (lane == 0) {
+            sh[warp][i][0] = x;
+            sh[warp][i][1] = m;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < kn) {
+        double x = 0, m = 0;
+        for (int w = 0; w < 8; w++) {
+            x += sh[w][threadIdx.x][0];
+            m += sh[w][threadIdx.x][1];
+        }
+        partial[((long)r * gridDim.x + blockIdx.x) * 32 + k0 + threadIdx.x] = make_double2(x, m);
+    }
+}
+__global__ void k_fdot_final(int nb, int k, const double2 *partial, double2 *out)
+{
+    const int i = blockIdx.x, r = blockIdx.y;
+    __shared__ double sx[128], sm[128];
+    double x = 0, m = 0;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+        const double2 v = partial[((long)r * nb + b) * 32 + i];
+        x += v.x;
+        m += v.y;
+    }
+    sx[threadIdx.x] = x;
+    sm[threadIdx.x] = m;
+    __syncthreads();
+    for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+        if (threadIdx.x < st) {
+            sx[threadIdx.x] += sx[threadIdx.x + st];
+            sm[threadIdx.x] += sm[threadIdx.x + st];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[r * k + i] = make_double2(sx[0], sm[0]);
+}
+// y_r += sign * sum_i cf[r*k + i] X_{i,r} (coefficients in device memory, FP64)
+__global__ void k_fmulti_axpy(long n, int k, const double2 *__restrict__ cf, const float2 *__restrict__ X, long sa,
+                              long fa, float2 *y, long fy, float sign)
+{
+    const int r = blockIdx.y;
+    const double2 *c = cf + r * k;
+    const float2 *Xr = X + r * fa;
+    float2 *yr = y + r * fy;
+    for (long j = blockIdx.x * (long)blockDim.x + threadIdx.x; j < n; j += (long)gridDim.x * blockDim.x) {
+        float2 b = yr[j];
+        float sr = 0.f, si = 0.f;
+        for (int i = 0; i < k; i++) {
+            const float2 a = Xr[i * sa + j];
+            const float cx = (float)c[i].x, cy = (float)c[i].y;
+            sr += cx * a.x - cy * a.y;
+            si += cx * a.y + cy * a.x;
+        }
+        yr[j] = make_float2(b.x + sign * sr, b.y + sign * si);
+    }
+}
+__global__ void k_fsub(long n, const float2 *a, const float2 *b, float2 *out)
+{
+    long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (i < n) out[i] = make_float2(a[i].x - b[i].x, a[i].y - b[i].y);
 }
 
 // batched little operator apply, out_r[b*Ns + k] = sum_j sum_l A[b][j][k][l]
@@ -713,8 +817,8 @@ lqcd_status little_apply_b(lqcd_ctx *c, const double2 *cv, double2 *out, int nrh
         float2 *cf;
         LQCD_TRY(coarse_f32(c, N * nrhs, &cf));
         k_to_float2<<<div_up(N * nrhs, 256), 256, 0, c->stream>>>(N * nrhs, cv, cf);
-        k_little_apply_b32<<<d->B.nblk, 32 * d->Ns, 0, c->stream>>>(d->B.nblk, d->Ns, N, nrhs, d->nbr, d->Aint32, cf,
-                                                                    out);
+        k_little_apply_b32<double2><<<d->B.nblk, 32 * d->Ns, 0, c->stream>>>(d->B.nblk, d->Ns, N, nrhs, d->nbr,
+                                                                             d->Aint32, cf, out);
         c->n_kernel_launches++;
     } else
         k_little_apply_b<<<d->B.nblk, 32 * d->Ns, 0, c->stream>>>(d->B.nblk, d->Ns, N, nrhs, d->nbr, d->Aint, cv, out);
@@ -732,7 +836,8 @@ lqcd_status block_jacobi(lqcd_ctx *c, const double2 *in, double2 *out, int nrhs)
         float2 *cf;
         LQCD_TRY(coarse_f32(c, N * nrhs, &cf));
         k_to_float2<<<div_up(N * nrhs, 256), 256, 0, c->stream>>>(N * nrhs, in, cf);
-        k_block_jacobi32<<<d->B.nblk, 32 * d->Ns, 0, c->stream>>>(d->B.nblk, d->Ns, N, nrhs, d->Dinv32, cf, out);
+        k_block_jacobi32<double2><<<d->B.nblk, 32 * d->Ns, 0, c->stream>>>(d->B.nblk, d->Ns, N, nrhs, d->Dinv32, cf,
+                                                                           out);
         c->n_kernel_launches++;
     } else
         k_block_jacobi<<<d->B.nblk, 32 * d->Ns, 0, c->stream>>>(d->B.nblk, d->Ns, N, nrhs, d->Dinv, in, out);
@@ -843,10 +948,14 @@ __global__ void k_c_restart(int nrhs, CoarseScal *s, int *n_active)
 // host; after each cycle the host reads the number of unconverged right-hand
 // sides (one synchronisation per cycle).  A right-hand side that converges
 // inside a cycle gets zero updates for the rest of it.
+lqcd_status coarse_gcr32(lqcd_ctx *c, const double2 *b, double2 *x, int nrhs, double tol, int nkv, int nmx,
+                         int *iters);
+
 lqcd_status coarse_gcr(lqcd_ctx *c, const double2 *b, double2 *x, int nrhs, double tol, int nkv, int nmx,
                        int *iters)
 {
     DflState *d = c->dfl;
+    if (d->Aint32) return coarse_gcr32(c, b, x, nrhs, tol, nkv, nmx, iters);
     const long N = (long)d->B.nblk * d->Ns;
     const long n2 = 2 * N;
     if (nkv < 1 || nkv > CG_K || nrhs > CG_R || nrhs * nkv > 2048)
@@ -901,6 +1010,107 @@ lqcd_status coarse_gcr(lqcd_ctx *c, const double2 *b, double2 *x, int nrhs, doub
         LQCD_CUDA_CHECK(c, cudaStreamSynchronize(c->stream));
         active = *n_active_host;
     }
+    d->coarse_iters += it;
+    d->coarse_solves += 1;
+    if (iters) *iters = it;
+    return active > 0 ? LQCD_ERR_NOT_CONVERGED : LQCD_OK;
+}
+
+// The same GCR with the FP32 little operator: coarse vectors, operator
+// applications and Gram-Schmidt in float (FP64 scalars and fixed-order FP64
+// sums of the per-CTA partial dots).  The coarse solve only needs to reach
+// coarse_tol (>= 1e-6 with the FP32 operator); the outer GCR stays FP64.
+lqcd_status coarse_gcr32(lqcd_ctx *c, const double2 *b, double2 *x, int nrhs, double tol, int nkv, int nmx,
+                         int *iters)
+{
+    DflState *d = c->dfl;
+    const long N = (long)d->B.nblk * d->Ns;
+    if (nkv < 1 || nkv > CG_K || nrhs > CG_R || nrhs * nkv > 2048)
+        return set_err(c, LQCD_ERR_ARG, "coarse nkv=%d nrhs=%d", nkv, nrhs);
+    const long bN = nrhs * N;
+    void *buf;
+    const size_t vec_bytes = (size_t)(2 * nkv + 4) * bN * sizeof(float2);
+    LQCD_TRY(ws_get(c, WS_COARSE, vec_bytes + sizeof(CoarseScal) + 256, &buf));
+    float2 *P = (float2 *)buf, *Q = P + nkv * bN, *rho = Q + nkv * bN, *w = rho + bN, *xf = w + bN, *bf = xf + bN;
+    CoarseScal *S = (CoarseScal *)((char *)buf + ((vec_bytes + 255) / 256) * 256);
+    int *n_active_dev = (int *)c->red_out;
+    int *n_active_host = (int *)c->red_host;
+    double2 *partial = (double2 *)c->red;
+    const int nb = std::max(1, std::min<int>(std::max(8, 4 * 152 / nrhs), (int)((N + 255) / 256)));
+    const int ga = std::max(1, std::min<int>(4 * 152 / std::max(1, nrhs), (int)((N + 255) / 256)));
+    auto dots = [&](const float2 *A, long sa, const float2 *B, int k, double2 *out) -> lqcd_status {
+        for (int k0 = 0; k0 < k; k0 += FDOT_K) {
+            const int kn = std::min(FDOT_K, k - k0);
+            k_fdot_partial<<<dim3(nb, nrhs), 256, 0, c->stream>>>(N, A, sa, N, B, N, k0, kn, partial);
+            c->n_kernel_launches++;
+        }
+        k_fdot_final<<<dim3(k, nrhs), 128, 0, c->stream>>>(nb, k, partial, out);
+        c->n_kernel_launches++;
+        LQCD_LAUNCH_CHECK(c);
+        return LQCD_OK;
+    };
+    auto axpy = [&](int k, const double2 *cf, const float2 *X, long sa, float2 *y, float sign) -> lqcd_status {
+        k_fmulti_axpy<<<dim3(ga, nrhs), 256, 0, c->stream>>>(N, k, cf, X, sa, N, y, N, sign);
+        c->n_kernel_launches++;
+        LQCD_LAUNCH_CHECK(c);
+        return LQCD_OK;
+    };
+    auto jacobi = [&](const float2 *in, float2 *out) {
+        k_block_jacobi32<float2><<<d->B.nblk, 32 * d->Ns, 0, c->stream>>>(d->B.nblk, d->Ns, N, nrhs, d->Dinv32, in,
+                                                                          out);
+        c->n_kernel_launches++;
+    };
+    auto apply = [&](const float2 *in, float2 *out) {
+        k_little_apply_b32<float2><<<d->B.nblk, 32 * d->Ns, 0, c->stream>>>(d->B.nblk, d->Ns, N, nrhs, d->nbr,
+                                                                            d->Aint32, in, out);
+        c->n_kernel_launches++;
+    };
+    const int gn = div_up(bN, 256);
+    k_to_float2<<<gn, 256, 0, c->stream>>>(bN, b, bf);
+    c->n_kernel_launches++;
+    LQCD_CUDA_CHECK(c, cudaMemsetAsync(xf, 0, bN * sizeof(float2), c->stream));
+    LQCD_CUDA_CHECK(c, cudaMemcpyAsync(rho, bf, bN * sizeof(float2), cudaMemcpyDeviceToDevice, c->stream));
+    LQCD_TRY(dots(bf, 0, bf, 1, S->dots));
+    k_c_init<<<1, CG_R, 0, c->stream>>>(nrhs, tol * tol, S);
+    c->n_kernel_launches++;
+    int it = 0, active = nrhs;
+    while (active > 0 && it < nmx) {
+        int nk = 0;
+        for (int k = 0; k < nkv && it < nmx; k++) {
+            float2 *pk = P + k * bN, *qk = Q + k * bN;
+            jacobi(rho, pk);
+            apply(pk, qk);
+            if (k > 0) {
+                LQCD_TRY(dots(Q, bN, qk, k, S->dots));
+                k_c_gs<<<nrhs, k, 0, c->stream>>>(nrhs, k, S);
+                c->n_kernel_launches++;
+                LQCD_TRY(axpy(k, S->dots, Q, bN, qk, -1.f));
+            }
+            LQCD_TRY(dots(qk, rho - qk, qk, 2, S->dots));   // |q_k|^2 and <rho, q_k>
+            k_c_norm<<<1, CG_R, 0, c->stream>>>(nrhs, k, S);
+            c->n_kernel_launches++;
+            LQCD_TRY(axpy(1, S->cfR, qk, 0, rho, -1.f));
+            LQCD_TRY(axpy(1, S->cfS, qk, 0, qk, 1.f));
+            it++;
+            nk = k + 1;
+        }
+        k_c_backsub<<<1, CG_R, 0, c->stream>>>(nrhs, nk, S);
+        c->n_kernel_launches++;
+        LQCD_TRY(axpy(nk, S->alpha, P, bN, xf, 1.f));
+        apply(xf, w);
+        k_fsub<<<gn, 256, 0, c->stream>>>(bN, bf, w, rho);
+        c->n_kernel_launches++;
+        LQCD_TRY(dots(rho, 0, rho, 1, S->dots));
+        k_c_restart<<<1, CG_R, 0, c->stream>>>(nrhs, S, n_active_dev);
+        c->n_kernel_launches++;
+        LQCD_LAUNCH_CHECK(c);
+        LQCD_CUDA_CHECK(c, cudaMemcpyAsync(n_active_host, n_active_dev, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+        LQCD_CUDA_CHECK(c, cudaStreamSynchronize(c->stream));
+        active = *n_active_host;
+    }
+    k_to_double2<<<gn, 256, 0, c->stream>>>(bN, xf, x);
+    c->n_kernel_launches++;
+    LQCD_LAUNCH_CHECK(c);
     d->coarse_iters += it;
     d->coarse_solves += 1;
     if (iters) *iters = it;
@@ -966,6 +1176,8 @@ lqcd_status lqcd_dfl_build(lqcd_ctx *c, const lqcd_dfl_params *p, const double *
     if (!c->have_clover) return set_err(c, LQCD_ERR_STATE, "clover term not built");
     if (p->Ns < 1 || p->Ns > NS_MAX) return set_err(c, LQCD_ERR_ARG, "Ns=%d (1..%d)", p->Ns, NS_MAX);
     if (p->prec != LQCD_F64 && p->prec != LQCD_F32) return set_err(c, LQCD_ERR_ARG, "subspace precision");
+    if (p->coarse_prec == LQCD_F32 && !(p->coarse_tol >= 1e-6))
+        return set_err(c, LQCD_ERR_ARG, "coarse_tol %g below 1e-6 with the FP32 little operator", p->coarse_tol);
     DBlk B;
     B.vol = 1;
     B.nblk = 1;

@@ -109,3 +109,33 @@ def test_dfl_requires_subspace_and_clover():
     assert st == 9
     with pytest.raises(lqcd.LqcdError):
         P.ctx.dfl_build(to_gpu(_v0(P, 2)), bs=(3, 4, 4, 4))
+
+
+def test_fp32_coarse_solve():
+    """FP32 little-Dirac solve (operator, Krylov vectors and Gram-Schmidt in
+    float): the residual under the FP64 little operator of the oracle reaches
+    coarse_tol, one and several right-hand sides; tolerances an FP32 solve
+    cannot reach are refused at build time."""
+    P = Pair((8, 8, 8, 8), kappa=0.1355)
+    v0 = _v0(P, NS)
+    with pytest.raises(lqcd.LqcdError):
+        P.ctx.dfl_build(to_gpu(v0), bs=(4, 4, 4, 4), ninv=2, ncy=2, nmr=4, prec=lqcd.F64, coarse_tol=1e-8,
+                        coarse_prec=lqcd.F32)
+    P.ctx.dfl_build(to_gpu(v0), bs=(4, 4, 4, 4), ninv=2, ncy=2, nmr=4, prec=lqcd.F64, coarse_tol=1e-5,
+                    coarse_prec=lqcd.F32)
+    assert P.o.dfl_build(v0, bs=(4, 4, 4, 4), ninv=2, ncy=2, nmr=4) == 0
+    A = P.o.dfl_little()
+    n = P.ctx.nblk * P.ctx.Ns
+    cc = np.ascontiguousarray(synth.gaussian_spinor(P.ctx.nblk * P.ctx.Ns, 34).reshape(-1)[:n])
+    x, it = P.ctx.dfl_coarse_solve(to_gpu(cc))
+    x = x.cpu().numpy().reshape(-1)
+    assert np.linalg.norm(A @ x - cc) <= 2e-5 * np.linalg.norm(cc)
+    assert it > 0
+    # several right-hand sides go through the coarse solve together inside the
+    # deflated solve; every one reaches the FP64 true residual
+    eta = np.stack([synth.gaussian_spinor(P.Vh, 40 + k) for k in range(3)])
+    psi, info, st = P.ctx.solve_dhat(to_gpu(eta), solver=lqcd.SOLVER_DFL_SAP_GCR, tol=1e-10, sap_prec=lqcd.F32,
+                                     inner=lqcd.F32)
+    assert st == 0
+    for k in range(3):
+        assert util.relerr(P.o.Dhat(psi[k].cpu().numpy()), eta[k]) <= 1e-10
