@@ -6,6 +6,8 @@
 #include <type_traits>
 
 #include "lqcd_f16s.cuh"
+#include <cstdlib>
+
 #include "lqcd_internal.cuh"
 
 lqcd_status set_err(lqcd_ctx *c, lqcd_status s, const char *fmt, ...)
@@ -297,6 +299,7 @@ lqcd_status lqcd_create(const lqcd_geom *geom, void *stream, lqcd_ctx **out)
     c->g.L3h = L[3] / 2;
     c->g.bc_t = geom->antiperiodic_t ? -1 : 1;
     c->stream = (cudaStream_t)stream;
+    c->prof_on = getenv("LQCD_PROFILE") && getenv("LQCD_PROFILE")[0] == '1';
     if (cudaMalloc(&c->red, 4096 * 2 * 64 * sizeof(double)) != cudaSuccess ||
         cudaMalloc(&c->red_out, 4 * 2048 * sizeof(double)) != cudaSuccess ||
         cudaMallocHost(&c->red_host, 4 * 2048 * sizeof(double)) != cudaSuccess) {

@@ -302,13 +302,18 @@ __global__ void k_little_build(Geom g, DBlk B, const T *phi, int Ns, long fstrid
     }
 }
 
-// c[b*Ns + k] = <phi_k|_b, in>  (in: native F64 full field)
+// c_r[b*Ns + k] = <phi_k|_b, in_r>  (in_r: native F64 full fields, stride in_rs;
+// c_r stride c_rs).  The nrhs CTAs of one block are consecutive, so the block's
+// subspace vectors are read from DRAM once and from L2 by the other fields.
 template <class T>
-__global__ void k_project(Geom g, DBlk B, const T *phi, int Ns, long fstride, const double2 *in, double2 *c)
+__global__ void k_project(Geom g, DBlk B, const T *phi, int Ns, long fstride, const double2 *in, double2 *c,
+                          int nrhs, long in_rs, long c_rs)
 {
     extern __shared__ double sh[];
     double *res = sh + 2 * RCHUNK * 32;
-    int b = blockIdx.x, t = threadIdx.x;
+    const int b = blockIdx.x / nrhs, t = threadIdx.x;
+    in += (blockIdx.x % nrhs) * in_rs;
+    c += (blockIdx.x % nrhs) * c_rs;
     BSite s;
     bsite(g, B, b, t, s);
     C w[12];
@@ -354,11 +359,15 @@ __global__ void k_project(Geom g, DBlk B, const T *phi, int Ns, long fstride, co
     }
 }
 
-// out(x) = sum_k c[b(x)*Ns + k] phi_k(x)  (out: native F64 full field)
+// out_r(x) = sum_k c_r[b(x)*Ns + k] phi_k(x)  (out_r: native F64 full fields,
+// stride out_rs; c_r stride c_rs; CTA order as in k_project)
 template <class T>
-__global__ void k_expand(Geom g, DBlk B, const T *phi, int Ns, long fstride, const double2 *c, double2 *out)
+__global__ void k_expand(Geom g, DBlk B, const T *phi, int Ns, long fstride, const double2 *c, double2 *out,
+                         int nrhs, long c_rs, long out_rs)
 {
-    int b = blockIdx.x, t = threadIdx.x;
+    const int b = blockIdx.x / nrhs, t = threadIdx.x;
+    c += (blockIdx.x % nrhs) * c_rs;
+    out += (blockIdx.x % nrhs) * out_rs;
     BSite s;
     bsite(g, B, b, t, s);
     const long hs = fstride / 2;
@@ -522,17 +531,25 @@ __global__ void k_block_jacobi(int nblk, int Ns, long N, int nrhs, const double2
 }
 
 // FP32 operator variants: matrices stored as float2, the input vector given in
-// float (converted once per application by k_to_float2), products and the row
-// sums in float; FP64 vectors out (the coarse GCR itself stays FP64)
-__device__ __forceinline__ void warp_sum2f(float &re, float &im)
-{
-    for (int o = 16; o > 0; o >>= 1) {
-        re += __shfl_down_sync(0xffffffffu, re, o);
-        im += __shfl_down_sync(0xffffffffu, im, o);
-    }
-}
+// float, products and the row sums in float; the output in double (FP64
+// coarse GCR, input converted once per application by k_to_float2) or in
+// float (FP32 coarse GCR)
 __device__ __forceinline__ void put2(double2 *p, float re, float im) { *p = make_double2(re, im); }
 __device__ __forceinline__ void put2(float2 *p, float re, float im) { *p = make_float2(re, im); }
+// CRB right-hand sides per pass: their loads and warp reductions are
+// independent and overlap (each one's arithmetic order is unchanged)
+constexpr int CRB = 4;
+template <int R>
+__device__ __forceinline__ void warp_sum2f_n(float (&re)[R], float (&im)[R])
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int q = 0; q < R; q++) {
+            re[q] += __shfl_down_sync(0xffffffffu, re[q], o);
+            im[q] += __shfl_down_sync(0xffffffffu, im[q], o);
+        }
+}
 template <class OT>
 __global__ void k_block_jacobi32(int nblk, int Ns, long N, int nrhs, const float2 *__restrict__ Dinv,
                                  const float2 *__restrict__ in, OT *out)
@@ -540,11 +557,19 @@ __global__ void k_block_jacobi32(int nblk, int Ns, long N, int nrhs, const float
     const int b = blockIdx.x, k = threadIdx.x >> 5, l = threadIdx.x & 31;
     if (b >= nblk || k >= Ns) return;
     float2 a = l < Ns ? Dinv[((size_t)b * Ns + k) * Ns + l] : make_float2(0, 0);
-    for (int r = 0; r < nrhs; r++) {
-        const float2 y = l < Ns ? in[r * N + (long)b * Ns + l] : make_float2(0, 0);
-        float re = a.x * y.x - a.y * y.y, im = a.x * y.y + a.y * y.x;
-        warp_sum2f(re, im);
-        if (l == 0) put2(out + r * N + (long)b * Ns + k, re, im);
+    for (int r0 = 0; r0 < nrhs; r0 += CRB) {
+        float re[CRB], im[CRB];
+#pragma unroll
+        for (int q = 0; q < CRB; q++) {
+            const float2 y = (l < Ns && r0 + q < nrhs) ? in[(r0 + q) * N + (long)b * Ns + l] : make_float2(0, 0);
+            re[q] = a.x * y.x - a.y * y.y;
+            im[q] = a.x * y.y + a.y * y.x;
+        }
+        warp_sum2f_n<CRB>(re, im);
+        if (l == 0)
+#pragma unroll
+            for (int q = 0; q < CRB; q++)
+                if (r0 + q < nrhs) put2(out + (r0 + q) * N + (long)b * Ns + k, re[q], im[q]);
     }
 }
 template <class OT>
@@ -560,19 +585,26 @@ __global__ void k_little_apply_b32(int nblk, int Ns, long N, int nrhs, const int
         nb[j] = nbr[b * 9 + j];
         a[j] = l < Ns ? Aint[(((long)b * 9 + j) * Ns + k) * Ns + l] : make_float2(0, 0);
     }
-    for (int r = 0; r < nrhs; r++) {
-        float re = 0, im = 0;
-        if (l < Ns) {
-            const float2 *cr = c + r * N + l;
+    for (int r0 = 0; r0 < nrhs; r0 += CRB) {
+        float re[CRB], im[CRB];
 #pragma unroll
-            for (int j = 0; j < 9; j++) {
-                const float2 y = cr[(long)nb[j] * Ns];
-                re += a[j].x * y.x - a[j].y * y.y;
-                im += a[j].x * y.y + a[j].y * y.x;
+        for (int q = 0; q < CRB; q++) {
+            re[q] = im[q] = 0;
+            if (l < Ns && r0 + q < nrhs) {
+                const float2 *cr = c + (r0 + q) * N + l;
+#pragma unroll
+                for (int j = 0; j < 9; j++) {
+                    const float2 y = cr[(long)nb[j] * Ns];
+                    re[q] += a[j].x * y.x - a[j].y * y.y;
+                    im[q] += a[j].x * y.y + a[j].y * y.x;
+                }
             }
         }
-        warp_sum2f(re, im);
-        if (l == 0) put2(out + r * N + (long)b * Ns + k, re, im);
+        warp_sum2f_n<CRB>(re, im);
+        if (l == 0)
+#pragma unroll
+            for (int q = 0; q < CRB; q++)
+                if (r0 + q < nrhs) put2(out + (r0 + q) * N + (long)b * Ns + k, re[q], im[q]);
     }
 }
 __global__ void k_to_float2(long n, const double2 *in, float2 *out)
@@ -771,34 +803,40 @@ lqcd_status scale_native(lqcd_ctx *c, lqcd_prec p, void *x, long nhalf, double s
 long field_elems(const lqcd_ctx *c, lqcd_prec p) { return 2 * (p == LQCD_F64 ? 12 : 6) * (long)c->g.Vh; }
 
 template <class T>
-lqcd_status launch_project(lqcd_ctx *c, const double2 *in, double2 *cv)
+lqcd_status launch_project(lqcd_ctx *c, const double2 *in, double2 *cv, int nrhs)
 {
     DflState *d = c->dfl;
     size_t sm = (2 * RCHUNK * 32 + 2 * RCHUNK) * sizeof(double);
-    k_project<T><<<d->B.nblk, d->B.vol, sm, c->stream>>>(c->g, d->B, (const T *)d->phi, d->Ns,
-                                                         field_elems(c, d->prec), in, cv);
+    const long N = (long)d->B.nblk * d->Ns, nf = 24 * (long)c->g.Vh;
+    k_project<T><<<d->B.nblk * nrhs, d->B.vol, sm, c->stream>>>(c->g, d->B, (const T *)d->phi, d->Ns,
+                                                                field_elems(c, d->prec), in, cv, nrhs, nf, N);
     c->n_kernel_launches++;
     LQCD_LAUNCH_CHECK(c);
     return LQCD_OK;
 }
 template <class T>
-lqcd_status launch_expand(lqcd_ctx *c, const double2 *cv, double2 *out)
+lqcd_status launch_expand(lqcd_ctx *c, const double2 *cv, double2 *out, int nrhs)
 {
     DflState *d = c->dfl;
-    k_expand<T><<<d->B.nblk, d->B.vol, 0, c->stream>>>(c->g, d->B, (const T *)d->phi, d->Ns,
-                                                       field_elems(c, d->prec), cv, out);
+    const long N = (long)d->B.nblk * d->Ns, nf = 24 * (long)c->g.Vh;
+    k_expand<T><<<d->B.nblk * nrhs, d->B.vol, 0, c->stream>>>(c->g, d->B, (const T *)d->phi, d->Ns,
+                                                              field_elems(c, d->prec), cv, out, nrhs, N, nf);
     c->n_kernel_launches++;
     LQCD_LAUNCH_CHECK(c);
     return LQCD_OK;
 }
 
-lqcd_status project(lqcd_ctx *c, const double2 *in, double2 *cv)
+// nrhs fields: in / out native F64 full fields one after the other, coarse
+// vectors of nblk*Ns entries one after the other
+lqcd_status project(lqcd_ctx *c, const double2 *in, double2 *cv, int nrhs = 1)
 {
-    return c->dfl->prec == LQCD_F64 ? launch_project<double2>(c, in, cv) : launch_project<float4>(c, in, cv);
+    return c->dfl->prec == LQCD_F64 ? launch_project<double2>(c, in, cv, nrhs)
+                                    : launch_project<float4>(c, in, cv, nrhs);
 }
-lqcd_status expand(lqcd_ctx *c, const double2 *cv, double2 *out)
+lqcd_status expand(lqcd_ctx *c, const double2 *cv, double2 *out, int nrhs = 1)
 {
-    return c->dfl->prec == LQCD_F64 ? launch_expand<double2>(c, cv, out) : launch_expand<float4>(c, cv, out);
+    return c->dfl->prec == LQCD_F64 ? launch_expand<double2>(c, cv, out, nrhs)
+                                    : launch_expand<float4>(c, cv, out, nrhs);
 }
 // float copy of coarse vectors for the FP32 operator (grown on demand)
 lqcd_status coarse_f32(lqcd_ctx *c, long n, float2 **out)
@@ -1142,12 +1180,16 @@ lqcd_status dfl_precond_native(lqcd_ctx *c, const lqcd_sap_params *sp, const dou
     void *buf;
     LQCD_TRY(ws_get(c, WS_DFL, (2 * N * nrhs + 2 * nf * nrhs) * sizeof(double2), &buf));
     double2 *cv = (double2 *)buf, *ev = cv + N * nrhs, *u = ev + N * nrhs, *w = u + nf * nrhs;
+    ProfClock pc(c);
     // u_r = Pi A^-1 Pi^dag rho_r, the coarse solves of all right-hand sides together
-    for (int r = 0; r < nrhs; r++) LQCD_TRY(project(c, rho + r * nf, cv + r * N));
+    LQCD_TRY(project(c, rho, cv, nrhs));
+    pc.lap(0);
     int it = 0;
     lqcd_status st = coarse_gcr(c, cv, ev, nrhs, d->params.coarse_tol, d->params.coarse_nkv, d->params.coarse_nmx, &it);
     if (st != LQCD_OK && st != LQCD_ERR_NOT_CONVERGED) return set_err(c, st, "coarse solve failed (%d)", (int)st);
-    for (int r = 0; r < nrhs; r++) LQCD_TRY(expand(c, ev + r * N, u + r * nf));
+    pc.lap(1);
+    LQCD_TRY(expand(c, ev, u, nrhs));
+    pc.lap(2);
     // w = rho - D u  (D in the SAP precision)
     if (sp->prec == LQCD_F64) {
         LQCD_TRY(dirac_D(c, LQCD_F64, u, w, nrhs));
@@ -1161,11 +1203,15 @@ lqcd_status dfl_precond_native(lqcd_ctx *c, const lqcd_sap_params *sp, const dou
         LQCD_TRY(convert_native(c, sp->prec, LQCD_F64, b2, w, 2 * nrhs));
     }
     LQCD_TRY(blas_sub(c, 2 * nf * nrhs, (const double *)rho, (const double *)w, (double *)w));
+    pc.lap(3);
     if (net)
         LQCD_TRY(net_apply_native(c, w, phi, nrhs));
     else
         LQCD_TRY(precond_sap(c, sp, w, phi, nrhs));
-    return blas_axpy(c, 2 * nf * nrhs, 1.0, 0, (const double *)u, (double *)phi);
+    pc.lap(4);
+    LQCD_TRY(blas_axpy(c, 2 * nf * nrhs, 1.0, 0, (const double *)u, (double *)phi));
+    pc.lap(5);
+    return LQCD_OK;
 }
 
 extern "C" {

@@ -8,6 +8,7 @@
 
 #include <cstdint>
 #include <cstdio>
+#include <ctime>
 #include <string>
 #include <vector>
 
@@ -115,6 +116,39 @@ struct lqcd_ctx {
     NetState *net = nullptr;
     ChronoState *chrono = nullptr;
     long n_kernel_launches = 0;
+    // LQCD_PROFILE=1: synchronised wall time of solver phases, reported on
+    // stderr by the GCR (developer instrumentation; off by default)
+    bool prof_on = false;
+    double prof_t[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    double prof_gs_bytes = 0;   // algorithmic bytes of the outer Gram-Schmidt
+    long prof_gs_second = 0;    // second Gram-Schmidt passes taken
+};
+
+// laps of the LQCD_PROFILE clock: lap(i) adds the time since the previous lap
+// (or construction) to c->prof_t[i]; nothing happens when profiling is off
+struct ProfClock {
+    lqcd_ctx *c;
+    double t0 = 0;
+    static double wall()
+    {
+        timespec ts;
+        clock_gettime(CLOCK_MONOTONIC, &ts);
+        return ts.tv_sec + 1e-9 * ts.tv_nsec;
+    }
+    explicit ProfClock(lqcd_ctx *ctx) : c(ctx)
+    {
+        if (!c->prof_on) return;
+        cudaStreamSynchronize(c->stream);
+        t0 = wall();
+    }
+    void lap(int i)
+    {
+        if (!c->prof_on) return;
+        cudaStreamSynchronize(c->stream);
+        const double t = wall();
+        c->prof_t[i] += t - t0;
+        t0 = t;
+    }
 };
 
 // error helpers
@@ -155,6 +189,7 @@ enum {
     WS_NET_FALLBACK,
     WS_HASEN,
     WS_COARSE_F32,
+    WS_PHI64,       // F64 preconditioner output converted into FP32 Krylov vectors
 };
 lqcd_status ws_get(lqcd_ctx *c, int slot, size_t bytes, void **out);
 
@@ -201,6 +236,19 @@ lqcd_status bblas_dot_dev(lqcd_ctx *c, long n2, int nrhs, const double *A, long 
                           int k, double2 *out_dev);
 lqcd_status bblas_multi_axpy_dev(lqcd_ctx *c, long n2, int nrhs, int k, const double2 *coef_dev, const double *X,
                                  long sa, long fa, double *y, long fy, double sign);
+// GCR with FP32 Krylov vectors: x, A, B, X, y are native F32 full fields
+// (float4, strides in float4), rho and psi native F64 full fields (double2,
+// strides in double2); dots land on the host as (re, im) pairs [r][i]
+lqcd_status bdot32(lqcd_ctx *c, long n4, int nrhs, const float4 *A, long sa, long fa, const float4 *B, long fb, int k,
+                   double *host_out);
+lqcd_status bnorm_rdot32(lqcd_ctx *c, int nrhs, const float4 *x, long fx, const double2 *rho, long fr,
+                         double *host_out);   // [r][0] = |x_r|^2, [r][1] = <rho_r, x_r>
+lqcd_status bmulti_axpy32(lqcd_ctx *c, long n4, int nrhs, int k, const double *coef_host, const float4 *X, long sa,
+                          long fa, float4 *y, long fy, double sign);
+lqcd_status brho_update32(lqcd_ctx *c, int nrhs, const double *cR_host, const double *sx_host, float4 *x, long fx,
+                          double2 *rho, long fr);   // rho_r -= cR_r x_r; x_r *= sx_r
+lqcd_status bmulti_axpy_mixed(lqcd_ctx *c, int nrhs, int k, const double *coef_host, const float4 *X, long sa,
+                              long fa, double2 *y, long fy);   // y_r += sum_i c_ri X_ir
 lqcd_status blas_gamma5_native64(lqcd_ctx *c, long nhalf, const double2 *in, double2 *out);
 lqcd_status blas_zero(lqcd_ctx *c, size_t bytes, void *p);
 

@@ -183,9 +183,20 @@ struct PhaseProf {
     }
     ~PhaseProf()
     {
-        if (on)
-            fprintf(stderr, "[lqcd gcr] precond %.4f s, D_inner %.4f s, gram-schmidt %.4f s, restart %.4f s\n", t[0],
-                    t[1], t[2], t[3]);
+        if (!on) return;
+        fprintf(stderr, "[lqcd gcr] precond %.4f s, D_inner %.4f s, gram-schmidt %.4f s, restart %.4f s\n", t[0],
+                t[1], t[2], t[3]);
+        double *p = ctx->prof_t;
+        if (p[0] + p[1] + p[2] + p[3] + p[4] + p[5] > 0)
+            fprintf(stderr,
+                    "[lqcd dfl] project %.4f s, coarse %.4f s, expand %.4f s, D+sub %.4f s, sap %.4f s, "
+                    "axpy %.4f s\n",
+                    p[0], p[1], p[2], p[3], p[4], p[5]);
+        fprintf(stderr, "[lqcd gcr] gram-schmidt %.1f GB, %.0f GB/s, %ld second passes\n", ctx->prof_gs_bytes * 1e-9,
+                t[2] > 0 ? ctx->prof_gs_bytes * 1e-9 / t[2] : 0.0, ctx->prof_gs_second);
+        for (int i = 0; i < 8; i++) p[i] = 0;
+        ctx->prof_gs_bytes = 0;
+        ctx->prof_gs_second = 0;
     }
 };
 
@@ -199,21 +210,137 @@ lqcd_status bnorm2(lqcd_ctx *c, long n2, int nrhs, const double2 *x, std::vector
     return LQCD_OK;
 }
 
+// Krylov-vector storage of the GCR.  Krylov64: phi_k and chi_k native F64
+// full fields.  Krylov32 (inner precision F32): phi_k and chi_k native F32
+// full fields, so D phi_k runs on them directly and the Gram-Schmidt moves
+// half the bytes; rho and psi stay F64, the products with FP32 vectors are
+// formed in float and accumulated in double.
+struct Krylov64 {
+    using T = double2;
+    lqcd_ctx *c;
+    const lqcd_solver_params *sp;
+    int nrhs;
+    long nf;   // elements (double2) per full field
+    long n2;   // doubles per full field
+    Krylov64(lqcd_ctx *ctx, const lqcd_solver_params *p, int n)
+        : c(ctx), sp(p), nrhs(n), nf(24 * (long)ctx->g.Vh), n2(48 * (long)ctx->g.Vh)
+    {
+    }
+    size_t field_bytes() const { return nf * sizeof(T); }
+    lqcd_status precond_with(const lqcd_solver_params *p, const double2 *rho, T *ph)
+    {
+        return precond(c, p, rho, ph, nrhs);
+    }
+    lqcd_status D_inner(const T *ph, T *ch) { return apply_D_inner(c, sp->inner, ph, ch, nrhs); }
+    lqcd_status dots(const T *A, long sa, const T *B, int kk, double *out)
+    {
+        return bblas_dot(c, n2, nrhs, (const double *)A, 2 * sa, n2, (const double *)B, n2, kk, out);
+    }
+    lqcd_status axpy(int k, const double *cf, const T *X, long sa, T *y, double sign)
+    {
+        return bblas_multi_axpy(c, n2, nrhs, k, cf, (const double *)X, 2 * sa, n2, (double *)y, n2, sign);
+    }
+    // |chi|^2 and <rho, chi> (the family {chi, rho} against chi)
+    lqcd_status norm_rdot(const T *ch, const double2 *rho, double *out)
+    {
+        return bblas_dot(c, n2, nrhs, (const double *)ch, 2 * (rho - ch), n2, (const double *)ch, n2, 2, out);
+    }
+    // rho -= cR chi; chi *= s
+    lqcd_status rho_update(const double *cR, const double *s, T *ch, double2 *rho)
+    {
+        std::vector<double> cs(2 * nrhs);
+        for (int r = 0; r < nrhs; r++) {
+            cs[2 * r] = s[r] - 1.0;
+            cs[2 * r + 1] = 0.0;
+        }
+        LQCD_TRY(bblas_multi_axpy(c, n2, nrhs, 1, cR, (const double *)ch, 0, n2, (double *)rho, n2, -1.0));
+        return bblas_multi_axpy(c, n2, nrhs, 1, cs.data(), (const double *)ch, 0, n2, (double *)ch, n2, 1.0);
+    }
+    lqcd_status psi_update(int nk, const double *cf, const T *phi, long sa, double2 *psi)
+    {
+        return bblas_multi_axpy(c, n2, nrhs, nk, cf, (const double *)phi, 2 * sa, n2, (double *)psi, n2, 1.0);
+    }
+    double final_fields() const { return 7.0; }   // F64-field transfers of norm_rdot + rho_update
+};
+
+struct Krylov32 {
+    using T = float4;
+    lqcd_ctx *c;
+    const lqcd_solver_params *sp;
+    int nrhs;
+    long nf;    // elements (float4) per full F32 field
+    long nf64;  // double2 per full F64 field
+    Krylov32(lqcd_ctx *ctx, const lqcd_solver_params *p, int n)
+        : c(ctx), sp(p), nrhs(n), nf(12 * (long)ctx->g.Vh), nf64(24 * (long)ctx->g.Vh)
+    {
+    }
+    size_t field_bytes() const { return nf * sizeof(T); }
+    // the preconditioner's output in F32: SAP in F32 writes it directly, other
+    // forms are converted from their own output precision
+    lqcd_status precond_with(const lqcd_solver_params *p, const double2 *rho, T *ph)
+    {
+        const lqcd_sap_params &sap = p->sap;
+        if (p->solver == LQCD_SOLVER_SAP_GCR && sap.prec != LQCD_F64) {
+            void *a;
+            const size_t fb = 2 * native_half_bytes(c, sap.prec) * nrhs;
+            LQCD_TRY(ws_get(c, WS_SAP_IN, fb, &a));
+            LQCD_TRY(convert_native(c, LQCD_F64, sap.prec, rho, a, 2 * nrhs));
+            if (sap.prec == LQCD_F32) return sap_apply(c, &sap, a, ph, nrhs);
+            void *b;
+            LQCD_TRY(ws_get(c, WS_SAP_PSI, fb, &b));
+            LQCD_TRY(sap_apply(c, &sap, a, b, nrhs));
+            return convert_native(c, sap.prec, LQCD_F32, b, ph, 2 * nrhs);
+        }
+        void *t;
+        LQCD_TRY(ws_get(c, WS_PHI64, (size_t)nf64 * nrhs * sizeof(double2), &t));
+        LQCD_TRY(precond(c, p, rho, (double2 *)t, nrhs));
+        return convert_native(c, LQCD_F64, LQCD_F32, t, ph, 2 * nrhs);
+    }
+    lqcd_status D_inner(const T *ph, T *ch) { return dirac_D(c, LQCD_F32, ph, ch, nrhs); }
+    lqcd_status dots(const T *A, long sa, const T *B, int kk, double *out)
+    {
+        return bdot32(c, nf, nrhs, A, sa, nf, B, nf, kk, out);
+    }
+    lqcd_status axpy(int k, const double *cf, const T *X, long sa, T *y, double sign)
+    {
+        return bmulti_axpy32(c, nf, nrhs, k, cf, X, sa, nf, y, nf, sign);
+    }
+    lqcd_status norm_rdot(const T *ch, const double2 *rho, double *out)
+    {
+        return bnorm_rdot32(c, nrhs, ch, nf, rho, nf64, out);
+    }
+    lqcd_status rho_update(const double *cR, const double *s, T *ch, double2 *rho)
+    {
+        return brho_update32(c, nrhs, cR, s, ch, nf, rho, nf64);
+    }
+    lqcd_status psi_update(int nk, const double *cf, const T *phi, long sa, double2 *psi)
+    {
+        return bmulti_axpy_mixed(c, nrhs, nk, cf, phi, sa, nf, psi, nf64);
+    }
+    double final_fields() const { return 4.5; }
+};
+
 // flexible GCR on D psi_r = eta_r, warm start from psi; tol per rhs
-lqcd_status gcr_native(lqcd_ctx *c, const lqcd_solver_params *sp, const std::vector<double> &tol,
-                       const double2 *eta, double2 *psi, int nrhs, int nmx, GcrState &S)
+template <class KV>
+lqcd_status gcr_impl(lqcd_ctx *c, const lqcd_solver_params *sp, const std::vector<double> &tol, const double2 *eta,
+                     double2 *psi, int nrhs, int nmx, GcrState &S)
 {
+    using T = typename KV::T;
+    KV kv(c, sp, nrhs);
     const long Vh = c->g.Vh;
-    const long n2 = 48 * Vh;   // doubles in one full field
-    const long nf = 24 * Vh;   // double2 in one full field
+    const long n2 = 48 * Vh;   // doubles in one full F64 field
+    const long nf = kv.nf;     // Krylov elements per field
     const int nkv = sp->nkv;
     if (nkv < 1 || nkv > 64) return set_err(c, LQCD_ERR_ARG, "nkv=%d", nkv);
-    if (nrhs * nkv > 2048) return set_err(c, LQCD_ERR_ARG, "nrhs*nkv too large");
-    const long bf = nrhs * nf;   // double2 per batch of fields
+    if (nrhs * nkv > 1024 || nrhs > 64) return set_err(c, LQCD_ERR_ARG, "nrhs=%d with nkv=%d too large", nrhs, nkv);
+    const long bf = nrhs * nf;   // Krylov elements per batch of fields
+    const size_t bf64 = (size_t)nrhs * 24 * Vh;   // double2 per batch of F64 fields
     void *buf;
-    LQCD_TRY(ws_get(c, WS_SOLVER, (size_t)(2 * nkv + 2) * bf * sizeof(double2), &buf));
-    double2 *phi = (double2 *)buf, *chi = phi + nkv * bf, *rho = chi + nkv * bf, *w = rho + bf;
+    LQCD_TRY(ws_get(c, WS_SOLVER, 2 * nkv * bf * sizeof(T) + 2 * bf64 * sizeof(double2), &buf));
+    T *phi = (T *)buf, *chi = phi + nkv * bf;
+    double2 *rho = (double2 *)(chi + nkv * bf), *w = rho + bf64;
     const double inner_gain = sp->inner == LQCD_F64 ? 0.0 : 1e-5;
+    const double gs_field = (double)bf * sizeof(T);
     PhaseProf prof(c);
     std::vector<double> eta2, rn2, eta_n(nrhs), res(nrhs), cycle_start(nrhs);
     LQCD_TRY(bnorm2(c, n2, nrhs, eta, eta2));
@@ -243,15 +370,15 @@ lqcd_status gcr_native(lqcd_ctx *c, const lqcd_solver_params *sp, const std::vec
         std::vector<char> done(nrhs, 0);
         for (int r = 0; r < nrhs; r++) cycle_start[r] = res[r];
         for (int k = 0; k < nkv && it < nmx; k++) {
-            double2 *ph = phi + k * bf, *ch = chi + k * bf;
+            T *ph = phi + k * bf, *ch = chi + k * bf;
             prof.start();
-            LQCD_TRY(precond(c, sp, rho, ph, nrhs));
+            LQCD_TRY(kv.precond_with(sp, rho, ph));
             prof.stop(0);
             // chi_k = D phi_k, orthogonalised against chi_0..chi_{k-1}; leaves |chi_k|^2
             // and <rho, chi_k> in dots
             auto orth = [&]() -> lqcd_status {
                 prof.start();
-                LQCD_TRY(apply_D_inner(c, sp->inner, ph, ch, nrhs));
+                LQCD_TRY(kv.D_inner(ph, ch));
                 prof.stop(1);
                 prof.start();
                 for (int r = 0; r < nrhs; r++)
@@ -261,8 +388,7 @@ lqcd_status gcr_native(lqcd_ctx *c, const lqcd_solver_params *sp, const std::vec
                 // first pass reduces chi_0..chi_k against chi_k, which also gives |chi_k|^2.
                 for (int pass = 0; pass < 2 && k > 0; pass++) {
                     const int kk = pass == 0 ? k + 1 : k;
-                    LQCD_TRY(bblas_dot(c, n2, nrhs, (const double *)chi, 2 * bf, n2, (const double *)ch, n2, kk,
-                                       dots.data()));
+                    LQCD_TRY(kv.dots(chi, bf, ch, kk, dots.data()));
                     bool again = false;
                     std::vector<double> cf(2 * (size_t)nrhs * k);
                     for (int r = 0; r < nrhs; r++) {
@@ -277,13 +403,13 @@ lqcd_status gcr_native(lqcd_ctx *c, const lqcd_solver_params *sp, const std::vec
                         }
                         if (pass == 0 && active[r] && removed > 0.5 * dots[2 * (r * kk + k)]) again = true;
                     }
-                    LQCD_TRY(bblas_multi_axpy(c, n2, nrhs, k, cf.data(), (const double *)chi, 2 * bf, n2,
-                                              (double *)ch, n2, -1.0));
+                    LQCD_TRY(kv.axpy(k, cf.data(), chi, bf, ch, -1.0));
+                    // bytes: the dot reads kk + 1 fields, the update k + 1 and writes one
+                    c->prof_gs_bytes += (kk + 1 + k + 2) * gs_field;
                     if (!again) break;
+                    c->prof_gs_second += pass == 0;
                 }
-                // |chi_k|^2 and <rho, chi_k> in one reduction (family {chi_k, rho} against chi_k)
-                return bblas_dot(c, n2, nrhs, (const double *)ch, 2 * (rho - ch), n2, (const double *)ch, n2, 2,
-                                 dots.data());
+                return kv.norm_rdot(ch, rho, dots.data());
             };
             LQCD_TRY(orth());
             if (sp->solver == LQCD_SOLVER_NET_GCR || sp->solver == LQCD_SOLVER_DFL_NET_GCR) {
@@ -300,20 +426,20 @@ lqcd_status gcr_native(lqcd_ctx *c, const lqcd_solver_params *sp, const std::vec
                 }
                 if (!reject.empty()) {
                     void *fb;
-                    LQCD_TRY(ws_get(c, WS_NET_FALLBACK, (size_t)bf * sizeof(double2), &fb));
+                    LQCD_TRY(ws_get(c, WS_NET_FALLBACK, (size_t)bf * sizeof(T), &fb));
                     lqcd_solver_params sap_only = *sp;
                     sap_only.solver = sp->solver == LQCD_SOLVER_DFL_NET_GCR ? LQCD_SOLVER_DFL_SAP_GCR
                                                                             : LQCD_SOLVER_SAP_GCR;
-                    LQCD_TRY(precond(c, &sap_only, rho, (double2 *)fb, nrhs));
+                    LQCD_TRY(kv.precond_with(&sap_only, rho, (T *)fb));
                     for (int r : reject) {
-                        LQCD_CUDA_CHECK(c, cudaMemcpyAsync(ph + r * nf, (double2 *)fb + r * nf, nf * sizeof(double2),
+                        LQCD_CUDA_CHECK(c, cudaMemcpyAsync(ph + r * nf, (T *)fb + r * nf, kv.field_bytes(),
                                                            cudaMemcpyDeviceToDevice, c->stream));
                         S.net_fallbacks[r]++;
                     }
                     LQCD_TRY(orth());
                 }
             }
-            std::vector<double> coef2(2 * (size_t)nrhs);
+            std::vector<double> sx(nrhs);
             for (int r = 0; r < nrhs; r++) {
                 const double bk = std::sqrt(dots[2 * (2 * r)]);
                 b[(size_t)r * nkv + k] = bk;
@@ -328,12 +454,11 @@ lqcd_status gcr_native(lqcd_ctx *c, const lqcd_solver_params *sp, const std::vec
                 // rho -= c_k chi_k / b_k (chi_k not yet normalised); chi_k *= 1/b_k
                 coef[2 * r] = active[r] ? cr * s : 0.0;
                 coef[2 * r + 1] = active[r] ? ci * s : 0.0;
-                coef2[2 * r] = s - 1.0;
-                coef2[2 * r + 1] = 0.0;
+                sx[r] = s;
                 if (active[r]) rn2[r] = std::max(0.0, rn2[r] - (cr * cr + ci * ci));
             }
-            LQCD_TRY(bblas_multi_axpy(c, n2, nrhs, 1, coef.data(), (const double *)ch, 0, n2, (double *)rho, n2, -1.0));
-            LQCD_TRY(bblas_multi_axpy(c, n2, nrhs, 1, coef2.data(), (const double *)ch, 0, n2, (double *)ch, n2, 1.0));
+            LQCD_TRY(kv.rho_update(coef.data(), sx.data(), ch, rho));
+            c->prof_gs_bytes += kv.final_fields() * (double)bf64 * sizeof(double2);
             it++;
             nk = k + 1;
             bool recompute = false;
@@ -370,9 +495,7 @@ lqcd_status gcr_native(lqcd_ctx *c, const lqcd_solver_params *sp, const std::vec
             }
         }
         prof.start();
-        if (nk > 0)
-            LQCD_TRY(bblas_multi_axpy(c, n2, nrhs, nk, coef.data(), (const double *)phi, 2 * bf, n2, (double *)psi, n2,
-                                      1.0));
+        if (nk > 0) LQCD_TRY(kv.psi_update(nk, coef.data(), phi, bf, psi));
         // restart from the FP64 true residual
         LQCD_TRY(dirac_D(c, LQCD_F64, psi, w, nrhs));
         LQCD_TRY(blas_sub(c, n2 * nrhs, (const double *)eta, (const double *)w, (double *)rho));
@@ -393,6 +516,14 @@ lqcd_status gcr_native(lqcd_ctx *c, const lqcd_solver_params *sp, const std::vec
     }
     for (int r = 0; r < nrhs; r++) S.relres[r] = eta_n[r] > 0 ? res[r] / eta_n[r] : 0;
     return LQCD_OK;
+}
+
+// Krylov vectors in the inner precision (F64 or F32)
+lqcd_status gcr_native(lqcd_ctx *c, const lqcd_solver_params *sp, const std::vector<double> &tol,
+                       const double2 *eta, double2 *psi, int nrhs, int nmx, GcrState &S)
+{
+    if (sp->inner == LQCD_F32) return gcr_impl<Krylov32>(c, sp, tol, eta, psi, nrhs, nmx, S);
+    return gcr_impl<Krylov64>(c, sp, tol, eta, psi, nrhs, nmx, S);
 }
 
 // |eta_e - Dhat psi_e| / |eta_e| per rhs; eta, psi: nrhs native full fields (even halves used)
