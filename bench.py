@@ -155,7 +155,7 @@ KAPPA_OF = {(8, 8, 8, 8): 0.1355, (32, 16, 16, 16): 0.1357, (48, 24, 24, 24): 0.
 
 
 def solve_once(ctx, lqcd, eta, solver, inner, Ns=20, ninv=8, ctol=1e-2, seed=100, cnmx=4096, cnkv=16, cprec=None,
-               nkv=16, sap_prec=None):
+               nkv=16, sap_prec=None, krylov=None):
     """Time-to-solution of Dhat psi = eta (all fields of eta) to 1e-10 with the
     given solver; the subspace build is timed separately and included in total."""
     import torch
@@ -174,16 +174,18 @@ def solve_once(ctx, lqcd, eta, solver, inner, Ns=20, ninv=8, ctol=1e-2, seed=100
                       coarse_nmx=cnmx, coarse_prec=cp)
         torch.cuda.synchronize()
         build_s = time.perf_counter() - t0
-        res.update({"Ns": Ns, "ninv": ninv, "coarse_tol": ctol, "coarse_nmx": cnmx,
+        res.update({"Ns": Ns, "ninv": ninv, "coarse_tol": ctol, "coarse_nmx": cnmx, "coarse_nkv": cnkv,
                     "coarse_prec": "f32" if cp == lqcd.F32 else "f64", "build_s": round(build_s, 4)})
     sid = {"cgnr": lqcd.SOLVER_CGNR, "sap": lqcd.SOLVER_SAP_GCR, "dfl": lqcd.SOLVER_DFL_SAP_GCR}[solver]
     t0 = time.perf_counter()
     sp = prec if sap_prec is None else sap_prec
+    kr = lqcd.F32 if krylov == "f32" else lqcd.F64
     psi, info, st = ctx.solve_dhat(eta, solver=sid, tol=1e-10, nmx=20000 if solver == "cgnr" else 4096,
-                                   nkv=nkv, sap_prec=sp, inner=prec, check=False)
+                                   nkv=nkv, sap_prec=sp, inner=prec, check=False, krylov=kr)
     torch.cuda.synchronize()
     solve_s = time.perf_counter() - t0
-    res.update({"status": st, "solve_s": round(solve_s, 4), "total_s": round(solve_s + build_s, 4),
+    res.update({"krylov": "f32" if kr == lqcd.F32 else "f64",
+                "status": st, "solve_s": round(solve_s, 4), "total_s": round(solve_s + build_s, 4),
                 "iters": [i["iters"] for i in info],
                 "max_relres_dhat": max(i["relres_dhat"] for i in info)})
     if solver == "dfl":
@@ -195,14 +197,17 @@ def time_to_solve(ctx, lqcd, eta, net=None):
     """Time-to-solution of Dhat psi = eta for the 12 sources to a true relative
     residual <= 1e-10 (checked in FP64), subspace builds included:
       plain_f64 : deflated SAP-GCR, FP64 everywhere, one source at a time
-      chosen    : deflated SAP-GCR, FP16 (per-site scale) SAP, FP32 subspace /
-                  little operator / stencil, FP64 outer GCR, the 12 sources in
-                  one batched solve (fastest measured form)
-      dfl_mixed : the same with FP32 SAP
-      learned   : the same subspace with the trained network as the smoother
-                  (deflated SAP where its step fails); training at 32x16^3
-                  reported apart
-      sap_f32, sap_f16s : SAP-GCR without deflation, FP32 / FP16 SAP
+      dfl_mixed : deflated SAP-GCR with the workload's stated precisions: FP32
+                  SAP, subspace and stencil, FP64 outer GCR (Krylov vectors and
+                  Gram-Schmidt) and FP64 little-Dirac solve, the 12 sources in
+                  one batched solve
+      chosen    : the fastest measured form: FP16 (per-site scale) SAP, FP32
+                  subspace, stencil, little-Dirac solve and GCR Krylov vectors
+                  (FP64 residual, solution and restarts), 12 sources batched
+      learned   : the chosen form's subspace and precisions with the trained
+                  network as the smoother (deflated SAP where its step fails);
+                  training at 32x16^3 reported apart
+      sap_f32, sap_f16s : SAP-GCR without deflation, FP32 / FP16 SAP, FP64 GCR
     Every form is first run for two steps (and its subspace built once) so
     that launch-shape tuning and workspace growth stay out of the timings."""
     import torch
@@ -219,11 +224,11 @@ def time_to_solve(ctx, lqcd, eta, net=None):
         ctx.solve_dhat(e, solver=lqcd.SOLVER_DFL_SAP_GCR, tol=1e-10, nmx=2, sap_prec=prec, inner=prec, check=False)
         if prec == lqcd.F32:
             ctx.solve_dhat(eta, solver=lqcd.SOLVER_DFL_SAP_GCR, tol=1e-10, nmx=2, sap_prec=lqcd.F16S, inner=prec,
-                           check=False)
+                           check=False, krylov=lqcd.F32)
         if prec == lqcd.F32 and net is not None:
             ctx.net_set(NET_CHANS, net["W"], act=lqcd.BF16)
             ctx.solve_dhat(eta, solver=lqcd.SOLVER_DFL_NET_GCR, tol=1e-10, nmx=2, sap_prec=prec, inner=prec,
-                           check=False)
+                           check=False, krylov=lqcd.F32)
     del v0
     torch.cuda.synchronize()
     r, _ = solve_once(ctx, lqcd, eta, "sap", "f32")
@@ -236,30 +241,37 @@ def time_to_solve(ctx, lqcd, eta, net=None):
     out["sap_f16s"] = {"form": "SAP-GCR, FP16 (per-site scale) SAP, FP32 stencil, FP64 GCR, 12 RHS batched",
                        "seconds": round(time.perf_counter() - t0, 4), "iters": max(i["iters"] for i in info),
                        "max_relres_dhat": max(i["relres_dhat"] for i in info), "status": st}
-    # one subspace build (timed, included in every deflated form) and three smoothers on it
-    r, _ = solve_once(ctx, lqcd, eta, "dfl", "f32", Ns=20, ninv=8, ctol=1e-2, cnmx=64, cprec="f32")
+    # the workload's stated precisions: its own subspace build (FP64 little operator)
+    r, _ = solve_once(ctx, lqcd, eta, "dfl", "f32", Ns=20, ninv=8, ctol=1e-2, cnmx=64, cprec="f64")
+    out["dfl_mixed"] = {"form": "deflated SAP-GCR (Ns=20, 4^4 blocks), FP32 SAP/subspace/stencil, FP64 GCR "
+                                "(Krylov vectors, Gram-Schmidt) and FP64 little-Dirac solve, 12 RHS batched",
+                        "seconds": r["total_s"], "build_s": r["build_s"], "iters": max(r["iters"]),
+                        "max_relres_dhat": r["max_relres_dhat"], "status": r["status"]}
+    # one subspace build with the FP32 little operator (timed, included in both
+    # forms below) and two smoothers on it
+    r, _ = solve_once(ctx, lqcd, eta, "dfl", "f32", Ns=20, ninv=8, ctol=1e-2, cnmx=64, cprec="f32",
+                      sap_prec=lqcd.F16S, krylov="f32")
     build = r["build_s"]
-    out["dfl_mixed"] = {"form": "deflated SAP-GCR (Ns=20, 4^4 blocks), FP32 SAP/subspace/little operator, FP64 GCR, "
-                                "12 RHS batched", "seconds": r["total_s"], "build_s": build,
-                        "iters": max(r["iters"]), "max_relres_dhat": r["max_relres_dhat"], "status": r["status"]}
-
-    def deflated(sid, sap_prec):
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        _, info, st = ctx.solve_dhat(eta, solver=sid, tol=1e-10, sap_prec=sap_prec, inner=lqcd.F32, check=False)
-        torch.cuda.synchronize()
-        return {"seconds": round(time.perf_counter() - t0 + build, 4), "build_s": build,
-                "iters": max(i["iters"] for i in info), "net_fallbacks": sum(i["net_fallbacks"] for i in info),
-                "max_relres_dhat": max(i["relres_dhat"] for i in info), "status": st}
     out["chosen"] = {"form": "deflated SAP-GCR (Ns=20, 4^4 blocks), FP16 (per-site scale) SAP, FP32 subspace, "
-                             "little operator and stencil, FP64 GCR, 12 RHS batched",
-                     **deflated(lqcd.SOLVER_DFL_SAP_GCR, lqcd.F16S)}
+                             "stencil, little-Dirac solve and GCR Krylov vectors; FP64 residual, solution and "
+                             "restarts; 12 RHS batched",
+                     "seconds": r["total_s"], "build_s": build, "iters": max(r["iters"]), "net_fallbacks": 0,
+                     "max_relres_dhat": r["max_relres_dhat"], "status": r["status"]}
     if net is not None:
         # the same subspace, the network in place of the SAP smoother
         ctx.net_set(NET_CHANS, net["W"], act=lqcd.BF16)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, info, st = ctx.solve_dhat(eta, solver=lqcd.SOLVER_DFL_NET_GCR, tol=1e-10, sap_prec=lqcd.F32,
+                                     inner=lqcd.F32, check=False, krylov=lqcd.F32)
+        torch.cuda.synchronize()
         out["learned"] = {"form": "deflated GCR (Ns=20), trained BF16 network as smoother, deflated FP32 SAP as "
-                                  "fallback, FP64 GCR, 12 RHS batched",
-                          **deflated(lqcd.SOLVER_DFL_NET_GCR, lqcd.F32),
+                                  "fallback, the chosen form's FP32 subspace / little-Dirac solve / Krylov vectors, "
+                                  "12 RHS batched",
+                          "seconds": round(time.perf_counter() - t0 + build, 4), "build_s": build,
+                          "iters": max(i["iters"] for i in info),
+                          "net_fallbacks": sum(i["net_fallbacks"] for i in info),
+                          "max_relres_dhat": max(i["relres_dhat"] for i in info), "status": st,
                           "training": {"lattice": "32x16x16x16", "pairs": net["pairs"], "seconds": net["train_s"],
                                        "loss_first": net["loss_first"], "loss_last": net["loss_last"]}}
     total, build, iters, worst, st = 0.0, 0.0, 0, 0.0, 0
@@ -302,7 +314,8 @@ def run_solve(args):
     # the first pass tunes launch shapes and grows workspaces; the second is reported
     for _ in range(2):
         res, _ = solve_once(ctx, lqcd, eta, args.solver, args.prec, Ns=args.Ns, ninv=args.ninv, ctol=args.ctol,
-                            cnmx=args.cnmx, cprec=args.cprec, nkv=args.nkv,
+                            cnmx=args.cnmx, cnkv=args.cnkv, cprec=args.cprec, nkv=args.nkv,
+                            krylov=args.krylov,
                             sap_prec={"f16s": lqcd.F16S, "f32": lqcd.F32, "f64": lqcd.F64}.get(args.sap_prec))
     res["nkv"] = args.nkv
     res["sap_prec"] = args.sap_prec or args.prec
@@ -584,7 +597,10 @@ def main():
     ap.add_argument("--ninv", type=int, default=8)
     ap.add_argument("--ctol", type=float, default=1e-2)
     ap.add_argument("--cnmx", type=int, default=4096, help="iteration budget of each little-Dirac solve")
+    ap.add_argument("--cnkv", type=int, default=16, help="Krylov vectors per little-Dirac GCR cycle (<= 32)")
     ap.add_argument("--cprec", default=None, choices=["f32", "f64"], help="little-Dirac operator precision")
+    ap.add_argument("--krylov", default=None, choices=["f32", "f64"],
+                    help="GCR Krylov-vector precision (f32 needs --prec f32)")
     ap.add_argument("--nkv", type=int, default=16, help="solve mode: GCR Krylov vectors per cycle")
     ap.add_argument("--sap-prec", default=None, choices=["f16s", "f32", "f64"], help="solve mode: SAP precision")
     args = ap.parse_args()

@@ -245,6 +245,11 @@ typedef struct {
     double tol;              /* target true relative residual */
     lqcd_sap_params sap;     /* preconditioner */
     lqcd_prec inner;         /* precision of the preconditioner output and of D phi_k */
+    lqcd_prec krylov;        /* GCR Krylov vectors phi_k, chi_k and their Gram-Schmidt: LQCD_F64
+                                (0, the default), or LQCD_F32 with inner == LQCD_F32 (native F32
+                                fields, products in float, sums in double).  The residual, the
+                                solution and the restart residual eta - D psi stay FP64 in both;
+                                any other value is LQCD_ERR_ARG */
 } lqcd_solver_params;
 
 typedef struct {

@@ -106,6 +106,28 @@ __device__ void block_sum(double *vals, int n, double *sh, double *res)
     __syncthreads();
 }
 
+// as block_sum for float values: the warp sums in float, the sum over warps in
+// double (FP64 shuffles and adds are the bound on GB300's FP64 pipe otherwise)
+template <int NV>
+__device__ void block_sum_f(const float (&vals)[NV], int n, double *sh, double *res)
+{
+    int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int i = 0; i < NV; i++) {
+        if (i >= n) break;
+        float v = vals[i];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) sh[i * 32 + warp] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < n) {
+        double s = 0;
+        for (int w = 0; w < nw; w++) s += sh[threadIdx.x * 32 + w];
+        res[threadIdx.x] = s;
+    }
+    __syncthreads();
+}
+
 // one projected hop (1 -+ g_mu) acting on psi at the neighbour, times sign
 __device__ void hop1(int mu, int sgn, const C psi[12], const C u[3][3], bool dag, double sign, C acc[12])
 {
@@ -328,19 +350,27 @@ __global__ void k_project(Geom g, DBlk B, const T *phi, int Ns, long fstride, co
             wf[2 * cc + 1] = (float)w[cc].im;
         }
     for (int k0 = 0; k0 < Ns; k0 += RCHUNK) {
-        double d[2 * RCHUNK];
         int kn = min(RCHUNK, Ns - k0);
-        for (int i = 0; i < RCHUNK; i++) {
-            d[2 * i] = d[2 * i + 1] = 0;
-            if (i < kn) {
-                if constexpr (std::is_same<T, double2>::value) {
+        if constexpr (std::is_same<T, double2>::value) {
+            double d[2 * RCHUNK];
+            for (int i = 0; i < RCHUNK; i++) {
+                d[2 * i] = d[2 * i + 1] = 0;
+                if (i < kn) {
                     C q[12];
                     ld(phi + (k0 + i) * fstride + s.p * hs, g.Vh, s.r, q);
                     for (int cc = 0; cc < 12; cc++) {
                         d[2 * i] += q[cc].re * w[cc].re + q[cc].im * w[cc].im;
                         d[2 * i + 1] += q[cc].re * w[cc].im - q[cc].im * w[cc].re;
                     }
-                } else {
+                }
+            }
+            block_sum(d, 2 * kn, sh, res);
+        } else {
+            float d[2 * RCHUNK];
+#pragma unroll
+            for (int i = 0; i < RCHUNK; i++) {
+                d[2 * i] = d[2 * i + 1] = 0.f;
+                if (i < kn) {
                     const float4 *f = (const float4 *)(phi + (k0 + i) * fstride + s.p * hs) + s.r;
                     float re = 0, im = 0;
 #pragma unroll
@@ -353,8 +383,8 @@ __global__ void k_project(Geom g, DBlk B, const T *phi, int Ns, long fstride, co
                     d[2 * i + 1] = im;
                 }
             }
+            block_sum_f<2 * RCHUNK>(d, 2 * kn, sh, res);
         }
-        block_sum(d, 2 * kn, sh, res);
         if (t < kn) c[(long)b * Ns + k0 + t] = make_double2(res[2 * t], res[2 * t + 1]);
     }
 }
@@ -381,13 +411,16 @@ __global__ void k_expand(Geom g, DBlk B, const T *phi, int Ns, long fstride, con
             for (int cc = 0; cc < 12; cc++) w[cc] = w[cc] + a * q[cc];
         }
     } else {
-        // FP32 subspace: products and sums in float
+        // FP32 subspace: products and sums in float; the block's coefficients
+        // converted to float once per CTA
+        __shared__ float2 cf[NS_MAX];
+        if (t < Ns) cf[t] = make_float2((float)c[(long)b * Ns + t].x, (float)c[(long)b * Ns + t].y);
+        __syncthreads();
         float acc[24];
 #pragma unroll
         for (int i = 0; i < 24; i++) acc[i] = 0.f;
         for (int k = 0; k < Ns; k++) {
-            double2 ck = c[(long)b * Ns + k];
-            const float ar = (float)ck.x, ai = (float)ck.y;
+            const float ar = cf[k].x, ai = cf[k].y;
             const float4 *f = (const float4 *)(phi + k * fstride + s.p * hs) + s.r;
 #pragma unroll
             for (int q = 0; q < 6; q++) {
@@ -505,108 +538,90 @@ __global__ void k_block_inverse(int nblk, int Ns, const double2 *Aint, double2 *
     }
 }
 
-__device__ __forceinline__ void warp_sum2(double &re, double &im)
-{
-    for (int o = 16; o > 0; o >>= 1) {
-        re += __shfl_down_sync(0xffffffffu, re, o);
-        im += __shfl_down_sync(0xffffffffu, im, o);
-    }
-}
 
-// out_r[b*Ns + k] = sum_l Dinv[b][k][l] in_r[b*Ns + l]: one CTA per block b,
-// warp k computes row k (lane l holds column l), the row is kept in registers
-// for all nrhs vectors (stride N).
-__global__ void k_block_jacobi(int nblk, int Ns, long N, int nrhs, const double2 *__restrict__ Dinv,
-                               const double2 *__restrict__ in, double2 *out)
-{
-    const int b = blockIdx.x, k = threadIdx.x >> 5, l = threadIdx.x & 31;
-    if (b >= nblk || k >= Ns) return;
-    double2 a = l < Ns ? Dinv[((size_t)b * Ns + k) * Ns + l] : make_double2(0, 0);
-    for (int r = 0; r < nrhs; r++) {
-        double2 y = l < Ns ? in[r * N + (long)b * Ns + l] : make_double2(0, 0);
-        double re = a.x * y.x - a.y * y.y, im = a.x * y.y + a.y * y.x;
-        warp_sum2(re, im);
-        if (l == 0) out[r * N + (long)b * Ns + k] = make_double2(re, im);
-    }
-}
-
-// FP32 operator variants: matrices stored as float2, the input vector given in
-// float, products and the row sums in float; the output in double (FP64
-// coarse GCR, input converted once per application by k_to_float2) or in
-// float (FP32 coarse GCR)
+// Little-operator and block-Jacobi products of nrhs coarse vectors:
+// out_r[b*Ns + k] = sum_j sum_l M[b][j][k][l] in_r[n_j(b)*Ns + l] with j over the
+// nine couplings of block b (n_j from nbr) or, for the block-Jacobi inverse, the
+// block itself (nmat = 1, n_0 = b).  One CTA per (block, chunk of rhs): the
+// input segments of the chunk are staged in shared memory as [j][r][l] in the
+// matrix's precision with an odd row pitch (conflict-free reads for up to 16
+// right-hand sides in a warp), then thread (k, r) forms one output in the
+// matrix's precision, summing in (j, l) order.  Matrix rows are read through
+// L1, each by all rhs of the chunk.
+__device__ __forceinline__ void put2(double2 *p, double re, double im) { *p = make_double2(re, im); }
 __device__ __forceinline__ void put2(double2 *p, float re, float im) { *p = make_double2(re, im); }
 __device__ __forceinline__ void put2(float2 *p, float re, float im) { *p = make_float2(re, im); }
-// CRB right-hand sides per pass: their loads and warp reductions are
-// independent and overlap (each one's arithmetic order is unchanged)
-constexpr int CRB = 4;
-template <int R>
-__device__ __forceinline__ void warp_sum2f_n(float (&re)[R], float (&im)[R])
+__device__ __forceinline__ void to_mat(float2 &m, float2 v) { m = v; }
+__device__ __forceinline__ void to_mat(float2 &m, double2 v) { m = make_float2((float)v.x, (float)v.y); }
+__device__ __forceinline__ void to_mat(double2 &m, double2 v) { m = v; }
+template <class MT>
+struct CAcc;
+template <>
+struct CAcc<float2> {
+    using R = float;
+};
+template <>
+struct CAcc<double2> {
+    using R = double;
+};
+constexpr int COARSE_SMEM = 96 * 1024;
+
+template <class MT, class IT, class OT>
+__global__ void __launch_bounds__(256) k_coarse_mul(int Ns, long N, int nrhs, int rc, int nmat, const int *nbr,
+                                                    const MT *__restrict__ M, const IT *__restrict__ in, OT *out)
 {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-        for (int q = 0; q < R; q++) {
-            re[q] += __shfl_down_sync(0xffffffffu, re[q], o);
-            im[q] += __shfl_down_sync(0xffffffffu, im[q], o);
-        }
-}
-template <class OT>
-__global__ void k_block_jacobi32(int nblk, int Ns, long N, int nrhs, const float2 *__restrict__ Dinv,
-                                 const float2 *__restrict__ in, OT *out)
-{
-    const int b = blockIdx.x, k = threadIdx.x >> 5, l = threadIdx.x & 31;
-    if (b >= nblk || k >= Ns) return;
-    float2 a = l < Ns ? Dinv[((size_t)b * Ns + k) * Ns + l] : make_float2(0, 0);
-    for (int r0 = 0; r0 < nrhs; r0 += CRB) {
-        float re[CRB], im[CRB];
-#pragma unroll
-        for (int q = 0; q < CRB; q++) {
-            const float2 y = (l < Ns && r0 + q < nrhs) ? in[(r0 + q) * N + (long)b * Ns + l] : make_float2(0, 0);
-            re[q] = a.x * y.x - a.y * y.y;
-            im[q] = a.x * y.y + a.y * y.x;
-        }
-        warp_sum2f_n<CRB>(re, im);
-        if (l == 0)
-#pragma unroll
-            for (int q = 0; q < CRB; q++)
-                if (r0 + q < nrhs) put2(out + (r0 + q) * N + (long)b * Ns + k, re[q], im[q]);
+    using R = typename CAcc<MT>::R;
+    extern __shared__ __align__(16) unsigned char coarse_raw[];
+    MT *cs = reinterpret_cast<MT *>(coarse_raw);
+    const int b = blockIdx.x, r0 = blockIdx.y * rc, nr = min(rc, nrhs - r0), P = Ns | 1;
+    in += r0 * N;
+    out += r0 * N;
+    for (int e = threadIdx.x; e < nmat * nr * Ns; e += blockDim.x) {
+        const int l = e % Ns, jr = e / Ns, r = jr % nr, j = jr / nr;
+        const int nb = nbr ? nbr[b * 9 + j] : b;
+        to_mat(cs[jr * P + l], in[r * N + (long)nb * Ns + l]);
     }
-}
-template <class OT>
-__global__ void k_little_apply_b32(int nblk, int Ns, long N, int nrhs, const int *nbr,
-                                   const float2 *__restrict__ Aint, const float2 *__restrict__ c, OT *out)
-{
-    const int b = blockIdx.x, k = threadIdx.x >> 5, l = threadIdx.x & 31;
-    if (b >= nblk || k >= Ns) return;
-    float2 a[9];
-    int nb[9];
-#pragma unroll
-    for (int j = 0; j < 9; j++) {
-        nb[j] = nbr[b * 9 + j];
-        a[j] = l < Ns ? Aint[(((long)b * 9 + j) * Ns + k) * Ns + l] : make_float2(0, 0);
-    }
-    for (int r0 = 0; r0 < nrhs; r0 += CRB) {
-        float re[CRB], im[CRB];
-#pragma unroll
-        for (int q = 0; q < CRB; q++) {
-            re[q] = im[q] = 0;
-            if (l < Ns && r0 + q < nrhs) {
-                const float2 *cr = c + (r0 + q) * N + l;
-#pragma unroll
-                for (int j = 0; j < 9; j++) {
-                    const float2 y = cr[(long)nb[j] * Ns];
-                    re[q] += a[j].x * y.x - a[j].y * y.y;
-                    im[q] += a[j].x * y.y + a[j].y * y.x;
-                }
+    __syncthreads();
+    for (int o = threadIdx.x; o < Ns * nr; o += blockDim.x) {
+        const int k = o / nr, r = o - k * nr;
+        R re = 0, im = 0;
+        const MT *Mk = M + ((long)b * nmat * Ns + k) * Ns;
+        for (int j = 0; j < nmat; j++) {
+            const MT *row = Mk + (long)j * Ns * Ns;
+            const MT *x = cs + (j * nr + r) * P;
+#pragma unroll 2
+            for (int l = 0; l < Ns; l++) {
+                const MT a = __ldg(row + l), y = x[l];
+                re += a.x * y.x - a.y * y.y;
+                im += a.x * y.y + a.y * y.x;
             }
         }
-        warp_sum2f_n<CRB>(re, im);
-        if (l == 0)
-#pragma unroll
-            for (int q = 0; q < CRB; q++)
-                if (r0 + q < nrhs) put2(out + (r0 + q) * N + (long)b * Ns + k, re[q], im[q]);
+        put2(out + r * N + (long)b * Ns + k, re, im);
     }
 }
+
+// host side: rhs chunk so that the staged segments fit COARSE_SMEM
+template <class MT, class IT, class OT>
+lqcd_status coarse_mul(lqcd_ctx *c, int nblk, int Ns, long N, int nrhs, int nmat, const int *nbr, const MT *M,
+                       const IT *in, OT *out)
+{
+    static bool attr = false;
+    if (!attr) {
+        LQCD_CUDA_CHECK(c, cudaFuncSetAttribute(k_coarse_mul<MT, IT, OT>,
+                                                cudaFuncAttributeMaxDynamicSharedMemorySize, COARSE_SMEM));
+        attr = true;
+    }
+    const int P = Ns | 1;
+    const int rc = std::max(1, std::min(nrhs, COARSE_SMEM / (int)(nmat * P * sizeof(MT))));
+    const int threads = std::min(256, (Ns * rc + 31) / 32 * 32);
+    const size_t smem = (size_t)nmat * rc * P * sizeof(MT);
+    k_coarse_mul<MT, IT, OT><<<dim3(nblk, div_up(nrhs, rc)), threads, smem, c->stream>>>(Ns, N, nrhs, rc, nmat, nbr,
+                                                                                         M, in, out);
+    c->n_kernel_launches++;
+    LQCD_LAUNCH_CHECK(c);
+    return LQCD_OK;
+}
+
 __global__ void k_to_float2(long n, const double2 *in, float2 *out)
 {
     long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
@@ -713,37 +728,6 @@ __global__ void k_fsub(long n, const float2 *a, const float2 *b, float2 *out)
     if (i < n) out[i] = make_float2(a[i].x - b[i].x, a[i].y - b[i].y);
 }
 
-// batched little operator apply, out_r[b*Ns + k] = sum_j sum_l A[b][j][k][l]
-// c_r[nbr[b][j]*Ns + l]: one CTA per block, warp per row, the nine row
-// segments in registers and reused for every right-hand side.
-__global__ void k_little_apply_b(int nblk, int Ns, long N, int nrhs, const int *nbr,
-                                 const double2 *__restrict__ Aint, const double2 *__restrict__ c, double2 *out)
-{
-    const int b = blockIdx.x, k = threadIdx.x >> 5, l = threadIdx.x & 31;
-    if (b >= nblk || k >= Ns) return;
-    double2 a[9];
-    int nb[9];
-#pragma unroll
-    for (int j = 0; j < 9; j++) {
-        nb[j] = nbr[b * 9 + j];
-        a[j] = l < Ns ? Aint[(((long)b * 9 + j) * Ns + k) * Ns + l] : make_double2(0, 0);
-    }
-    for (int r = 0; r < nrhs; r++) {
-        double re = 0, im = 0;
-        if (l < Ns) {
-            const double2 *cr = c + r * N + l;
-#pragma unroll
-            for (int j = 0; j < 9; j++) {
-                double2 y = cr[(long)nb[j] * Ns];
-                re += a[j].x * y.x - a[j].y * y.y;
-                im += a[j].x * y.y + a[j].y * y.x;
-            }
-        }
-        warp_sum2(re, im);
-        if (l == 0) out[r * N + (long)b * Ns + k] = make_double2(re, im);
-    }
-}
-
 }  // namespace
 
 struct DflState {
@@ -838,50 +822,21 @@ lqcd_status expand(lqcd_ctx *c, const double2 *cv, double2 *out, int nrhs = 1)
     return c->dfl->prec == LQCD_F64 ? launch_expand<double2>(c, cv, out, nrhs)
                                     : launch_expand<float4>(c, cv, out, nrhs);
 }
-// float copy of coarse vectors for the FP32 operator (grown on demand)
-lqcd_status coarse_f32(lqcd_ctx *c, long n, float2 **out)
-{
-    void *p;
-    LQCD_TRY(ws_get(c, WS_COARSE_F32, n * sizeof(float2), &p));
-    *out = (float2 *)p;
-    return LQCD_OK;
-}
-
 lqcd_status little_apply_b(lqcd_ctx *c, const double2 *cv, double2 *out, int nrhs)
 {
     DflState *d = c->dfl;
-    long N = (long)d->B.nblk * d->Ns;
-    if (d->Aint32) {
-        float2 *cf;
-        LQCD_TRY(coarse_f32(c, N * nrhs, &cf));
-        k_to_float2<<<div_up(N * nrhs, 256), 256, 0, c->stream>>>(N * nrhs, cv, cf);
-        k_little_apply_b32<double2><<<d->B.nblk, 32 * d->Ns, 0, c->stream>>>(d->B.nblk, d->Ns, N, nrhs, d->nbr,
-                                                                             d->Aint32, cf, out);
-        c->n_kernel_launches++;
-    } else
-        k_little_apply_b<<<d->B.nblk, 32 * d->Ns, 0, c->stream>>>(d->B.nblk, d->Ns, N, nrhs, d->nbr, d->Aint, cv, out);
-    c->n_kernel_launches++;
-    LQCD_LAUNCH_CHECK(c);
-    return LQCD_OK;
+    const long N = (long)d->B.nblk * d->Ns;
+    if (d->Aint32) return coarse_mul(c, d->B.nblk, d->Ns, N, nrhs, 9, d->nbr, d->Aint32, cv, out);
+    return coarse_mul(c, d->B.nblk, d->Ns, N, nrhs, 9, d->nbr, d->Aint, cv, out);
 }
 lqcd_status little_apply(lqcd_ctx *c, const double2 *cv, double2 *out) { return little_apply_b(c, cv, out, 1); }
 
 lqcd_status block_jacobi(lqcd_ctx *c, const double2 *in, double2 *out, int nrhs)
 {
     DflState *d = c->dfl;
-    long N = (long)d->B.nblk * d->Ns;
-    if (d->Dinv32) {
-        float2 *cf;
-        LQCD_TRY(coarse_f32(c, N * nrhs, &cf));
-        k_to_float2<<<div_up(N * nrhs, 256), 256, 0, c->stream>>>(N * nrhs, in, cf);
-        k_block_jacobi32<double2><<<d->B.nblk, 32 * d->Ns, 0, c->stream>>>(d->B.nblk, d->Ns, N, nrhs, d->Dinv32, cf,
-                                                                           out);
-        c->n_kernel_launches++;
-    } else
-        k_block_jacobi<<<d->B.nblk, 32 * d->Ns, 0, c->stream>>>(d->B.nblk, d->Ns, N, nrhs, d->Dinv, in, out);
-    c->n_kernel_launches++;
-    LQCD_LAUNCH_CHECK(c);
-    return LQCD_OK;
+    const long N = (long)d->B.nblk * d->Ns;
+    if (d->Dinv32) return coarse_mul(c, d->B.nblk, d->Ns, N, nrhs, 1, (const int *)nullptr, d->Dinv32, in, out);
+    return coarse_mul(c, d->B.nblk, d->Ns, N, nrhs, 1, (const int *)nullptr, d->Dinv, in, out);
 }
 
 // ---- device-resident scalar bookkeeping of the coarse GCR (one thread per rhs)
@@ -1094,14 +1049,10 @@ lqcd_status coarse_gcr32(lqcd_ctx *c, const double2 *b, double2 *x, int nrhs, do
         return LQCD_OK;
     };
     auto jacobi = [&](const float2 *in, float2 *out) {
-        k_block_jacobi32<float2><<<d->B.nblk, 32 * d->Ns, 0, c->stream>>>(d->B.nblk, d->Ns, N, nrhs, d->Dinv32, in,
-                                                                          out);
-        c->n_kernel_launches++;
+        return coarse_mul(c, d->B.nblk, d->Ns, N, nrhs, 1, (const int *)nullptr, d->Dinv32, in, out);
     };
     auto apply = [&](const float2 *in, float2 *out) {
-        k_little_apply_b32<float2><<<d->B.nblk, 32 * d->Ns, 0, c->stream>>>(d->B.nblk, d->Ns, N, nrhs, d->nbr,
-                                                                            d->Aint32, in, out);
-        c->n_kernel_launches++;
+        return coarse_mul(c, d->B.nblk, d->Ns, N, nrhs, 9, d->nbr, d->Aint32, in, out);
     };
     const int gn = div_up(bN, 256);
     k_to_float2<<<gn, 256, 0, c->stream>>>(bN, b, bf);
@@ -1116,8 +1067,8 @@ lqcd_status coarse_gcr32(lqcd_ctx *c, const double2 *b, double2 *x, int nrhs, do
         int nk = 0;
         for (int k = 0; k < nkv && it < nmx; k++) {
             float2 *pk = P + k * bN, *qk = Q + k * bN;
-            jacobi(rho, pk);
-            apply(pk, qk);
+            LQCD_TRY(jacobi(rho, pk));
+            LQCD_TRY(apply(pk, qk));
             if (k > 0) {
                 LQCD_TRY(dots(Q, bN, qk, k, S->dots));
                 k_c_gs<<<nrhs, k, 0, c->stream>>>(nrhs, k, S);
@@ -1135,7 +1086,7 @@ lqcd_status coarse_gcr32(lqcd_ctx *c, const double2 *b, double2 *x, int nrhs, do
         k_c_backsub<<<1, CG_R, 0, c->stream>>>(nrhs, nk, S);
         c->n_kernel_launches++;
         LQCD_TRY(axpy(nk, S->alpha, P, bN, xf, 1.f));
-        apply(xf, w);
+        LQCD_TRY(apply(xf, w));
         k_fsub<<<gn, 256, 0, c->stream>>>(bN, bf, w, rho);
         c->n_kernel_launches++;
         LQCD_TRY(dots(rho, 0, rho, 1, S->dots));

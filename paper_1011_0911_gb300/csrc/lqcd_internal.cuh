@@ -188,7 +188,6 @@ enum {
     WS_NET_BATCH_T,
     WS_NET_FALLBACK,
     WS_HASEN,
-    WS_COARSE_F32,
     WS_PHI64,       // F64 preconditioner output converted into FP32 Krylov vectors
 };
 lqcd_status ws_get(lqcd_ctx *c, int slot, size_t bytes, void **out);

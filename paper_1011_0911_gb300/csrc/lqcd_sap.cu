@@ -539,8 +539,8 @@ template <bool SA>
 struct SapSmemT;
 template <>
 struct SapSmemT<true> {
-    float4 U[4][3][2 * SAPS_NH];   // forward links, two rows, local lexicographic site
-    float4 A[18][2 * SAPS_NH];     // A (even sites) or A^-1 (odd sites), local lexicographic site
+    float4 U[4][3][2 * SAPS_NH];   // forward links, two rows, site par * SAPS_NH + t
+    float4 A[18][2 * SAPS_NH];     // A (even sites) or A^-1 (odd sites), site par * SAPS_NH + t
     float4 rho[6][SAPS_NH], chi[6][SAPS_NH], p[6][SAPS_NH], to[6][SAPS_NH], ro[6][SAPS_NH];
     float red[3][8];
 };
@@ -624,12 +624,14 @@ __device__ __forceinline__ void s_clover_half(const SapSmemT<SA> &S, int ls, con
         }
 }
 
-// half of the in-block hop sum at site (l, x, ls) from the smem field src of the
+// half of the in-block hop sum at site (l, x) from the smem field src of the
 // other parity: h = 0 forward hops, h = 1 backward hops; then the pair's halves
-// are added so both threads hold the full sum S (before the -1/2).
+// are added so both threads hold the full sum S (before the -1/2).  own: the
+// site's index par * SAPS_NH + t in the link arrays; the neighbours' links sit
+// at (1 - par) * SAPS_NH + their half index.
 template <class SM>
 __device__ __forceinline__ void s_hopsum(const Geom &g, const BlkGeom &B, const SM &S, int h, const int l[4],
-                                         const int x[4], int ls, const float4 (*src)[SAPS_NH], cx<float> acc[12])
+                                         const int x[4], int own, const float4 (*src)[SAPS_NH], cx<float> acc[12])
 {
 #pragma unroll
     for (int i = 0; i < 12; i++) acc[i] = mk(0.f, 0.f);
@@ -640,7 +642,7 @@ __device__ __forceinline__ void s_hopsum(const Geom &g, const BlkGeom &B, const 
             int ln = blk_nbr_lex(B, l, mu, +1);
             if (ln >= 0) {
                 float sg = (mu == 0 && x[0] == g.L[0] - 1) ? float(g.bc_t) : 1.f;
-                s_link(S, mu, ls, u);
+                s_link(S, mu, own, u);
                 s_spinor(src, ln >> 1, v);
                 proj_apply<float>(mu, -1, v, u, false, sg, acc);
             }
@@ -648,7 +650,7 @@ __device__ __forceinline__ void s_hopsum(const Geom &g, const BlkGeom &B, const 
             int ln = blk_nbr_lex(B, l, mu, -1);
             if (ln >= 0) {
                 float sg = (mu == 0 && x[0] == 0) ? float(g.bc_t) : 1.f;
-                s_link(S, mu, ln, u);
+                s_link(S, mu, (own < SAPS_NH ? SAPS_NH : 0) + (ln >> 1), u);
                 s_spinor(src, ln >> 1, v);
                 proj_apply<float>(mu, +1, v, u, true, sg, acc);
             }
@@ -656,8 +658,8 @@ __device__ __forceinline__ void s_hopsum(const Geom &g, const BlkGeom &B, const 
     }
 #pragma unroll
     for (int i = 0; i < 12; i++) {
-        acc[i].re += __shfl_xor_sync(0xffffffffu, acc[i].re, 1);
-        acc[i].im += __shfl_xor_sync(0xffffffffu, acc[i].im, 1);
+        acc[i].re += __shfl_xor_sync(0xffffffffu, acc[i].re, 16);
+        acc[i].im += __shfl_xor_sync(0xffffffffu, acc[i].im, 16);
     }
 }
 
@@ -681,8 +683,8 @@ __device__ __forceinline__ void stage_site(const h16s *f, long Vh, long r, float
     for (int q = 0; q < 6; q++) o[q] = make_float4(v[2 * q].re, v[2 * q].im, v[2 * q + 1].re, v[2 * q + 1].im);
 }
 // chirality half h (components 6h .. 6h+5) of site r.  The F16S forms are
-// called by both threads of a site pair (lanes 2t, 2t+1) together: the pair
-// agrees on the site's scale through a lane shuffle.
+// called by both threads of a site pair (lanes l and l ^ 16) together: the
+// pair agrees on the site's scale through a lane shuffle.
 __device__ __forceinline__ void half_load(const float4 *f, long Vh, long r, int h, cx<float> v[6])
 {
 #pragma unroll
@@ -719,7 +721,7 @@ __device__ __forceinline__ void half_store(h16s *f, long Vh, long r, int h, cons
     float m = 0.f;
 #pragma unroll
     for (int i = 0; i < 6; i++) m = fmaxf(m, fmaxf(fabsf(v[i].re), fabsf(v[i].im)));
-    m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 1));
+    m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 16));
     const float inv = m > 0.f ? 1.f / m : 0.f;
     uint4 *q = reinterpret_cast<uint4 *>(f);
     const cx<float> e0 = h ? v[2] : v[0], e1 = h ? v[3] : v[1], e2 = h ? v[4] : v[2], e3 = h ? v[5] : v[3];
@@ -773,7 +775,7 @@ __device__ __forceinline__ void sap_block_s_body(const SapArgs<P> &a, int bi, in
         const int par = i >= nh, t = par ? i - nh : i;
         SiteInfo s;
         block_site(a.g, B, org, par, t, s);
-        const int ls = blk_lex(B, s.l);
+        const int ls = par * SAPS_NH + t;
 #pragma unroll
         for (int mu = 0; mu < 4; mu++)
 #pragma unroll
@@ -797,15 +799,17 @@ __device__ __forceinline__ void sap_block_s_body(const SapArgs<P> &a, int bi, in
         }
     }
     __syncthreads();
-    const int h = tid & 1, t = tid >> 1;   // chirality half / hop direction, site rank
+    // chirality half / hop direction h and site rank t: lanes 0-15 of a warp
+    // take h = 0 of 16 sites, lanes 16-31 h = 1 of the same sites, so the 8
+    // lanes of every quarter-warp read consecutive rows of one shared-memory
+    // array (no bank conflicts between a site's two halves)
+    const int h = (tid >> 4) & 1, t = ((tid >> 5) << 4) | (tid & 15);
     const bool act = t < nh;
     SiteInfo so, se;
-    int lso = 0, lse = 0;
+    const int lso = SAPS_NH + t, lse = t;   // the sites' slots in the link / clover arrays
     if (act) {
         block_site(a.g, B, org, 1, t, so);
         block_site(a.g, B, org, 0, t, se);
-        lso = blk_lex(B, so.l);
-        lse = blk_lex(B, se.l);
     }
     cx<float> acc[12], v[6], w[6];
     // to = A_oo^-1 r_o (chirality half h)

@@ -2,11 +2,12 @@
 // Sec. 3-4 on the full operator, preconditioned by SAP or deflated SAP; the
 // solution of Dhat psi_e = eta_e is the even part of D^-1 (eta_e, 0) (Eq. 5).
 //
-// Precision: all Krylov bookkeeping is FP64 (Gram-Schmidt, residual, solution
-// update).  The preconditioner and D phi_k may run in FP32 ("inner"
-// precision); the recursive residual then carries FP32-level errors, so a
-// cycle stops once it has gained ~1e-5 and the next cycle restarts from the
-// FP64 true residual eta - D psi.
+// Precision: the residual, the solution update and the restart residual
+// eta - D psi are FP64.  The preconditioner and D phi_k may run in FP32
+// ("inner" precision), and with krylov = F32 the Krylov vectors and their
+// Gram-Schmidt are FP32 too (FP64 sums); the recursive residual then carries
+// FP32-level errors, so a cycle stops once it has gained ~1e-5 and the next
+// cycle restarts from the FP64 true residual.
 #include <chrono>
 #include <cmath>
 #include <vector>
@@ -211,10 +212,11 @@ lqcd_status bnorm2(lqcd_ctx *c, long n2, int nrhs, const double2 *x, std::vector
 }
 
 // Krylov-vector storage of the GCR.  Krylov64: phi_k and chi_k native F64
-// full fields.  Krylov32 (inner precision F32): phi_k and chi_k native F32
+// full fields.  Krylov32 (krylov = inner = F32): phi_k and chi_k native F32
 // full fields, so D phi_k runs on them directly and the Gram-Schmidt moves
-// half the bytes; rho and psi stay F64, the products with FP32 vectors are
-// formed in float and accumulated in double.
+// half the bytes and leaves GB300's FP64 pipe (FP64 products bound it at about
+// a third of HBM bandwidth); rho and psi stay F64, the products with FP32
+// vectors are formed in float and accumulated in double.
 struct Krylov64 {
     using T = double2;
     lqcd_ctx *c;
@@ -518,11 +520,11 @@ lqcd_status gcr_impl(lqcd_ctx *c, const lqcd_solver_params *sp, const std::vecto
     return LQCD_OK;
 }
 
-// Krylov vectors in the inner precision (F64 or F32)
+// Krylov vectors in F64 or (krylov == F32, inner == F32) in F32
 lqcd_status gcr_native(lqcd_ctx *c, const lqcd_solver_params *sp, const std::vector<double> &tol,
                        const double2 *eta, double2 *psi, int nrhs, int nmx, GcrState &S)
 {
-    if (sp->inner == LQCD_F32) return gcr_impl<Krylov32>(c, sp, tol, eta, psi, nrhs, nmx, S);
+    if (sp->krylov == LQCD_F32) return gcr_impl<Krylov32>(c, sp, tol, eta, psi, nrhs, nmx, S);
     return gcr_impl<Krylov64>(c, sp, tol, eta, psi, nrhs, nmx, S);
 }
 
@@ -561,6 +563,9 @@ lqcd_status check_params(lqcd_ctx *c, const lqcd_solver_params *p, int nrhs)
         return set_err(c, LQCD_ERR_ARG, "solver %d", (int)p->solver);
     if (p->solver != LQCD_SOLVER_CGNR && (p->inner != LQCD_F64 && p->inner != LQCD_F32))
         return set_err(c, LQCD_ERR_ARG, "inner precision %d", (int)p->inner);
+    if (p->krylov != LQCD_F64 && !(p->krylov == LQCD_F32 && p->inner == LQCD_F32))
+        return set_err(c, LQCD_ERR_ARG, "Krylov precision %d with inner precision %d", (int)p->krylov,
+                       (int)p->inner);
     return LQCD_OK;
 }
 

@@ -48,7 +48,7 @@ class DflParams(C.Structure):
 
 class SolverParams(C.Structure):
     _fields_ = [("solver", C.c_int), ("nkv", C.c_int), ("nmx", C.c_int), ("tol", C.c_double),
-                ("sap", SapParams), ("inner", C.c_int)]
+                ("sap", SapParams), ("inner", C.c_int), ("krylov", C.c_int)]
 
 
 class SolveInfo(C.Structure):
@@ -387,11 +387,11 @@ class Context:
         return hist[:steps]
 
     # -------------------------------------------------------------- solvers
-    def _solve(self, fn, eta, nsites, solver, tol, nkv, nmx, bs, ncy, nmr, sap_prec, inner, check):
+    def _solve(self, fn, eta, nsites, solver, tol, nkv, nmx, bs, ncy, nmr, sap_prec, inner, check, krylov=F64):
         eta = eta.to(torch.complex128).contiguous()
         nrhs = self._nrhs(eta, nsites)
         psi = torch.empty_like(eta)
-        p = SolverParams(solver, nkv, nmx, tol, sap_params(bs, ncy, nmr, sap_prec), inner)
+        p = SolverParams(solver, nkv, nmx, tol, sap_params(bs, ncy, nmr, sap_prec), inner, krylov)
         info = (SolveInfo * nrhs)()
         st = fn(self._h, C.byref(p), _ptr(eta), _ptr(psi), nrhs, info)
         infos = [i.as_dict() for i in info]
@@ -400,17 +400,17 @@ class Context:
         return psi, infos, st
 
     def solve_dhat(self, eta, solver=SOLVER_SAP_GCR, tol=1e-10, nkv=16, nmx=4096, bs=(4, 4, 4, 4), ncy=4, nmr=5,
-                   sap_prec=F64, inner=F64, check=True):
+                   sap_prec=F64, inner=F64, check=True, krylov=F64):
         return self._solve(lib().lqcd_solve_dhat, eta, self.Vh, solver, tol, nkv, nmx, bs, ncy, nmr, sap_prec,
-                           inner, check)
+                           inner, check, krylov)
 
     def solve_dhat_guess(self, eta, x0, solver=SOLVER_SAP_GCR, tol=1e-10, nkv=16, nmx=4096, bs=(4, 4, 4, 4),
-                         ncy=4, nmr=5, sap_prec=F64, inner=F64, check=True):
+                         ncy=4, nmr=5, sap_prec=F64, inner=F64, check=True, krylov=F64):
         """As solve_dhat, starting from the guess x0 (even fields)."""
         eta = eta.to(torch.complex128).contiguous()
         nrhs = self._nrhs(eta, self.Vh)
         psi = x0.to(torch.complex128).contiguous().clone()
-        p = SolverParams(solver, nkv, nmx, tol, sap_params(bs, ncy, nmr, sap_prec), inner)
+        p = SolverParams(solver, nkv, nmx, tol, sap_params(bs, ncy, nmr, sap_prec), inner, krylov)
         info = (SolveInfo * nrhs)()
         st = lib().lqcd_solve_dhat_guess(self._h, C.byref(p), _ptr(eta), _ptr(psi), nrhs, info)
         if check:
@@ -440,11 +440,11 @@ class Context:
         return out
 
     def solve_W(self, eta, dm, solver=SOLVER_SAP_GCR, tol=1e-10, nkv=16, nmx=4096, bs=(4, 4, 4, 4), ncy=4, nmr=5,
-                sap_prec=F64, inner=F64, check=True):
+                sap_prec=F64, inner=F64, check=True, krylov=F64):
         eta = eta.to(torch.complex128).contiguous()
         nrhs = self._nrhs(eta, self.Vh)
         psi = torch.empty_like(eta)
-        p = SolverParams(solver, nkv, nmx, tol, sap_params(bs, ncy, nmr, sap_prec), inner)
+        p = SolverParams(solver, nkv, nmx, tol, sap_params(bs, ncy, nmr, sap_prec), inner, krylov)
         info = (SolveInfo * nrhs)()
         st = lib().lqcd_solve_W(self._h, C.byref(p), float(dm), _ptr(eta), _ptr(psi), nrhs, info)
         if check:
@@ -452,9 +452,9 @@ class Context:
         return psi, [i.as_dict() for i in info], st
 
     def solve_D(self, eta, solver=SOLVER_SAP_GCR, tol=1e-10, nkv=16, nmx=4096, bs=(4, 4, 4, 4), ncy=4, nmr=5,
-                sap_prec=F64, inner=F64, check=True):
+                sap_prec=F64, inner=F64, check=True, krylov=F64):
         return self._solve(lib().lqcd_solve_D, eta, self.V, solver, tol, nkv, nmx, bs, ncy, nmr, sap_prec, inner,
-                           check)
+                           check, krylov)
 
 
 class Batch:

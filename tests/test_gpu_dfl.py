@@ -133,9 +133,11 @@ def test_fp32_coarse_solve():
     assert it > 0
     # several right-hand sides go through the coarse solve together inside the
     # deflated solve; every one reaches the FP64 true residual
+    # (FP64 and FP32 Krylov vectors in the outer GCR)
     eta = np.stack([synth.gaussian_spinor(P.Vh, 40 + k) for k in range(3)])
-    psi, info, st = P.ctx.solve_dhat(to_gpu(eta), solver=lqcd.SOLVER_DFL_SAP_GCR, tol=1e-10, sap_prec=lqcd.F32,
-                                     inner=lqcd.F32)
-    assert st == 0
-    for k in range(3):
-        assert util.relerr(P.o.Dhat(psi[k].cpu().numpy()), eta[k]) <= 1e-10
+    for krylov in (lqcd.F64, lqcd.F32):
+        psi, info, st = P.ctx.solve_dhat(to_gpu(eta), solver=lqcd.SOLVER_DFL_SAP_GCR, tol=1e-10, sap_prec=lqcd.F32,
+                                         inner=lqcd.F32, krylov=krylov)
+        assert st == 0
+        for k in range(3):
+            assert util.relerr(P.o.Dhat(psi[k].cpu().numpy()), eta[k]) <= 1e-10

@@ -164,13 +164,15 @@ def test_trained_net_gain(trained):
     assert np.all(r_net < 0.9 * r_id), (r_net, r_id)
 
 
-def test_net_gcr_solve(trained):
+@pytest.mark.parametrize("inner", [lqcd.F64, lqcd.F32], ids=["f64-krylov", "f32-krylov"])
+def test_net_gcr_solve(trained, inner):
     """The network inside the flexible GCR: FP64 true residual at 1e-10, with
-    SAP taking over the steps where the network's direction is poor."""
+    SAP taking over the steps where the network's direction is poor (Krylov
+    vectors in FP64, or FP32 with the FP32 inner precision)."""
     P, _ = trained
     eta = torch.from_numpy(sources(P.V, 2, 600)).cuda()
     psi, infos, st = P.ctx.solve_D(eta, solver=lqcd.SOLVER_NET_GCR, tol=1e-10, nkv=16, nmx=2000,
-                                   sap_prec=lqcd.F32)
+                                   sap_prec=lqcd.F32, inner=inner, krylov=inner)
     assert st == 0
     for k, inf in enumerate(infos):
         assert inf["true_relres"] <= 1e-10

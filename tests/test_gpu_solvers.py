@@ -72,6 +72,38 @@ def test_sap_gcr_f16s_sap(p8):
         assert util.relerr(P.o.Dhat(x[k]), eta[k]) <= 1e-10
 
 
+@pytest.mark.parametrize("sap_prec", [lqcd.F32, lqcd.F16S], ids=["f32-sap", "f16s-sap"])
+def test_sap_gcr_fp32_krylov(p8, sap_prec):
+    """GCR with FP32 Krylov vectors and Gram-Schmidt (FP64 residual, solution and
+    restarts): three sources, one of them zero, each reaches the FP64 true
+    residual; the full-lattice solve too."""
+    P = p8
+    eta = synth.gaussian_spinor(3 * P.Vh, 23).reshape(3, P.Vh, 4, 3)
+    eta[1] = 0
+    psi, info, st = P.ctx.solve_dhat(to_gpu(eta), solver=lqcd.SOLVER_SAP_GCR, tol=1e-10, nkv=16, nmx=2000,
+                                     sap_prec=sap_prec, inner=lqcd.F32, krylov=lqcd.F32)
+    assert st == 0
+    x = psi.cpu().numpy()
+    for k in (0, 2):
+        assert util.relerr(P.o.Dhat(x[k]), eta[k]) <= 1e-10
+    assert np.all(x[1] == 0)
+    e = synth.gaussian_spinor(P.V, 24)
+    psi, info, st = P.ctx.solve_D(to_gpu(e), solver=lqcd.SOLVER_SAP_GCR, tol=1e-10, sap_prec=sap_prec,
+                                  inner=lqcd.F32, krylov=lqcd.F32)
+    assert st == 0
+    assert util.relerr(P.o.D(psi.cpu().numpy()), e) <= 1e-10
+
+
+def test_krylov_precision_checked(p8):
+    """FP32 Krylov vectors need the FP32 inner precision; other precisions are refused."""
+    P = p8
+    eta = to_gpu(synth.gaussian_spinor(P.Vh, 25))
+    for inner, krylov in ((lqcd.F64, lqcd.F32), (lqcd.F32, lqcd.F16S), (lqcd.F32, 7)):
+        _, _, st = P.ctx.solve_dhat(eta, solver=lqcd.SOLVER_SAP_GCR, tol=1e-10, sap_prec=lqcd.F32, inner=inner,
+                                    krylov=krylov, check=False)
+        assert st == 1
+
+
 def test_sap_gcr_full_D(p8):
     P = p8
     eta = synth.gaussian_spinor(P.V, 4)
