@@ -311,9 +311,13 @@ __global__ void k_bmulti_axpy32(long n, int k, const __grid_constant__ CoefParam
                                 long sa, long fa, float4 *y, long fy, float sign)
 {
     const int r = blockIdx.y;
-    const double2 *c = cf.c + r * k;
     const float4 *Xr = X + r * fa;
     float4 *yr = y + r * fy;
+    // coefficients converted to float once per CTA (not per element on the FP64 pipe)
+    __shared__ float2 c[64];
+    for (int i = threadIdx.x; i < k; i += blockDim.x)
+        c[i] = make_float2((float)cf.c[r * k + i].x, (float)cf.c[r * k + i].y);
+    __syncthreads();
     for (long j = blockIdx.x * (long)blockDim.x + threadIdx.x; j < n; j += (long)gridDim.x * blockDim.x) {
         float4 b = yr[j];
         float s0 = 0, s1 = 0, s2 = 0, s3 = 0;
@@ -324,7 +328,7 @@ __global__ void k_bmulti_axpy32(long n, int k, const __grid_constant__ CoefParam
             for (int u = 0; u < 4; u++) a[u] = Xr[(i + u) * sa + j];
 #pragma unroll
             for (int u = 0; u < 4; u++) {
-                const float cr = (float)c[i + u].x, ci = (float)c[i + u].y;
+                const float cr = c[i + u].x, ci = c[i + u].y;
                 s0 += cr * a[u].x - ci * a[u].y;
                 s1 += cr * a[u].y + ci * a[u].x;
                 s2 += cr * a[u].z - ci * a[u].w;
@@ -333,7 +337,7 @@ __global__ void k_bmulti_axpy32(long n, int k, const __grid_constant__ CoefParam
         }
         for (; i < k; i++) {
             const float4 a = Xr[i * sa + j];
-            const float cr = (float)c[i].x, ci = (float)c[i].y;
+            const float cr = c[i].x, ci = c[i].y;
             s0 += cr * a.x - ci * a.y;
             s1 += cr * a.y + ci * a.x;
             s2 += cr * a.z - ci * a.w;
@@ -375,15 +379,18 @@ __global__ void k_bmulti_axpy_mixed(long Vh, int k, const __grid_constant__ Coef
                                     const float4 *__restrict__ X, long sa, long fa, double2 *y, long fy)
 {
     const int rh = blockIdx.y;
-    const double2 *c = cf.c + rh * k;
     const float4 *Xr = X + rh * fa;
     double2 *yr = y + rh * fy;
+    __shared__ float2 c[64];
+    for (int i = threadIdx.x; i < k; i += blockDim.x)
+        c[i] = make_float2((float)cf.c[rh * k + i].x, (float)cf.c[rh * k + i].y);
+    __syncthreads();
     for (long s = blockIdx.x * (long)blockDim.x + threadIdx.x; s < Vh; s += (long)gridDim.x * blockDim.x) {
         for (int p = 0; p < 12; p++) {
             float s0 = 0, s1 = 0, s2 = 0, s3 = 0;
             for (int i = 0; i < k; i++) {
                 const float4 a = Xr[i * sa + p * Vh + s];
-                const float cr = (float)c[i].x, ci = (float)c[i].y;
+                const float cr = c[i].x, ci = c[i].y;
                 s0 += cr * a.x - ci * a.y;
                 s1 += cr * a.y + ci * a.x;
                 s2 += cr * a.z - ci * a.w;

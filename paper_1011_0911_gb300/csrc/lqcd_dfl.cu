@@ -707,15 +707,19 @@ __global__ void k_fmulti_axpy(long n, int k, const double2 *__restrict__ cf, con
                               long fa, float2 *y, long fy, float sign)
 {
     const int r = blockIdx.y;
-    const double2 *c = cf + r * k;
     const float2 *Xr = X + r * fa;
     float2 *yr = y + r * fy;
+    // the coefficients converted to float once per CTA (a conversion per element
+    // would run on GB300's FP64 pipe)
+    __shared__ float2 cs[32];
+    for (int i = threadIdx.x; i < k; i += blockDim.x) cs[i] = make_float2((float)cf[r * k + i].x, (float)cf[r * k + i].y);
+    __syncthreads();
     for (long j = blockIdx.x * (long)blockDim.x + threadIdx.x; j < n; j += (long)gridDim.x * blockDim.x) {
         float2 b = yr[j];
         float sr = 0.f, si = 0.f;
         for (int i = 0; i < k; i++) {
             const float2 a = Xr[i * sa + j];
-            const float cx = (float)c[i].x, cy = (float)c[i].y;
+            const float cx = cs[i].x, cy = cs[i].y;
             sr += cx * a.x - cy * a.y;
             si += cx * a.y + cy * a.x;
         }

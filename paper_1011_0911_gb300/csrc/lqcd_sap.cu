@@ -12,6 +12,7 @@
 // H_blk keeps only hops whose both ends lie in the block (Dirichlet); a block
 // that spans a whole lattice direction keeps the wrapped hop of that direction.
 #include <algorithm>
+#include <type_traits>
 #include <vector>
 
 #include "lqcd_f16s.cuh"
@@ -523,11 +524,13 @@ __global__ void __launch_bounds__(128) k_sap_block(SapArgs<P> a)
 // as k_sap_block, different summation order.
 constexpr int SAPS_NH = 128;   // sites of one parity per block (4^4 blocks)
 
-// SA: the clover term of the block is staged in shared memory (184 KB, one
-// CTA per SM); without it (110 KB) two CTAs fit on an SM and every clover
-// application reads its 6x6 block through L1/L2 instead (same values).
-// staging loads of the resident kernel: one 4-real word of a link row pair or
-// of the clover term, and one site of a residual field
+// Shared memory of the resident block kernel.  SA: the clover term of the
+// block is staged too (172 KB, one CTA per SM); without it every clover
+// application reads its 6x6 block through L1/L2 (same values) and two FP32
+// CTAs (98 KB) or three F16S CTAs (74 KB: the links kept in FP16, the
+// precision they are stored in) fit on an SM.  The MinRes correction chi stays
+// in registers (each thread owns its half-site) and goes through p at the end.
+// staging loads: one 4-real word of a link row pair or of the clover term
 __device__ __forceinline__ float4 stage4(const float4 *p) { return __ldg(p); }
 __device__ __forceinline__ float4 stage4(const uint2 *p)
 {
@@ -535,21 +538,36 @@ __device__ __forceinline__ float4 stage4(const uint2 *p)
     cx<float> a = f16s_h2c(t.x, 1.f), b = f16s_h2c(t.y, 1.f);
     return make_float4(a.re, a.im, b.re, b.im);
 }
-template <bool SA>
-struct SapSmemT;
-template <>
-struct SapSmemT<true> {
+__device__ __forceinline__ void stage_link(float4 &d, const float4 *p) { d = __ldg(p); }
+__device__ __forceinline__ void stage_link(float4 &d, const uint2 *p) { d = stage4(p); }
+__device__ __forceinline__ void stage_link(uint2 &d, const uint2 *p) { d = __ldg(p); }
+__device__ __forceinline__ float4 link4(float4 v) { return v; }
+__device__ __forceinline__ float4 link4(uint2 t)
+{
+    cx<float> a = f16s_h2c(t.x, 1.f), b = f16s_h2c(t.y, 1.f);
+    return make_float4(a.re, a.im, b.re, b.im);
+}
+struct SapSmemA {
     float4 U[4][3][2 * SAPS_NH];   // forward links, two rows, site par * SAPS_NH + t
     float4 A[18][2 * SAPS_NH];     // A (even sites) or A^-1 (odd sites), site par * SAPS_NH + t
-    float4 rho[6][SAPS_NH], chi[6][SAPS_NH], p[6][SAPS_NH], to[6][SAPS_NH], ro[6][SAPS_NH];
+    float4 rho[6][SAPS_NH], p[6][SAPS_NH], to[6][SAPS_NH], ro[6][SAPS_NH];
     float red[3][8];
 };
-template <>
-struct SapSmemT<false> {
+struct SapSmemL {
     float4 U[4][3][2 * SAPS_NH];
-    float4 rho[6][SAPS_NH], chi[6][SAPS_NH], p[6][SAPS_NH], to[6][SAPS_NH], ro[6][SAPS_NH];
+    float4 rho[6][SAPS_NH], p[6][SAPS_NH], to[6][SAPS_NH], ro[6][SAPS_NH];
     float red[3][8];
 };
+struct SapSmemH {
+    uint2 U[4][3][2 * SAPS_NH];    // FP16 link rows
+    float4 rho[6][SAPS_NH], p[6][SAPS_NH], to[6][SAPS_NH], ro[6][SAPS_NH];
+    float red[3][8];
+};
+template <int P, bool SA>
+using SapSmem = std::conditional_t<SA, SapSmemA, std::conditional_t<P == LQCD_F16S, SapSmemH, SapSmemL>>;
+// resident CTAs per SM of each layout (the launch bounds)
+template <int P, bool SA>
+constexpr int sap_ctas() { return SA ? 1 : (P == LQCD_F16S ? 3 : 2); }
 
 __device__ __forceinline__ int blk_lex(const BlkGeom &B, const int l[4])
 {
@@ -583,7 +601,7 @@ __device__ __forceinline__ void s_link(const SM &S, int mu, int ls, cx<float> u[
 {
 #pragma unroll
     for (int q = 0; q < 3; q++) {
-        float4 a = S.U[mu][q][ls];
+        const float4 a = link4(S.U[mu][q][ls]);
         u[(2 * q) / 3][(2 * q) % 3] = mk(a.x, a.y);
         u[(2 * q + 1) / 3][(2 * q + 1) % 3] = mk(a.z, a.w);
     }
@@ -593,8 +611,8 @@ __device__ __forceinline__ void s_link(const SM &S, int mu, int ls, cx<float> u[
 }
 // one chirality block h of the clover matrix applied to v[6]; the block is
 // read from shared memory (local site ls) or from global memory (rank grank)
-template <bool SA, class CL>
-__device__ __forceinline__ void s_clover_half(const SapSmemT<SA> &S, int ls, const CL *A, long Vh, long grank, int h,
+template <bool SA, class SM, class CL>
+__device__ __forceinline__ void s_clover_half(const SM &S, int ls, const CL *A, long Vh, long grank, int h,
                                               const cx<float> v[6], cx<float> w[6])
 {
     float a[36];
@@ -746,7 +764,7 @@ __device__ __forceinline__ void sap_block_s_body(const SapArgs<P> &a, int bi, in
 {
     using SP = typename SapT<P>::SP;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    SapSmemT<SA> &S = *reinterpret_cast<SapSmemT<SA> *>(smem_raw);
+    SapSmem<P, SA> &S = *reinterpret_cast<SapSmem<P, SA> *>(smem_raw);
     const BlkGeom &B = a.B;
     const int nh = B.nh;
     const long Vh = a.g.Vh;
@@ -779,7 +797,7 @@ __device__ __forceinline__ void sap_block_s_body(const SapArgs<P> &a, int bi, in
 #pragma unroll
         for (int mu = 0; mu < 4; mu++)
 #pragma unroll
-            for (int q = 0; q < 3; q++) S.U[mu][q][ls] = stage4(a.U + ((long)(par * 4 + mu) * 3 + q) * Vh + s.grank);
+            for (int q = 0; q < 3; q++) stage_link(S.U[mu][q][ls], a.U + ((long)(par * 4 + mu) * 3 + q) * Vh + s.grank);
         if constexpr (SA) {
             const typename SapT<P>::CL *A = par ? a.Aio : a.Ae;
 #pragma unroll
@@ -792,10 +810,7 @@ __device__ __forceinline__ void sap_block_s_body(const SapArgs<P> &a, int bi, in
             for (int q = 0; q < 6; q++) S.ro[q][t] = site[q];
         } else {
 #pragma unroll
-            for (int q = 0; q < 6; q++) {
-                S.rho[q][t] = site[q];
-                S.chi[q][t] = make_float4(0.f, 0.f, 0.f, 0.f);
-            }
+            for (int q = 0; q < 6; q++) S.rho[q][t] = site[q];
         }
     }
     __syncthreads();
@@ -812,6 +827,9 @@ __device__ __forceinline__ void sap_block_s_body(const SapArgs<P> &a, int bi, in
         block_site(a.g, B, org, 0, t, se);
     }
     cx<float> acc[12], v[6], w[6];
+    float4 chi4[3];   // this thread's half of chi_e
+#pragma unroll
+    for (int q = 0; q < 3; q++) chi4[q] = make_float4(0.f, 0.f, 0.f, 0.f);
     // to = A_oo^-1 r_o (chirality half h)
     if (act) {
 #pragma unroll
@@ -897,7 +915,7 @@ __device__ __forceinline__ void sap_block_s_body(const SapArgs<P> &a, int bi, in
         if (act) {
 #pragma unroll
             for (int q = 0; q < 3; q++) {
-                float4 rv = S.rho[3 * h + q][t], pv = S.p[3 * h + q][t], cv = S.chi[3 * h + q][t];
+                float4 rv = S.rho[3 * h + q][t], pv = S.p[3 * h + q][t], cv = chi4[q];
                 // chi += alpha rho, rho -= alpha p
                 cv.x += ar * rv.x - ai * rv.y;
                 cv.y += ar * rv.y + ai * rv.x;
@@ -907,15 +925,20 @@ __device__ __forceinline__ void sap_block_s_body(const SapArgs<P> &a, int bi, in
                 rv.y -= ar * pv.y + ai * pv.x;
                 rv.z -= ar * pv.z - ai * pv.w;
                 rv.w -= ar * pv.w + ai * pv.z;
-                S.chi[3 * h + q][t] = cv;
+                chi4[q] = cv;
                 S.rho[3 * h + q][t] = rv;
             }
         }
         __syncthreads();
     }
     // chi_o = A_oo^-1 (r_o + 1/2 S(chi_e)); psi += chi; delta = chi; r <- (rho, 0)
+    // (chi_e goes to the block through p, which is free now)
+    if (act)
+#pragma unroll
+        for (int q = 0; q < 3; q++) S.p[3 * h + q][t] = chi4[q];
+    __syncthreads();
     if (act) {
-        s_hopsum(a.g, B, S, h, so.l, so.x, lso, S.chi, acc);
+        s_hopsum(a.g, B, S, h, so.l, so.x, lso, S.p, acc);
         cx<float> ah[6];
         s_half(acc, h, ah);
 #pragma unroll
@@ -928,7 +951,7 @@ __device__ __forceinline__ void sap_block_s_body(const SapArgs<P> &a, int bi, in
         cx<float> ce[6], re[6], zero[6];
 #pragma unroll
         for (int q = 0; q < 3; q++) {
-            const float4 c4 = S.chi[3 * h + q][t], r4 = S.rho[3 * h + q][t];
+            const float4 c4 = chi4[q], r4 = S.rho[3 * h + q][t];
             ce[2 * q] = mk(c4.x, c4.y);
             ce[2 * q + 1] = mk(c4.z, c4.w);
             re[2 * q] = mk(r4.x, r4.y);
@@ -945,7 +968,7 @@ __device__ __forceinline__ void sap_block_s_body(const SapArgs<P> &a, int bi, in
 }
 
 template <int P, bool SA>
-__global__ void __launch_bounds__(2 * SAPS_NH, SA ? 1 : 2) k_sap_block_s(SapArgs<P> a)
+__global__ void __launch_bounds__(2 * SAPS_NH, sap_ctas<P, SA>()) k_sap_block_s(SapArgs<P> a)
 {
     sap_block_s_body<P, SA>(a, blockIdx.x, blockIdx.y);
 }
@@ -1023,7 +1046,7 @@ __global__ void __launch_bounds__(128) k_sap_face(SapArgs<P> a, int col)
 // a device counter (*queue, zero before the launch) until the list is empty;
 // items of lattices whose active flag is 0 are skipped.
 template <int P, bool SA>
-__global__ void __launch_bounds__(2 * SAPS_NH, SA ? 1 : 2)
+__global__ void __launch_bounds__(2 * SAPS_NH, sap_ctas<P, SA>())
     k_sap_block_s_batch(const SapArgs<P> *args, int col, const int2 *items, int nitems, const int *active, int *queue)
 {
     __shared__ int s_item;
@@ -1165,9 +1188,9 @@ lqcd_status sap_run(lqcd_ctx *c, const SapPlan &P_, int ncy, int nmr, const void
         static bool attr_s = false;
         if (!attr_s) {
             cudaFuncSetAttribute(k_sap_block_s<P, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)sizeof(SapSmemT<true>));
+                                 (int)sizeof(SapSmem<P, true>));
             cudaFuncSetAttribute(k_sap_block_s<P, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)sizeof(SapSmemT<false>));
+                                 (int)sizeof(SapSmem<P, false>));
             attr_s = true;
         }
         resident = Pl.B.nh <= SAPS_NH && (2 * Pl.B.nh) % 32 == 0 && !sap_force_generic();
@@ -1181,10 +1204,10 @@ lqcd_status sap_run(lqcd_ctx *c, const SapPlan &P_, int ncy, int nmr, const void
             if constexpr (P != LQCD_F64) {
                 if (resident && sap_stage_clover())
                     k_sap_block_s<P, true>
-                        <<<dim3(Pl.count[col], nrhs), 2 * Pl.B.nh, sizeof(SapSmemT<true>), c->stream>>>(a);
+                        <<<dim3(Pl.count[col], nrhs), 2 * Pl.B.nh, sizeof(SapSmem<P, true>), c->stream>>>(a);
                 else if (resident)
                     k_sap_block_s<P, false>
-                        <<<dim3(Pl.count[col], nrhs), 2 * Pl.B.nh, sizeof(SapSmemT<false>), c->stream>>>(a);
+                        <<<dim3(Pl.count[col], nrhs), 2 * Pl.B.nh, sizeof(SapSmem<P, false>), c->stream>>>(a);
                 else
                     k_sap_block<P><<<dim3(Pl.count[col], nrhs), threads, smem, c->stream>>>(a);
             } else {
@@ -1334,9 +1357,9 @@ lqcd_status sap_batch_run(lqcd_ctx *hc, SapBatch *b, const int *active)
     static bool attr = false;
     if (!attr) {
         cudaFuncSetAttribute(k_sap_block_s_batch<P, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)sizeof(SapSmemT<true>));
+                             (int)sizeof(SapSmem<P, true>));
         cudaFuncSetAttribute(k_sap_block_s_batch<P, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)sizeof(SapSmemT<false>));
+                             (int)sizeof(SapSmem<P, false>));
         attr = true;
     }
     const bool sa = sap_stage_clover();
@@ -1346,12 +1369,12 @@ lqcd_status sap_batch_run(lqcd_ctx *hc, SapBatch *b, const int *active)
         for (int col = 0; col < 2; col++) {
             if (b->nblk[col] == 0) continue;
             if (sa)
-                k_sap_block_s_batch<P, true><<<std::min(b->nblk[col], b->nsm), 2 * b->nh, sizeof(SapSmemT<true>),
+                k_sap_block_s_batch<P, true><<<std::min(b->nblk[col], b->nsm), 2 * b->nh, sizeof(SapSmem<P, true>),
                                                hc->stream>>>(args, col, b->blk[col], b->nblk[col], active,
                                                              b->queue + 2 * cyc + col);
             else
-                k_sap_block_s_batch<P, false><<<std::min(b->nblk[col], 2 * b->nsm), 2 * b->nh,
-                                                sizeof(SapSmemT<false>), hc->stream>>>(
+                k_sap_block_s_batch<P, false><<<std::min(b->nblk[col], sap_ctas<P, false>() * b->nsm), 2 * b->nh,
+                                                sizeof(SapSmem<P, false>), hc->stream>>>(
                     args, col, b->blk[col], b->nblk[col], active, b->queue + 2 * cyc + col);
             hc->n_kernel_launches++;
             LQCD_LAUNCH_CHECK(hc);
