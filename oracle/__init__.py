@@ -53,6 +53,8 @@ def lib():
             "or_sap": (None, [P, IP, I, I, P, P]),
             "or_sap_block_solve": (None, [P, IP, LG, I, P, P]),
             "or_gcr": (I, [P, I, IP, I, I, I, I, D, P, P, IP, DP]),
+            "or_block_dhat": (None, [P, IP, P, P]),
+            "or_block_bicgstab": (I, [P, IP, P, P, D, I, IP, DP]),
             "or_dfl_build": (I, [P, IP, I, I, I, I, P]),
             "or_dfl_project": (None, [P, P, P]),
             "or_dfl_expand": (None, [P, P, P]),
@@ -210,6 +212,32 @@ class Oracle:
         chi = np.zeros_like(r)
         lib().or_sap_block_solve(self._o, self._bs(bs), int(blk), nmr, _p(r), _p(chi))
         return chi
+
+    # ---- DD-HMC block solves (Sec. 3)
+    def nblocks(self, bs):
+        n = 1
+        for L, b in zip(self.dims, bs):
+            n *= L // b
+        return n
+
+    def block_dhat(self, x_e, bs):
+        """Dhat_blk x_e on every Dirichlet block of extents bs (even half fields)."""
+        x_e = _c(x_e).reshape(self.Vh, 4, 3)
+        out = np.empty_like(x_e)
+        lib().or_block_dhat(self._o, self._bs(bs), _p(x_e), _p(out))
+        return out
+
+    def block_bicgstab(self, eta_e, bs, tol=1e-10, maxit=1000):
+        """BiCGstab on every block: (psi_e, status, iters[nblk], relres[nblk])."""
+        eta_e = _c(eta_e).reshape(self.Vh, 4, 3)
+        psi = np.empty_like(eta_e)
+        nb = self.nblocks(bs)
+        its = np.zeros(nb, dtype=np.int32)
+        rr = np.zeros(nb)
+        st = lib().or_block_bicgstab(self._o, self._bs(bs), _p(eta_e), _p(psi), tol, maxit,
+                                     its.ctypes.data_as(C.POINTER(C.c_int)),
+                                     rr.ctypes.data_as(C.POINTER(C.c_double)))
+        return psi, st, its, rr
 
     def gcr(self, eta, precond=1, bs=(4, 4, 4, 4), ncy=4, nmr=5, nkv=16, nmx=2048, tol=1e-10):
         eta = _c(eta).reshape(self.V, 4, 3)

@@ -93,6 +93,11 @@ void or_sap(const oracle *o, const int bs[4], int ncy, int nmr, const double *et
             double *psi);
 void or_sap_block_solve(const oracle *o, const int bs[4], long blk, int nmr,
                         const double *r, double *chi);
+/* DD-HMC block solves: Dhat_blk (Dirichlet blocks of extents bs) on even half
+ * fields, and BiCGstab on every block to tol (iters / relres per block) */
+void or_block_dhat(const oracle *o, const int bs[4], const double *in_e, double *out_e);
+int or_block_bicgstab(const oracle *o, const int bs[4], const double *eta_e, double *psi_e, double tol,
+                      int maxit, int *iters, double *relres);
 int or_gcr(const oracle *o, int precond, const int bs[4], int ncy, int nmr, int nkv, int nmx,
            double tol, const double *eta, double *psi, int *iters, double *relres);
 

@@ -225,6 +225,147 @@ void or_sap(const oracle *o, const int bs[4], int ncy, int nmr, const double *et
 }
 
 /* ------------------------------------------------------------------------ */
+/* DD-HMC block solves (Sec. 3: the inversions on the blocks needed for the   */
+/* block force F_1 use BiCGstab).  Every block's Dirichlet operator Dhat_blk  */
+/* is an independent system; BiCGstab (van der Vorst 1992) runs on each from */
+/* psi = 0 with rhat = r_0 = eta|_blk.                                        */
+
+/* out_e = Dhat_blk in_e on every block (even half fields, canonical rank order) */
+void or_block_dhat(const oracle *o, const int bs[4], const double *in_, double *out_)
+{
+    blocking B;
+    ob_load_gammas();
+    if (ob_make_blocking(o, bs, &B) != OR_OK) return;
+    const ocplx *in = (const ocplx *)in_;
+    ocplx *out = (ocplx *)out_;
+    long h = B.vol / 2, n = 12 * h;
+#pragma omp parallel for schedule(dynamic)
+    for (long b = 0; b < B.nblk; b++) {
+        ocplx *x = malloc(sizeof(ocplx) * n), *y = malloc(sizeof(ocplx) * n), *t = malloc(sizeof(ocplx) * n);
+        for (long k = 0; k < h; k++)
+            for (int i = 0; i < 12; i++) x[12 * k + i] = in[12 * o->rank[B.se[b * h + k]] + i];
+        block_dhat(o, &B, b, x, y, t);
+        for (long k = 0; k < h; k++)
+            for (int i = 0; i < 12; i++) out[12 * o->rank[B.se[b * h + k]] + i] = y[12 * k + i];
+        free(x);
+        free(y);
+        free(t);
+    }
+    ob_free_blocking(&B);
+}
+
+/* One block: BiCGstab steps in the order of the method,
+ *   rho = <rhat, r>, beta = (rho / rho_prev)(alpha / omega),
+ *   p = r + beta (p - omega v), v = A p, alpha = rho / <rhat, v>, s = r - alpha v,
+ *   (|s| <= tol |eta|: x += alpha p, done), t = A s, omega = <t, s> / <t, t>,
+ *   x += alpha p + omega s, r = s - omega t, converged when |r| <= tol |eta|.
+ * Returns the status; *iters the steps taken, *relres the recomputed residual. */
+static int block_bicgstab(const oracle *o, const blocking *B, long blk, const ocplx *eta, ocplx *x, double tol,
+                          int maxit, int *iters, double *relres)
+{
+    long h = B->vol / 2, n = 12 * h;
+    ocplx *r = malloc(sizeof(ocplx) * n), *rh = malloc(sizeof(ocplx) * n), *p = malloc(sizeof(ocplx) * n);
+    ocplx *v = malloc(sizeof(ocplx) * n), *sv = malloc(sizeof(ocplx) * n), *t = malloc(sizeof(ocplx) * n);
+    ocplx *tmp = malloc(sizeof(ocplx) * n);
+    double e2 = vnorm2(n, eta);
+    for (long i = 0; i < n; i++) {
+        x[i] = 0;
+        r[i] = eta[i];
+        rh[i] = eta[i];
+        p[i] = 0;
+        v[i] = 0;
+    }
+    ocplx rho_prev = 1, alpha = 1, omega = 1;
+    int it = 0, status = OR_ERR_NOT_CONVERGED;
+    if (e2 == 0) status = OR_OK;
+    while (status == OR_ERR_NOT_CONVERGED && it < maxit) {
+        ocplx rho = vdot(n, rh, r);
+        if (rho == 0) {
+            status = OR_ERR_BREAKDOWN;
+            break;
+        }
+        ocplx beta = (rho / rho_prev) * (alpha / omega);
+        for (long i = 0; i < n; i++) p[i] = r[i] + beta * (p[i] - omega * v[i]);
+        block_dhat(o, B, blk, p, v, tmp);
+        ocplx rv = vdot(n, rh, v);
+        if (rv == 0) {
+            status = OR_ERR_BREAKDOWN;
+            break;
+        }
+        alpha = rho / rv;
+        for (long i = 0; i < n; i++) sv[i] = r[i] - alpha * v[i];
+        it++;
+        if (vnorm2(n, sv) <= tol * tol * e2) {
+            vaxpy(n, alpha, p, x);
+            status = OR_OK;
+            break;
+        }
+        block_dhat(o, B, blk, sv, t, tmp);
+        double tt = vnorm2(n, t);
+        if (tt == 0) {
+            status = OR_ERR_BREAKDOWN;
+            break;
+        }
+        omega = vdot(n, t, sv) / tt;
+        for (long i = 0; i < n; i++) {
+            x[i] += alpha * p[i] + omega * sv[i];
+            r[i] = sv[i] - omega * t[i];
+        }
+        rho_prev = rho;
+        if (vnorm2(n, r) <= tol * tol * e2) status = OR_OK;
+    }
+    /* recomputed residual */
+    block_dhat(o, B, blk, x, t, tmp);
+    double r2 = 0;
+    for (long i = 0; i < n; i++) r2 += creal((eta[i] - t[i]) * conj(eta[i] - t[i]));
+    *iters = it;
+    *relres = e2 > 0 ? sqrt(r2 / e2) : 0;
+    free(r);
+    free(rh);
+    free(p);
+    free(v);
+    free(sv);
+    free(t);
+    free(tmp);
+    return status;
+}
+
+/* Dhat_blk psi_e = eta_e on every block; iters / relres per block (may be NULL).
+ * Returns the worst block status. */
+int or_block_bicgstab(const oracle *o, const int bs[4], const double *eta_, double *psi_, double tol, int maxit,
+                      int *iters, double *relres)
+{
+    blocking B;
+    ob_load_gammas();
+    if (ob_make_blocking(o, bs, &B) != OR_OK) return OR_ERR_ARG;
+    const ocplx *eta = (const ocplx *)eta_;
+    ocplx *psi = (ocplx *)psi_;
+    long h = B.vol / 2, n = 12 * h;
+    int *st = malloc(sizeof(int) * B.nblk);
+#pragma omp parallel for schedule(dynamic)
+    for (long b = 0; b < B.nblk; b++) {
+        ocplx *e = malloc(sizeof(ocplx) * n), *x = malloc(sizeof(ocplx) * n);
+        for (long k = 0; k < h; k++)
+            for (int i = 0; i < 12; i++) e[12 * k + i] = eta[12 * o->rank[B.se[b * h + k]] + i];
+        int it;
+        double rr;
+        st[b] = block_bicgstab(o, &B, b, e, x, tol, maxit, &it, &rr);
+        if (iters) iters[b] = it;
+        if (relres) relres[b] = rr;
+        for (long k = 0; k < h; k++)
+            for (int i = 0; i < 12; i++) psi[12 * o->rank[B.se[b * h + k]] + i] = x[12 * k + i];
+        free(e);
+        free(x);
+    }
+    int worst = OR_OK;
+    for (long b = 0; b < B.nblk; b++)
+        if (st[b] != OR_OK && worst == OR_OK) worst = st[b];
+    free(st);
+    ob_free_blocking(&B);
+    return worst;
+}
+
+/* ------------------------------------------------------------------------ */
 /* flexible GCR on the full lattice                                         */
 
 /* precond: 0 identity, 1 SAP, 2 deflated SAP (subspace built beforehand) */
