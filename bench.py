@@ -155,7 +155,7 @@ KAPPA_OF = {(8, 8, 8, 8): 0.1355, (32, 16, 16, 16): 0.1357, (48, 24, 24, 24): 0.
 
 
 def solve_once(ctx, lqcd, eta, solver, inner, Ns=20, ninv=8, ctol=1e-2, seed=100, cnmx=4096, cnkv=16, cprec=None,
-               nkv=16, sap_prec=None, krylov=None):
+               nkv=16, sap_prec=None, krylov=None, ncy=4, nmr=5):
     """Time-to-solution of Dhat psi = eta (all fields of eta) to 1e-10 with the
     given solver; the subspace build is timed separately and included in total."""
     import torch
@@ -181,7 +181,7 @@ def solve_once(ctx, lqcd, eta, solver, inner, Ns=20, ninv=8, ctol=1e-2, seed=100
     sp = prec if sap_prec is None else sap_prec
     kr = lqcd.F32 if krylov == "f32" else lqcd.F64
     psi, info, st = ctx.solve_dhat(eta, solver=sid, tol=1e-10, nmx=20000 if solver == "cgnr" else 4096,
-                                   nkv=nkv, sap_prec=sp, inner=prec, check=False, krylov=kr)
+                                   nkv=nkv, sap_prec=sp, inner=prec, check=False, krylov=kr, ncy=ncy, nmr=nmr)
     torch.cuda.synchronize()
     solve_s = time.perf_counter() - t0
     res.update({"krylov": "f32" if kr == lqcd.F32 else "f64",
@@ -315,9 +315,10 @@ def run_solve(args):
     for _ in range(2):
         res, _ = solve_once(ctx, lqcd, eta, args.solver, args.prec, Ns=args.Ns, ninv=args.ninv, ctol=args.ctol,
                             cnmx=args.cnmx, cnkv=args.cnkv, cprec=args.cprec, nkv=args.nkv,
-                            krylov=args.krylov,
+                            krylov=args.krylov, ncy=args.ncy, nmr=args.nmr,
                             sap_prec={"f16s": lqcd.F16S, "f32": lqcd.F32, "f64": lqcd.F64}.get(args.sap_prec))
     res["nkv"] = args.nkv
+    res["ncy"], res["nmr"] = args.ncy, args.nmr
     res["sap_prec"] = args.sap_prec or args.prec
     res.update({"mode": "solve", "lattice": args.lattice, "kappa": kappa})
     print(json.dumps(res))
@@ -463,6 +464,48 @@ def run_net(args):
     print(json.dumps(out))
 
 
+def run_block(args):
+    """DD-HMC block solves (Sec. 3): BiCGstab on every Dirichlet block of
+    extents --bs (the paper's 6^2 x 12^2 at 48x24^3), one Gaussian source, FP64,
+    tolerance 1e-10 per block.  One warm-up solve of two steps first.  The
+    oracle's block operator is timed on the host cores for one application and
+    scaled by the operator applications the GPU solve made (the oracle's solve
+    itself takes minutes at this size)."""
+    import torch
+    import oracle as orc
+    from paper_1011_0911_gb300 import lqcd, synth
+    kappa = args.kappa or KAPPA_OF.get(DIMS, 0.1355)
+    bs = tuple(int(v) for v in args.bs.split(","))
+    U = synth.su3_links(DIMS, 0)
+    ctx = lqcd.Context(DIMS)
+    ctx.set_gauge(torch.from_numpy(U).cuda())
+    ctx.clover_invert(kappa, CSW)
+    eta_h = synth.gaussian_spinor(ctx.Vh, 1)
+    eta = torch.from_numpy(eta_h).cuda()
+    ctx.block_solve(eta, bs, tol=1e-10, nmx=2, check=False)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    psi, st, its, rr, sts = ctx.block_solve(eta, bs, tol=1e-10, nmx=1000, check=False)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    napp = 2 * int(its.max()) + 1   # lockstep: two block operators per step, one residual check
+    out = {"mode": "block", "lattice": args.lattice, "kappa": kappa, "bs": list(bs), "nblk": int(len(its)),
+           "status": int(st), "seconds": round(dt, 4), "iters_max": int(its.max()),
+           "iters_mean": round(float(its.mean()), 1), "max_relres": float(rr.max()),
+           "dhat_blk_applications": napp,
+           "gflops": round(napp * FLOP_PER_SITE * ctx.Vh / dt / 1e9, 2)}
+    if not args.no_cpu_baseline:
+        o = orc.Oracle(DIMS, U, kappa, CSW)
+        t0 = time.perf_counter()
+        o.block_dhat(eta_h, bs)
+        t1 = time.perf_counter() - t0
+        out["cpu_baseline"] = {"kind": "oracle", "cores": orc.num_threads(),
+                               "sample": "one application of the block operator on all blocks, scaled by the "
+                                         "GPU solve's operator applications",
+                               "seconds_per_application": round(t1, 3), "seconds_extrapolated": round(t1 * napp, 1)}
+    print(json.dumps(out))
+
+
 def run_configs(args):
     """The small configurations: Dhat per precision (one field, native
     resident, CUDA events) at 8^4 and 32x16^3, the 8^4 FP64 CGNR solve and the
@@ -584,7 +627,7 @@ def main():
     ap.add_argument("--no-solve", action="store_true", help="skip the time-to-solution comparison")
     ap.add_argument("--no-net", action="store_true", help="time-to-solution without the learned form")
     ap.add_argument("--lattice", default="48x24x24x24", help="TxL1xL2xL3 (profiling runs use smaller ones)")
-    ap.add_argument("--mode", default="dhat", choices=["dhat", "solve", "batch", "net", "configs"],
+    ap.add_argument("--mode", default="dhat", choices=["dhat", "solve", "batch", "net", "configs", "block"],
                     help="solve: one time-to-solution run; batch: the uneven multi-lattice batch")
     ap.add_argument("--nlat", type=int, default=16, help="lattices of the batch mode")
     ap.add_argument("--nfields", type=int, default=10, help="net mode: training gauge fields")
@@ -602,6 +645,9 @@ def main():
     ap.add_argument("--krylov", default=None, choices=["f32", "f64"],
                     help="GCR Krylov-vector precision (f32 needs --prec f32)")
     ap.add_argument("--nkv", type=int, default=16, help="solve mode: GCR Krylov vectors per cycle")
+    ap.add_argument("--bs", default="6,6,12,12", help="block mode: Dirichlet block extents")
+    ap.add_argument("--ncy", type=int, default=4, help="solve mode: SAP cycles per preconditioner application")
+    ap.add_argument("--nmr", type=int, default=5, help="solve mode: MinRes steps per SAP block solve")
     ap.add_argument("--sap-prec", default=None, choices=["f16s", "f32", "f64"], help="solve mode: SAP precision")
     args = ap.parse_args()
     global DIMS
@@ -616,6 +662,8 @@ def main():
         return run_net(args)
     if args.mode == "configs":
         return run_configs(args)
+    if args.mode == "block":
+        return run_block(args)
 
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))

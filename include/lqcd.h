@@ -348,6 +348,35 @@ LQCD_API lqcd_status lqcd_apply_W(lqcd_ctx *ctx, lqcd_prec prec, double dm, cons
 LQCD_API lqcd_status lqcd_solve_W(lqcd_ctx *ctx, const lqcd_solver_params *p, double dm, const double *eta_dev,
                                   double *psi_dev, int nrhs, lqcd_solve_info *info);
 
+/* ------------------------------------------------------ DD-HMC block solves */
+/* Sec. 3: the inversions on the blocks needed for the DD-HMC block force use
+ * BiCGstab.  The lattice is cut into Dirichlet blocks of extents bs (even,
+ * tiling the lattice; 6,6,12,12 in the paper's 48x24^3 runs): hops whose
+ * other end lies in another block are dropped, a block that spans a whole
+ * direction keeps the wrapped hop.  Each block's Schur operator
+ * Dhat_blk = A_ee - H_eo,blk A_oo^-1 H_oe,blk is an independent system.
+ * Blocks are numbered lexicographically in their block coordinates
+ * (b = c3 + nb3 (c2 + nb2 (c1 + nb1 c0)), nb = L / bs).  FP64. */
+typedef struct {
+    int bs[4];    /* block extents */
+    double tol;   /* per block: |eta_b - Dhat_blk psi_b| <= tol |eta_b| */
+    int nmx;      /* BiCGstab iterations per block at most (>= 0) */
+} lqcd_block_params;
+
+/* Number of blocks of extents bs, or -1 if bs does not tile the lattice. */
+LQCD_API long lqcd_block_count(const lqcd_ctx *ctx, const int bs[4]);
+/* out = Dhat_blk in on every block: one canonical FP64 even field (device). */
+LQCD_API lqcd_status lqcd_apply_Dhat_block(lqcd_ctx *ctx, const int bs[4], const double *in_dev, double *out_dev);
+/* Solve Dhat_blk psi = eta on every block by BiCGstab from psi = 0 (all
+ * blocks in lockstep; a converged block takes no further updates).
+ * eta_dev, psi_dev: one canonical FP64 even field each (device).  iters,
+ * relres, status: optional host arrays of lqcd_block_count entries receiving
+ * each block's steps, recomputed relative residual and status (LQCD_OK,
+ * LQCD_ERR_NOT_CONVERGED, LQCD_ERR_BREAKDOWN, LQCD_ERR_NAN).  Returns the
+ * first non-OK block status, LQCD_OK when every block converged. */
+LQCD_API lqcd_status lqcd_block_solve(lqcd_ctx *ctx, const lqcd_block_params *p, const double *eta_dev,
+                                      double *psi_dev, int *iters, double *relres, int *status);
+
 /* ------------------------------------------------ batched multi-lattice solve */
 /* Several independent lattices (each its own context: gauge field, kappa,
  * clover term) solved together with the SAP-preconditioned flexible GCR of

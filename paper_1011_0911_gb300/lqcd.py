@@ -60,6 +60,10 @@ class SolveInfo(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class BlockParams(C.Structure):
+    _fields_ = [("bs", C.c_int * 4), ("tol", C.c_double), ("nmx", C.c_int)]
+
+
 class BatchParams(C.Structure):
     _fields_ = [("nkv", C.c_int), ("nmx", C.c_int), ("tol", C.c_double), ("sap", SapParams),
                 ("use_graph", C.c_int), ("wait_timeout_s", C.c_double), ("stall_test", C.c_int)]
@@ -125,6 +129,8 @@ def lib():
             "lqcd_chrono_add": [P, P],
             "lqcd_chrono_guess": [P, P, P, C.POINTER(I)],
             "lqcd_solve_W": [P, C.POINTER(SolverParams), D, P, P, I, C.POINTER(SolveInfo)],
+            "lqcd_apply_Dhat_block": [P, C.POINTER(I), P, P],
+            "lqcd_block_solve": [P, C.POINTER(BlockParams), P, P, C.POINTER(I), C.POINTER(D), C.POINTER(I)],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -134,6 +140,8 @@ def lib():
         L.lqcd_last_error.restype = C.c_char_p
         L.lqcd_native_bytes.argtypes = [P, I, I, I]
         L.lqcd_native_bytes.restype = S
+        L.lqcd_block_count.argtypes = [P, C.POINTER(I)]
+        L.lqcd_block_count.restype = C.c_long
         L.lqcd_kernel_launches.argtypes = [P]
         L.lqcd_kernel_launches.restype = C.c_long
         L.lqcd_dfl_stats.argtypes = [P, C.POINTER(C.c_long), C.POINTER(C.c_long)]
@@ -430,6 +438,36 @@ class Context:
         n = C.c_int()
         self._check(lib().lqcd_chrono_guess(self._h, _ptr(eta), _ptr(x0), C.byref(n)), "chrono_guess")
         return x0, n.value
+
+    # ------------------------------------------------- DD-HMC block solves
+    def block_count(self, bs) -> int:
+        return int(lib().lqcd_block_count(self._h, (C.c_int * 4)(*bs)))
+
+    def apply_Dhat_block(self, x: torch.Tensor, bs) -> torch.Tensor:
+        """Dhat_blk x on every Dirichlet block of extents bs (one even FP64 field)."""
+        x = x.to(torch.complex128).contiguous()
+        out = torch.empty_like(x)
+        self._check(lib().lqcd_apply_Dhat_block(self._h, (C.c_int * 4)(*bs), _ptr(x), _ptr(out)), "apply_Dhat_block")
+        return out
+
+    def block_solve(self, eta: torch.Tensor, bs, tol=1e-10, nmx=1000, check=True):
+        """BiCGstab on every block: (psi, status, iters[nblk], relres[nblk], status[nblk])."""
+        import numpy as np
+        eta = eta.to(torch.complex128).contiguous()
+        psi = torch.empty_like(eta)
+        nb = self.block_count(bs)
+        if nb < 1:
+            raise LqcdError(1, "block extents %s do not tile the lattice" % (tuple(bs),))
+        its = np.zeros(nb, dtype=np.int32)
+        rr = np.zeros(nb)
+        sts = np.zeros(nb, dtype=np.int32)
+        p = BlockParams((C.c_int * 4)(*bs), tol, nmx)
+        st = lib().lqcd_block_solve(self._h, C.byref(p), _ptr(eta), _ptr(psi),
+                                    its.ctypes.data_as(C.POINTER(C.c_int)), rr.ctypes.data_as(C.POINTER(C.c_double)),
+                                    sts.ctypes.data_as(C.POINTER(C.c_int)))
+        if check:
+            self._check(st, "block_solve")
+        return psi, st, its, rr, sts
 
     def apply_W(self, x: torch.Tensor, dm: float, prec=F64) -> torch.Tensor:
         """Hasenbusch operator W(dm) = Q_S + dm on even fields (Eq. 3)."""
