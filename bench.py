@@ -155,7 +155,7 @@ KAPPA_OF = {(8, 8, 8, 8): 0.1355, (32, 16, 16, 16): 0.1357, (48, 24, 24, 24): 0.
 
 
 def solve_once(ctx, lqcd, eta, solver, inner, Ns=20, ninv=8, ctol=1e-2, seed=100, cnmx=4096, cnkv=16, cprec=None,
-               nkv=16, sap_prec=None, krylov=None, ncy=4, nmr=5):
+               nkv=16, sap_prec=None, krylov=None, ncy=4, nmr=5, bncy=4, bnmr=4):
     """Time-to-solution of Dhat psi = eta (all fields of eta) to 1e-10 with the
     given solver; the subspace build is timed separately and included in total."""
     import torch
@@ -170,11 +170,12 @@ def solve_once(ctx, lqcd, eta, solver, inner, Ns=20, ninv=8, ctol=1e-2, seed=100
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         cp = prec if cprec is None else (lqcd.F32 if cprec == "f32" else lqcd.F64)
-        ctx.dfl_build(v0, bs=(4, 4, 4, 4), ninv=ninv, ncy=4, nmr=4, prec=prec, coarse_tol=ctol, coarse_nkv=cnkv,
-                      coarse_nmx=cnmx, coarse_prec=cp)
+        ctx.dfl_build(v0, bs=(4, 4, 4, 4), ninv=ninv, ncy=bncy, nmr=bnmr, prec=prec, coarse_tol=ctol,
+                      coarse_nkv=cnkv, coarse_nmx=cnmx, coarse_prec=cp)
         torch.cuda.synchronize()
         build_s = time.perf_counter() - t0
-        res.update({"Ns": Ns, "ninv": ninv, "coarse_tol": ctol, "coarse_nmx": cnmx, "coarse_nkv": cnkv,
+        res.update({"Ns": Ns, "ninv": ninv, "build_sap": [bncy, bnmr], "coarse_tol": ctol, "coarse_nmx": cnmx,
+                    "coarse_nkv": cnkv,
                     "coarse_prec": "f32" if cp == lqcd.F32 else "f64", "build_s": round(build_s, 4)})
     sid = {"cgnr": lqcd.SOLVER_CGNR, "sap": lqcd.SOLVER_SAP_GCR, "dfl": lqcd.SOLVER_DFL_SAP_GCR}[solver]
     t0 = time.perf_counter()
@@ -317,7 +318,7 @@ def run_solve(args):
     for _ in range(2):
         res, _ = solve_once(ctx, lqcd, eta, args.solver, args.prec, Ns=args.Ns, ninv=args.ninv, ctol=args.ctol,
                             cnmx=args.cnmx, cnkv=args.cnkv, cprec=args.cprec, nkv=args.nkv,
-                            krylov=args.krylov, ncy=args.ncy, nmr=args.nmr,
+                            krylov=args.krylov, ncy=args.ncy, nmr=args.nmr, bncy=args.bncy, bnmr=args.bnmr,
                             sap_prec={"f16s": lqcd.F16S, "f32": lqcd.F32, "f64": lqcd.F64}.get(args.sap_prec))
     res["nkv"] = args.nkv
     res["ncy"], res["nmr"] = args.ncy, args.nmr
@@ -650,6 +651,8 @@ def main():
     ap.add_argument("--bs", default="6,6,12,12", help="block mode: Dirichlet block extents")
     ap.add_argument("--ncy", type=int, default=4, help="solve mode: SAP cycles per preconditioner application")
     ap.add_argument("--nmr", type=int, default=5, help="solve mode: MinRes steps per SAP block solve")
+    ap.add_argument("--bncy", type=int, default=4, help="solve mode: SAP cycles in the subspace build")
+    ap.add_argument("--bnmr", type=int, default=4, help="solve mode: SAP MinRes steps in the subspace build")
     ap.add_argument("--sap-prec", default=None, choices=["f16s", "f32", "f64"], help="solve mode: SAP precision")
     args = ap.parse_args()
     global DIMS
