@@ -54,6 +54,9 @@ def lib():
             "or_sap_block_solve": (None, [P, IP, LG, I, P, P]),
             "or_gcr": (I, [P, I, IP, I, I, I, I, D, P, P, IP, DP]),
             "or_block_dhat": (None, [P, IP, P, P]),
+            "or_dD_apply": (None, [P, LG, I, I, P, P]),
+            "or_force_dD": (None, [P, P, P, P]),
+            "or_force_logdet": (None, [P, I, P]),
             "or_block_bicgstab": (I, [P, IP, P, P, D, I, IP, DP]),
             "or_dfl_build": (I, [P, IP, I, I, I, I, P]),
             "or_dfl_project": (None, [P, P, P]),
@@ -212,6 +215,136 @@ class Oracle:
         chi = np.zeros_like(r)
         lib().or_sap_block_solve(self._o, self._bs(bs), int(blk), nmr, _p(r), _p(chi))
         return chi
+
+    # ---- Lie derivatives and MD force gradients (Sec. 2, Eq. 4)
+    # A link moves along U_mu(x) -> exp(eps T_a) U_mu(x), T_a = i lambda_a / 2; gradients
+    # are dS/d eps in arrays [V][4][8] (the MD force is minus the gradient).
+    def dD_apply(self, x, site, mu, a):
+        """(dD/d eps) x for the link (site, mu) moved along T_a (full fields)."""
+        x = _c(x).reshape(self.V, 4, 3)
+        out = np.empty_like(x)
+        lib().or_dD_apply(self._o, int(site), int(mu), int(a), _p(x), _p(out))
+        return out
+
+    def force_dD(self, X, Y):
+        """Re <Y, (dD/d eps) X> for every link and generator."""
+        X = _c(X).reshape(self.V, 4, 3)
+        Y = _c(Y).reshape(self.V, 4, 3)
+        g = np.empty((self.V, 4, 8))
+        lib().or_force_dD(self._o, _p(X), _p(Y), _p(g))
+        return g
+
+    def grad_logdet(self, parity):
+        """d log|det A_parity| / d eps (the clover term of Eq. 4 is -2 x this, summed over parities)."""
+        g = np.empty((self.V, 4, 8))
+        lib().or_force_logdet(self._o, int(parity), _p(g))
+        return g
+
+    def _full(self, xe, xo=None):
+        f = np.zeros((self.V, 4, 3), dtype=np.complex128)
+        f[self.even_sites()] = np.asarray(xe).reshape(self.Vh, 4, 3)
+        if xo is not None:
+            f[self.odd_sites()] = np.asarray(xo).reshape(self.Vh, 4, 3)
+        return f
+
+    def _g5(self, x):
+        y = np.array(x, dtype=np.complex128, copy=True)
+        y[..., 2:, :] *= -1
+        return y
+
+    def _complete_x(self, xe):
+        """(x_e, -A_oo^-1 H_oe x_e): D of it is (Dhat x_e, 0)."""
+        h = self.hop(self._full(xe))
+        t = np.zeros_like(h)
+        t[self.odd_sites()] = h[self.odd_sites()]
+        xo = -self.clover(t, inverse=True)[self.odd_sites()]
+        return self._full(xe, xo)
+
+    def _complete_y(self, ye):
+        """(y_e, -A_oo^-1 H_eo^dag y_e), with H^dag = gamma5 H gamma5: <y, dD x> = <y_e, dDhat x_e>."""
+        h = self._g5(self.hop(self._g5(self._full(ye))))
+        t = np.zeros_like(h)
+        t[self.odd_sites()] = h[self.odd_sites()]
+        yo = -self.clover(t, inverse=True)[self.odd_sites()]
+        return self._full(ye, yo)
+
+    def dhat_inv(self, eta_e, tol=1e-13):
+        psi, st, _ = self.cgnr(eta_e, tol=tol, maxit=100000)
+        assert st == 0
+        return psi
+
+    def grad_pf(self, phi_e):
+        """d/d eps |Dhat^-1 phi_e|^2 = -2 Re <Y, dDhat X>, X = Dhat^-1 phi, Y = Dhat^-dag X."""
+        xe = self.dhat_inv(phi_e)
+        ye = self._g5(self.dhat_inv(self._g5(xe)))
+        return -2.0 * self.force_dD(self._complete_x(xe), self._complete_y(ye))
+
+    # W(dm) = A_ee^-1 Dhat + dm (Eq. 3) and its adjoint Dhat^dag A_ee^-1 + dm on even fields
+    def _aee(self, xe, inverse=False):
+        return self.clover(self._full(xe), inverse=inverse)[self.even_sites()]
+
+    def _w_dag(self, xe, dm):
+        return self._g5(self.Dhat(self._g5(self._aee(xe, inverse=True)))) + dm * np.asarray(xe).reshape(self.Vh, 4, 3)
+
+    def w_inv(self, eta_e, dm, tol=1e-13, maxit=100000):
+        """W(dm)^-1 eta by CG on W^dag W (plain, for the force pins)."""
+        b = self._w_dag(eta_e, dm).ravel()
+        x = np.zeros_like(b)
+        r = b.copy()
+        p = r.copy()
+        rr = np.vdot(r, r).real
+        b2 = rr
+        for _ in range(maxit):
+            if rr <= tol * tol * b2:
+                break
+            q = self._w_dag(self.W(p, dm), dm).ravel()
+            al = rr / np.vdot(p, q).real
+            x += al * p
+            r -= al * q
+            rn = np.vdot(r, r).real
+            p = r + (rn / rr) * p
+            rr = rn
+        return x.reshape(self.Vh, 4, 3)
+
+    def w_dag_inv(self, eta_e, dm):
+        """W(dm)^-dag eta = W (W^dag W)^-1 eta, by CG on W^dag W (plain, for the force pins)."""
+        b = np.asarray(eta_e, dtype=np.complex128).ravel()
+        y = np.zeros_like(b)
+        r = b.copy()
+        p = r.copy()
+        rr = np.vdot(r, r).real
+        b2 = rr
+        for _ in range(100000):
+            if rr <= 1e-26 * b2:
+                break
+            q = self._w_dag(self.W(p, dm), dm).ravel()
+            al = rr / np.vdot(p, q).real
+            y += al * p
+            r -= al * q
+            rn = np.vdot(r, r).real
+            p = r + (rn / rr) * p
+            rr = rn
+        return self.W(y.reshape(self.Vh, 4, 3), dm)
+
+    def _grad_qs(self, u, z):
+        """Re <z, dQ_S u> for even fields, Q_S = A_ee^-1 Dhat:
+        dQ_S = A_ee^-1 (dDhat - dA_ee Q_S), so <z, dQ_S u> = <A_ee^-1 z, dDhat u> - <A_ee^-1 z, dA_ee Q_S u>."""
+        zz = self._aee(z, inverse=True)
+        v = self.W(u, 0.0)
+        return (self.force_dD(self._complete_x(u), self._complete_y(zz))
+                - self.force_dD(self._full(v), self._full(zz)))
+
+    def grad_w1(self, phi_e, dm):
+        """d/d eps |W(dm)^-1 phi|^2 (the F1 term of Eq. 4) = -2 Re <W^-dag X, dQ_S X>, X = W^-1 phi."""
+        x = self.w_inv(phi_e, dm)
+        return -2.0 * self._grad_qs(x, self.w_dag_inv(x, dm))
+
+    def grad_w2(self, phi_e, dm):
+        """d/d eps |(1 + dm / Q_S) phi|^2 (the F2 term of Eq. 4): with u = Q_S^-1 phi, v = W(dm) u,
+        dv = -dm Q_S^-1 dQ_S u, so the gradient is -2 dm Re <Q_S^-dag v, dQ_S u>."""
+        u = self.w_inv(phi_e, 0.0)
+        v = self.W(u, dm)
+        return -2.0 * dm * self._grad_qs(u, self.w_dag_inv(v, 0.0))
 
     # ---- DD-HMC block solves (Sec. 3)
     def nblocks(self, bs):

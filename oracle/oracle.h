@@ -86,6 +86,13 @@ void or_d_site(const oracle *o, const double *in, long x, double *out12);
 long or_even_rank_to_site(const oracle *o, int parity, long r);
 int or_num_threads(void);
 
+/* --- Lie derivatives for the MD forces (Sec. 2, Eq. 4), oracle_dirac.c ---
+ * The link U_mu(x) moves along exp(eps T_a) U_mu(x), T_a = i lambda_a / 2.
+ * or_dD_apply: out = (dD/d eps) in (full fields).  Arrays g hold [V][4][8]. */
+void or_dD_apply(const oracle *o, long x, int mu, int a, const double *in, double *out);
+void or_force_dD(const oracle *o, const double *X, const double *Y, double *g);   /* Re <Y, dD X> */
+void or_force_logdet(const oracle *o, int parity, double *g);                     /* d log|det A_p| */
+
 /* --- solvers (oracle_solvers.c) --- */
 int or_cgnr(const oracle *o, const double *eta_e, double *psi_e, double tol, int maxit,
             int *iters);

@@ -591,3 +591,186 @@ int or_num_threads(void)
     return 1;
 #endif
 }
+
+/* ------------------------------------------------------------------------ */
+/* Lie derivatives for the molecular-dynamics forces (Sec. 2, Eq. 4: the    */
+/* forces F1, F2 of the pseudofermion terms and of the clover log det).     */
+/* A link is moved along U_mu(x) -> exp(eps T_a) U_mu(x), T_a = i lambda_a/2 */
+/* (Gell-Mann lambda_a); the derivative at eps = 0 replaces the link by     */
+/* dU = T_a U_mu(x), and its adjoint by dU^dag = -U^dag T_a.  D is a sum of */
+/* products in which a given link occurs at most once per term (every      */
+/* clover leaf holds four distinct links when all extents are >= 2), so the */
+/* derivative of a term is the term with that one factor replaced.          */
+
+/* T_a = i lambda_a / 2, a = 0..7 for lambda_1..lambda_8 */
+static void gen_T(int a, ocplx *T)
+{
+    for (int i = 0; i < 9; i++) T[i] = 0;
+    ocplx h = 0.5 * I;
+    switch (a) {
+        case 0: T[1] = T[3] = h; break;                          /* lambda_1 */
+        case 1: T[1] = -I * h; T[3] = I * h; break;               /* lambda_2 */
+        case 2: T[0] = h; T[4] = -h; break;                       /* lambda_3 */
+        case 3: T[2] = T[6] = h; break;                           /* lambda_4 */
+        case 4: T[2] = -I * h; T[6] = I * h; break;               /* lambda_5 */
+        case 5: T[5] = T[7] = h; break;                           /* lambda_6 */
+        case 6: T[5] = -I * h; T[7] = I * h; break;               /* lambda_7 */
+        default: {                                                /* lambda_8 */
+            double r = 1.0 / sqrt(3.0);
+            T[0] = T[4] = h * r;
+            T[8] = -2.0 * h * r;
+        }
+    }
+}
+
+/* the moved link: (px, pmu) and dU = T_a U_pmu(px) */
+typedef struct {
+    long px;
+    int pmu;
+    ocplx dU[9];
+} or_pert;
+
+/* derivative of the product f0 f1 f2 f3 of links (site s[i], direction d[i],
+ * adjoint if g[i]); returns 0 (and leaves out untouched) if the moved link
+ * is not a factor */
+static int leaf_deriv(const oracle *o, const long s[4], const int d[4], const int g[4], const or_pert *P,
+                      ocplx *out)
+{
+    int k = -1;
+    for (int i = 0; i < 4; i++)
+        if (s[i] == P->px && d[i] == P->pmu) k = i;
+    if (k < 0) return 0;
+    ocplx f[4][9];
+    for (int i = 0; i < 4; i++) {
+        const ocplx *M = i == k ? P->dU : link(o, s[i], d[i]);
+        if (g[i])
+            dag(M, f[i]);
+        else
+            for (int j = 0; j < 9; j++) f[i][j] = M[j];
+    }
+    mm4(f[0], f[1], f[2], f[3], out);
+    return 1;
+}
+
+/* d Fhat_{mu nu}(x): the four leaves of or_fhat_site, differentiated */
+static int dfhat_site(const oracle *o, long x, int mu, int nu, const or_pert *P, ocplx *dF)
+{
+    long xpm = o->fw[4 * x + mu], xpn = o->fw[4 * x + nu];
+    long xmm = o->bw[4 * x + mu], xmn = o->bw[4 * x + nu];
+    long xmm_pn = o->fw[4 * xmm + nu], xmm_mn = o->bw[4 * xmm + nu], xmn_pm = o->fw[4 * xmn + mu];
+    const long S[4][4] = {{x, xpm, xpn, x}, {x, xmm_pn, xmm, xmm}, {xmm, xmm_mn, xmm_mn, xmn}, {xmn, xmn, xmn_pm, x}};
+    const int Dd[4][4] = {{mu, nu, mu, nu}, {nu, mu, nu, mu}, {mu, nu, mu, nu}, {nu, mu, nu, mu}};
+    const int Gd[4][4] = {{0, 0, 1, 1}, {0, 1, 1, 0}, {1, 1, 0, 0}, {1, 0, 0, 1}};
+    ocplx q[9] = {0}, t[9];
+    int hit = 0;
+    for (int l = 0; l < 4; l++)
+        if (leaf_deriv(o, S[l], Dd[l], Gd[l], P, t)) {
+            hit = 1;
+            for (int i = 0; i < 9; i++) q[i] += t[i];
+        }
+    if (!hit) return 0;
+    for (int a = 0; a < 3; a++)
+        for (int b = 0; b < 3; b++) dF[3 * a + b] = (q[3 * a + b] - conj(q[3 * b + a])) / 8.0;
+    return 1;
+}
+
+/* d A(x) = c_sw sum_{mu != nu} (i/4) sigma_{mu nu} (x) d Fhat_{mu nu}(x); 0 if it vanishes */
+static int dclover_site(const oracle *o, long x, const or_pert *P, ocplx *dA)
+{
+    int hit = 0;
+    for (int i = 0; i < 144; i++) dA[i] = 0;
+    for (int mu = 0; mu < 4; mu++)
+        for (int nu = 0; nu < 4; nu++) {
+            if (mu == nu) continue;
+            ocplx s[4][4], dF[9];
+            if (!dfhat_site(o, x, mu, nu, P, dF)) continue;
+            hit = 1;
+            sigma(mu, nu, s);
+            for (int si = 0; si < 4; si++)
+                for (int sj = 0; sj < 4; sj++)
+                    for (int a = 0; a < 3; a++)
+                        for (int b = 0; b < 3; b++)
+                            dA[12 * (3 * si + a) + 3 * sj + b] += o->csw * 0.25 * I * s[si][sj] * dF[3 * a + b];
+        }
+    return hit;
+}
+
+static void make_pert(const oracle *o, long x, int mu, int a, or_pert *P)
+{
+    ocplx T[9];
+    gen_T(a, T);
+    P->px = x;
+    P->pmu = mu;
+    mm(T, link(o, x, mu), P->dU);
+}
+
+/* out = (d D / d eps) in for the link (x, mu) moved along T_a (full fields):
+ * the clover term at every site whose leaves hold the link, and the two hops
+ * that use it (forward out of x, backward into x + mu) */
+static void dD_apply(const oracle *o, const or_pert *P, const ocplx *in, ocplx *out)
+{
+    for (long i = 0; i < 12 * o->V; i++) out[i] = 0;
+    ocplx dA[144];
+    for (long y = 0; y < o->V; y++)
+        if (dclover_site(o, y, P, dA)) mat12_vec(dA, in + 12 * y, out + 12 * y);
+    long x = P->px, y = o->fw[4 * x + P->pmu];
+    int mu = P->pmu, x0 = o->coord[4 * x], y0 = o->coord[4 * y];
+    ocplx t[12];
+    double sf = (mu == 0 && x0 == o->L[0] - 1) ? o->bc_t : 1.0;
+    colour_mul(P->dU, 0, in + 12 * y, t);
+    add_proj(out + 12 * x, t, mu, -1.0, -0.5 * sf);
+    double sb = (mu == 0 && y0 == 0) ? o->bc_t : 1.0;
+    colour_mul(P->dU, 1, in + 12 * x, t);
+    add_proj(out + 12 * y, t, mu, +1.0, -0.5 * sb);
+}
+
+void or_dD_apply(const oracle *o, long x, int mu, int a, const double *in, double *out)
+{
+    build_gammas();
+    or_pert P;
+    make_pert(o, x, mu, a, &P);
+    dD_apply(o, &P, (const ocplx *)in, (ocplx *)out);
+}
+
+/* g[(4 x + mu) 8 + a] = Re <Y, (d D / d eps_{x,mu,a}) X> for every link and
+ * generator (X, Y full fields) */
+void or_force_dD(const oracle *o, const double *X_, const double *Y_, double *g)
+{
+    build_gammas();
+    const ocplx *X = (const ocplx *)X_, *Y = (const ocplx *)Y_;
+#pragma omp parallel for schedule(dynamic)
+    for (long l = 0; l < 4 * o->V; l++) {
+        ocplx *w = malloc(sizeof(ocplx) * 12 * o->V);
+        for (int a = 0; a < 8; a++) {
+            or_pert P;
+            make_pert(o, l / 4, (int)(l % 4), a, &P);
+            dD_apply(o, &P, X, w);
+            double acc = 0;
+            for (long i = 0; i < 12 * o->V; i++) acc += creal(conj(Y[i]) * w[i]);
+            g[8 * l + a] = acc;
+        }
+        free(w);
+    }
+}
+
+/* g[(4 x + mu) 8 + a] = d/d eps log|det A| summed over the sites of the given
+ * parity = sum_y Re tr(A(y)^-1 dA(y)) */
+void or_force_logdet(const oracle *o, int parity, double *g)
+{
+    build_gammas();
+#pragma omp parallel for schedule(dynamic)
+    for (long l = 0; l < 4 * o->V; l++)
+        for (int a = 0; a < 8; a++) {
+            or_pert P;
+            make_pert(o, l / 4, (int)(l % 4), a, &P);
+            double acc = 0;
+            ocplx dA[144];
+            for (long y = 0; y < o->V; y++) {
+                if (o->par[y] != parity || !dclover_site(o, y, &P, dA)) continue;
+                const ocplx *Ai = o->Ainv + 144 * y;
+                for (int i = 0; i < 12; i++)
+                    for (int k = 0; k < 12; k++) acc += creal(Ai[12 * i + k] * dA[12 * k + i]);
+            }
+            g[8 * l + a] = acc;
+        }
+}
