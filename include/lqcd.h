@@ -9,7 +9,12 @@
  *   - the clover term, its inverse and log det (Eq. 1, Eq. 4),
  *   - the Schwarz (SAP) preconditioner and the locally deflated GCR solver
  *     named in Sec. 3-4 (Table 1), and the solution of Dhat psi = eta through
- *     a full-lattice solve (Eq. 5).
+ *     a full-lattice solve (Eq. 5),
+ *   - the Hasenbusch operator W(dm) = Q_S + dm and its solves (Eq. 3-4), the
+ *     chronological initial guess (Sec. 2) and the DD-HMC block solves by
+ *     BiCGstab on Dirichlet blocks (Sec. 3),
+ *   - a batched solver for several lattices in one set of launches, and a
+ *     learned gauge-equivariant preconditioner usable inside the GCR.
  *
  * Conventions (shared by every entry point):
  *   Lattice   T x L1 x L2 x L3, every extent even; x0 is time and the slowest
