@@ -141,7 +141,7 @@ template <int ND>
 __global__ void __launch_bounds__(256) k_bdot(long Vh, int hb, int nch, const int *list, DotSet<ND> d,
                                               double2 *partial)
 {
-    const int c = blockIdx.x, b = blockIdx.y;
+    const int b = blockIdx.x, c = blockIdx.y;   // blocks on x (no 65535 limit), chunks on y
     const int per = (hb + nch - 1) / nch, k0 = c * per, k1 = min(hb, k0 + per);
     double re[ND], im[ND];
 #pragma unroll
@@ -398,7 +398,7 @@ struct BlockRun {
     template <int ND>
     lqcd_status bdots(DotSet<ND> d)
     {
-        k_bdot<ND><<<dim3(nch, B.nblk), 256, 0, c->stream>>>(c->g.Vh, B.hb, nch, list, d, partial);
+        k_bdot<ND><<<dim3(B.nblk, nch), 256, 0, c->stream>>>(c->g.Vh, B.hb, nch, list, d, partial);
         k_bdot_fin<ND><<<div_up(B.nblk * ND, 128), 128, 0, c->stream>>>(B.nblk, nch, partial, dots);
         c->n_kernel_launches += 2;
         LQCD_LAUNCH_CHECK(c);
