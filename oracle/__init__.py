@@ -57,6 +57,8 @@ def lib():
             "or_dD_apply": (None, [P, LG, I, I, P, P]),
             "or_force_dD": (None, [P, P, P, P]),
             "or_force_logdet": (None, [P, I, P]),
+            "or_gauge_action": (D, [P, D]),
+            "or_grad_gauge": (None, [P, D, P]),
             "or_block_bicgstab": (I, [P, IP, P, P, D, I, IP, DP]),
             "or_dfl_build": (I, [P, IP, I, I, I, I, P]),
             "or_dfl_project": (None, [P, P, P]),
@@ -346,6 +348,15 @@ class Oracle:
         v = self.W(u, dm)
         return -2.0 * dm * self._grad_qs(u, self.w_dag_inv(v, 0.0))
 
+    def gauge_action(self, beta):
+        """Wilson gauge action beta sum_P (1 - Re tr U_P / 3)."""
+        return lib().or_gauge_action(self._o, float(beta))
+
+    def grad_gauge(self, beta):
+        g = np.empty((self.V, 4, 8))
+        lib().or_grad_gauge(self._o, float(beta), _p(g))
+        return g
+
     # ---- DD-HMC block solves (Sec. 3)
     def nblocks(self, bs):
         n = 1
@@ -490,3 +501,63 @@ def even_odd_split(o: Oracle, x: np.ndarray):
     """(x_e, x_o) of a full field in the oracle's even/odd rank order."""
     x = np.asarray(x).reshape(o.V, 4, 3)
     return x[o.even_sites()], x[o.odd_sites()]
+
+
+# ---------------------------------------------------------------- MD step
+# The molecular-dynamics step of the two-flavour HMC (Sec. 2): links U, momenta
+# p^a per link (P = sum_a p^a T_a, T_a = i lambda_a / 2, kinetic energy
+# sum p^2 / 2), action S = S_g + |Dhat^-1 phi|^2 - 2 log|det A_oo| (the
+# even-odd factorisation of det(D^dag D) with the clover term, Eq. 2 and 4).
+# Equations of motion: dU/dt = P U, dp^a/dt = -dS/d eps_a.  Leapfrog (the
+# paper's integrator): p -= dt/2 g, U <- exp(dt P) U, p -= dt/2 g.
+
+def _gell_mann_T():
+    lam = np.zeros((8, 3, 3), dtype=np.complex128)
+    lam[0][0, 1] = lam[0][1, 0] = 1
+    lam[1][0, 1], lam[1][1, 0] = -1j, 1j
+    lam[2][0, 0], lam[2][1, 1] = 1, -1
+    lam[3][0, 2] = lam[3][2, 0] = 1
+    lam[4][0, 2], lam[4][2, 0] = -1j, 1j
+    lam[5][1, 2] = lam[5][2, 1] = 1
+    lam[6][1, 2], lam[6][2, 1] = -1j, 1j
+    lam[7] = np.diag([1, 1, -2]) / np.sqrt(3)
+    return 0.5j * lam
+
+
+GENERATORS = _gell_mann_T()
+
+
+def md_action(dims, U, phi_e, kappa, csw, beta):
+    o = Oracle(dims, U, kappa, csw)
+    x = o.dhat_inv(phi_e)
+    return o.gauge_action(beta) + float(np.vdot(x, x).real) - 2.0 * o.logdet(1)
+
+
+def md_gradient(dims, U, phi_e, kappa, csw, beta):
+    o = Oracle(dims, U, kappa, csw)
+    return o.grad_gauge(beta) + o.grad_pf(phi_e) - 2.0 * o.grad_logdet(1)
+
+
+def hamiltonian(dims, U, p, phi_e, kappa, csw, beta):
+    return 0.5 * float(np.sum(p * p)) + md_action(dims, U, phi_e, kappa, csw, beta)
+
+
+def _move_links(U, p, dt):
+    from scipy.linalg import expm
+    P = np.einsum("xma,aij->xmij", p, GENERATORS)
+    V = np.empty_like(U)
+    for x in range(U.shape[0]):
+        for mu in range(4):
+            V[x, mu] = expm(dt * P[x, mu]) @ U[x, mu]
+    return V
+
+
+def leapfrog(dims, U, p, phi_e, kappa, csw, beta, dt, nsteps):
+    """nsteps leapfrog steps of size dt: returns (U, p)."""
+    U = np.array(U, copy=True)
+    p = np.array(p, dtype=np.float64, copy=True)
+    for _ in range(nsteps):
+        p -= 0.5 * dt * md_gradient(dims, U, phi_e, kappa, csw, beta)
+        U = _move_links(U, p, dt)
+        p -= 0.5 * dt * md_gradient(dims, U, phi_e, kappa, csw, beta)
+    return U, p

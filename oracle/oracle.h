@@ -92,6 +92,9 @@ int or_num_threads(void);
 void or_dD_apply(const oracle *o, long x, int mu, int a, const double *in, double *out);
 void or_force_dD(const oracle *o, const double *X, const double *Y, double *g);   /* Re <Y, dD X> */
 void or_force_logdet(const oracle *o, int parity, double *g);                     /* d log|det A_p| */
+/* Wilson gauge action beta sum_P (1 - Re tr U_P / 3) and its gradient */
+double or_gauge_action(const oracle *o, double beta);
+void or_grad_gauge(const oracle *o, double beta, double *g);
 
 /* --- solvers (oracle_solvers.c) --- */
 int or_cgnr(const oracle *o, const double *eta_e, double *psi_e, double tol, int maxit,

@@ -774,3 +774,59 @@ void or_force_logdet(const oracle *o, int parity, double *g)
             g[8 * l + a] = acc;
         }
 }
+
+/* Wilson gauge action S_g = beta sum_{x, mu < nu} (1 - (1/3) Re tr U_P(x; mu, nu)),
+ * U_P(x; mu, nu) = U_mu(x) U_nu(x+mu) U_mu(x+nu)^dag U_nu(x)^dag (the MD step of
+ * the HMC, Sec. 2), and its gradient along exp(eps T_a) U link by link. */
+static void plaquette_links(const oracle *o, long x, int mu, int nu, long s[4], int d[4], int g[4])
+{
+    s[0] = x;
+    s[1] = o->fw[4 * x + mu];
+    s[2] = o->fw[4 * x + nu];
+    s[3] = x;
+    d[0] = mu;
+    d[1] = nu;
+    d[2] = mu;
+    d[3] = nu;
+    g[0] = g[1] = 0;
+    g[2] = g[3] = 1;
+}
+
+double or_gauge_action(const oracle *o, double beta)
+{
+    double acc = 0;
+    for (long x = 0; x < o->V; x++)
+        for (int mu = 0; mu < 4; mu++)
+            for (int nu = mu + 1; nu < 4; nu++) {
+                long s[4];
+                int d[4], g[4];
+                plaquette_links(o, x, mu, nu, s, d, g);
+                ocplx d1[9], d2[9], P[9];
+                dag(link(o, s[2], mu), d1);
+                dag(link(o, s[3], nu), d2);
+                mm4(link(o, s[0], mu), link(o, s[1], nu), d1, d2, P);
+                acc += 1.0 - creal(P[0] + P[4] + P[8]) / 3.0;
+            }
+    return beta * acc;
+}
+
+void or_grad_gauge(const oracle *o, double beta, double *g_out)
+{
+#pragma omp parallel for schedule(dynamic)
+    for (long l = 0; l < 4 * o->V; l++)
+        for (int a = 0; a < 8; a++) {
+            or_pert P;
+            make_pert(o, l / 4, (int)(l % 4), a, &P);
+            double acc = 0;
+            for (long x = 0; x < o->V; x++)
+                for (int mu = 0; mu < 4; mu++)
+                    for (int nu = mu + 1; nu < 4; nu++) {
+                        long s[4];
+                        int d[4], g[4];
+                        ocplx dP[9];
+                        plaquette_links(o, x, mu, nu, s, d, g);
+                        if (leaf_deriv(o, s, d, g, &P, dP)) acc -= creal(dP[0] + dP[4] + dP[8]) / 3.0;
+                    }
+            g_out[8 * l + a] = beta * acc;
+        }
+}
