@@ -4,7 +4,9 @@ differences of its action, evaluated by the oracle's operators and solvers on
 gauge fields with one link moved to exp(+-eps T_a) U (scipy's matrix
 exponential), so a dropped clover leaf, a wrong sign or adjoint, or a wrong
 generator normalisation fails.  The force of the pseudofermion action is also
-checked for gauge covariance, and the clover log det has no force at c_sw = 0."""
+checked for gauge covariance, the clover log det has no force at c_sw = 0, and
+the link-by-link derivative equals the local formulation of the force (spin-
+summed outer products for the hops, staples through every clover leaf)."""
 import numpy as np
 import pytest
 
@@ -153,3 +155,75 @@ def test_force_is_gauge_covariant():
     Mg = np.einsum("xma,aij->xmij", og.grad_pf(phig), T)
     ref = np.einsum("xij,xmjk,xlk->xmil", G, M, G.conj())
     assert util.relerr(Mg, ref) < 1e-9
+
+
+def gammas():
+    s = [np.array([[0, 1], [1, 0]]), np.array([[0, -1j], [1j, 0]]), np.array([[1, 0], [0, -1]])]
+    z = np.zeros((2, 2))
+    g = [np.block([[z, -np.eye(2)], [-np.eye(2), z]])]
+    for k in range(3):
+        g.append(np.block([[z, -1j * s[k]], [1j * s[k], z]]))
+    return [np.asarray(m, dtype=np.complex128) for m in g]
+
+
+def force_local(dims, U, X, Y, csw, bc_t=-1.0):
+    """Re <Y, dD X> per link and generator from local colour matrices: the two
+    hops give M = -1/2 s_f U B1 + 1/2 s_b B2 U^dag (B1, B2 spin-summed outer
+    products of the projected X with Y), and every clover leaf through the
+    link gives (c_sw / 8) U B Om A (or -B Om A U^dag for an adjoint factor),
+    Om = Lam - Lam^dag, Lam = (i/4) sum sigma X Y^dag; the gradient is Re tr(T_a M)."""
+    V = U.shape[0]
+    c = util.coords(dims)
+    G = gammas()
+    one = np.eye(4)
+    M = np.zeros((V, 4, 3, 3), dtype=np.complex128)
+    X, Y = X.reshape(V, 4, 3), Y.reshape(V, 4, 3)
+    fw = [util.shift(dims, m, +1) for m in range(4)]
+    bw = [util.shift(dims, m, -1) for m in range(4)]
+    for x in range(V):
+        for mu in range(4):
+            y = fw[mu][x]
+            sf = bc_t if (mu == 0 and c[x, 0] == dims[0] - 1) else 1.0
+            sb = bc_t if (mu == 0 and c[y, 0] == 0) else 1.0
+            a = (one - G[mu]) @ X[y]
+            b = (one + G[mu]) @ X[x]
+            B1 = np.einsum("sk,si->ki", a, Y[x].conj())
+            B2 = np.einsum("sk,si->ki", b, Y[y].conj())
+            M[x, mu] += -0.5 * sf * U[x, mu] @ B1 + 0.5 * sb * B2 @ U[x, mu].conj().T
+    for yy in range(V):
+        for mu in range(4):
+            for nu in range(4):
+                if mu == nu:
+                    continue
+                sig = 0.5j * (G[mu] @ G[nu] - G[nu] @ G[mu])
+                lam = 0.25j * np.einsum("ab,bk,ai->ki", sig, X[yy], Y[yy].conj())
+                om = lam - lam.conj().T
+                pm, pn, mm, mn = fw[mu][yy], fw[nu][yy], bw[mu][yy], bw[nu][yy]
+                leaves = [[(yy, mu, 0), (pm, nu, 0), (pn, mu, 1), (yy, nu, 1)],
+                          [(yy, nu, 0), (fw[nu][mm], mu, 1), (mm, nu, 1), (mm, mu, 0)],
+                          [(mm, mu, 1), (bw[nu][mm], nu, 1), (bw[nu][mm], mu, 0), (mn, nu, 0)],
+                          [(mn, nu, 1), (mn, mu, 0), (fw[mu][mn], nu, 0), (yy, mu, 1)]]
+                for leaf in leaves:
+                    f = [U[s, d].conj().T if dg else U[s, d] for s, d, dg in leaf]
+                    for i, (s, d, dg) in enumerate(leaf):
+                        A = np.eye(3, dtype=np.complex128)
+                        for k in range(i):
+                            A = A @ f[k]
+                        B = np.eye(3, dtype=np.complex128)
+                        for k in range(i + 1, 4):
+                            B = B @ f[k]
+                        if dg:
+                            M[s, d] += -(csw / 8.0) * B @ om @ A @ U[s, d].conj().T
+                        else:
+                            M[s, d] += (csw / 8.0) * U[s, d] @ B @ om @ A
+    return np.einsum("aij,xmji->xma", T, M).real
+
+
+@pytest.mark.parametrize("dims", DIMS)
+def test_force_from_local_outer_products_and_staples(dims):
+    """The local formulation of the force (the one a per-link kernel uses)
+    equals the oracle's link-by-link derivative of D."""
+    U = synth.su3_links(dims, 7)
+    o = orc.Oracle(dims, U, KAPPA, CSW)
+    X, Y = synth.gaussian_spinor(o.V, 9), synth.gaussian_spinor(o.V, 10)
+    assert util.relerr(force_local(dims, U, X, Y, CSW), o.force_dD(X, Y)) < 1e-12
