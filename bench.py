@@ -749,7 +749,9 @@ def main():
         e2e_ms = round(e2e_ms, 4)
 
     tts = None
-    if not args.no_solve and rank == 0 and DIMS == (48, 24, 24, 24):
+    # the time-to-solution table (minutes of GPU time) belongs to the one-GPU run;
+    # under torchrun the other GPUs would idle meanwhile
+    if not args.no_solve and world == 1 and DIMS == (48, 24, 24, 24):
         net = None
         if not args.no_net:
             W, hist, train_s = train_net(lqcd, synth, KAPPA, args.nfields, args.npairs, args.train_steps)
