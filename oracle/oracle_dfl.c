@@ -11,9 +11,12 @@
  *   4. the little Dirac operator A_{(L k),(L' l)} = <phi^L_k, D phi^L'_l>;
  *   5. M_dfl rho = M_sap(rho - D Pi A^-1 Pi^dag rho) + Pi A^-1 Pi^dag rho, with
  *      A^-1 applied by plain GCR to a relative residual ctol.
- * Pinned by (tests/test_oracle_dfl.py): block orthonormality; A equal to the
- * dense Pi^dag D Pi; Pi^dag P_L = 0 and P_L^2 = P_L for P_L = 1 - D Pi A^-1 Pi^dag;
- * the deflated GCR reaching the dense LU solution.
+ * Pinned by (tests/test_oracle_solvers.py): block orthonormality; the subspace
+ * equal to numpy's per-block QR factor of v0, M_sap v0 and M_sap^2 v0 (ninv = 0,
+ * 1, 2); A equal to the dense Pi^dag D Pi; Pi^dag P_L = 0 and P_L^2 = P_L for
+ * P_L = 1 - D Pi A^-1 Pi^dag; M_dfl equal to the composition assembled from the
+ * dense Pi, an LU solve of A and the (separately pinned) SAP, and
+ * M_dfl (D Pi c) = Pi c; the deflated GCR reaching the SAP-GCR solution.
  */
 #include "oracle_internal.h"
 

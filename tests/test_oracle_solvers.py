@@ -177,3 +177,80 @@ def test_dfl_gcr_converges_and_reduces_iterations(dfl8):
     assert st2 == 0
     assert util.relerr(psi, psi2) < 1e-7
     assert it_d <= it_s
+
+
+def _block_ids(dims, bs):
+    c = util.coords(dims) // np.asarray(bs)
+    nb = [L // b for L, b in zip(dims, bs)]
+    return c[:, 3] + nb[3] * (c[:, 2] + nb[2] * (c[:, 1] + nb[1] * c[:, 0])), int(np.prod(nb))
+
+
+def _block_qr(v, blk, nblk):
+    """Per block, the orthonormal factor of the QR decomposition of the Ns
+    columns v[l] restricted to the block, with the phases fixed so that R has a
+    positive real diagonal -- the unique factor that Gram-Schmidt produces."""
+    Ns = v.shape[0]
+    out = np.zeros_like(v)
+    for b in range(nblk):
+        m = blk == b
+        M = v[:, m].reshape(Ns, -1).T
+        Q, R = np.linalg.qr(M)
+        ph = np.diag(R) / np.abs(np.diag(R))
+        Q = Q * ph[None, :]
+        out[:, m] = Q.T.reshape((Ns,) + v[:, m].shape[1:])
+    return out
+
+
+@pytest.mark.parametrize("ninv", [0, 1, 2])
+def test_dfl_build_is_block_qr_of_sap_iterates(ninv):
+    """Subspace generation (Sec. 4, locally deflated SAP-GCR; the inverse-iteration
+    reading of the design notes): after ninv passes v <- M_sap v / |M_sap v| the
+    block-orthonormal fields are the per-block QR factors of the iterates.  M_sap is
+    positively homogeneous (the MinRes coefficients are scale free), so the
+    normalisation does not change the directions; the oracle's SAP is pinned on
+    its own (dense block inverse, one-block limit, vanishing residual)."""
+    dims, bs, Ns, ncy, nmr = (8, 8, 8, 8), (4, 4, 4, 4), 4, 2, 4
+    o, _ = make(dims)
+    v0 = synth.gaussian_spinor(Ns * o.V, 100, synth.STREAM_SUBSPACE).reshape(Ns, o.V, 4, 3)
+    assert o.dfl_build(v0, bs=bs, ninv=ninv, ncy=ncy, nmr=nmr) == 0
+    v = v0.copy()
+    for _ in range(ninv):
+        v = np.stack([o.sap(v[l], bs=bs, ncy=ncy, nmr=nmr) for l in range(Ns)])
+    blk, nblk = _block_ids(dims, bs)
+    ref = _block_qr(v, blk, nblk)
+    phi = o.dfl_subspace()
+    assert util.relerr(phi, ref) < 1e-12
+    if ninv > 0:   # the iterates differ from the Gaussian start
+        assert util.relerr(_block_qr(v0, blk, nblk), ref) > 0.1
+
+
+def test_dfl_precond_is_sap_on_deflated_residual_plus_coarse_correction(dfl8):
+    """M_dfl rho = M_sap(P_L rho) + Pi A^-1 Pi^dag rho (Sec. 4, deflated SAP),
+    with Pi and A = Pi^dag D Pi assembled densely in numpy and A^-1 by LU; the
+    oracle's coarse solve runs to 1e-13 so both sides see the same P_L rho."""
+    o, Ns = dfl8
+    bs, ncy, nmr = (4, 4, 4, 4), 3, 4
+    phi = o.dfl_subspace()
+    blk, nblk = _block_ids(o.dims, bs)
+    Pi = np.zeros((o.V * 12, nblk * Ns), dtype=np.complex128)
+    for b in range(nblk):
+        for k in range(Ns):
+            f = np.zeros((o.V, 4, 3), dtype=np.complex128)
+            f[blk == b] = phi[k, blk == b]
+            Pi[:, b * Ns + k] = f.ravel()
+    DPi = np.stack([o.D(Pi[:, j].reshape(o.V, 4, 3)).ravel() for j in range(nblk * Ns)], axis=1)
+    A = Pi.conj().T @ DPi
+    rho = synth.gaussian_spinor(o.V, 41)
+    e = np.linalg.solve(A, Pi.conj().T @ rho.ravel())
+    PL = rho.ravel() - DPi @ e
+    ref = o.sap(PL.reshape(o.V, 4, 3), bs=bs, ncy=ncy, nmr=nmr).ravel() + Pi @ e
+    got = o.dfl_precond(rho, bs=bs, ncy=ncy, nmr=nmr, ctol=1e-13).ravel()
+    assert util.relerr(got, ref) < 1e-10
+    # either half alone is far from the whole
+    assert util.relerr(Pi @ e, ref) > 1e-2
+    assert util.relerr(ref - Pi @ e, ref) > 1e-2
+    # closed form: on the image of D Pi the deflated residual vanishes, M_sap(0) = 0
+    # and M_dfl returns the coarse preimage, M_dfl (D Pi c) = Pi c
+    c = synth.gaussian_spinor(nblk * Ns // 12 + 1, 42).ravel()[: nblk * Ns]
+    got = o.dfl_precond((DPi @ c).reshape(o.V, 4, 3), bs=bs, ncy=ncy, nmr=nmr, ctol=1e-13).ravel()
+    assert util.relerr(got, Pi @ c) < 1e-10
