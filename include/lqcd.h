@@ -153,7 +153,9 @@ LQCD_API lqcd_status lqcd_apply_Dhat_native(lqcd_ctx *ctx, lqcd_prec prec, const
 LQCD_API lqcd_status lqcd_apply_D_native(lqcd_ctx *ctx, lqcd_prec prec, const void *in_dev, void *out_dev,
                                 int nrhs);
 
-/* Dhat on native fields exactly as lqcd_apply_Dhat_native, except that the
+/* Dhat on native fields exactly as lqcd_apply_Dhat_native (FP64, FP32 or
+ * F16S; the same kernels and launch shapes, so the results are bitwise those
+ * of lqcd_apply_Dhat_native), except that the
  * odd-site intermediate A_oo^-1 H_oe in_e lives in a fixed device array
  * compiled into the library instead of the context's workspace, so that the
  * call never allocates device memory.  The paper has no counterpart: it is
@@ -161,8 +163,9 @@ LQCD_API lqcd_status lqcd_apply_D_native(lqcd_ctx *ctx, lqcd_prec prec, const vo
  * that has handed the rest of the device to its memory pool, or code that
  * cannot afford the device-wide synchronisation an allocation can imply.
  * Limit: native_half_bytes(prec) * nrhs <= LQCD_DHAT_STATIC_SCRATCH_BYTES
- * (32 MiB: one FP32 right-hand side of a 48x24^3 lattice); larger requests
- * return LQCD_ERR_ARG before any work.  The array is one per device and per
+ * (32 MiB: one FP32 right-hand side of a 48x24^3 lattice); larger requests,
+ * and any precision other than FP64, FP32 and F16S, return LQCD_ERR_ARG
+ * before any work.  The array is one per device and per
  * process: calls that overlap in time (other streams, host threads or
  * contexts on the same device) share it and race.  The first call on a device
  * looks up the array's device address (and, for a new shape, the autotuner may

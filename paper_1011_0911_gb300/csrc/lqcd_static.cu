@@ -46,7 +46,8 @@ lqcd_status scratch_address(lqcd_ctx *c, void **out)
 extern "C" lqcd_status lqcd_apply_Dhat_native_static(lqcd_ctx *c, lqcd_prec p, const void *in, void *out, int nrhs)
 {
     if (!c || !in || !out || nrhs < 1) return set_err(c, LQCD_ERR_ARG, "bad argument");
-    if (p != LQCD_F64 && p != LQCD_F32) return set_err(c, LQCD_ERR_ARG, "precision %d", (int)p);
+    if (p != LQCD_F64 && p != LQCD_F32 && p != LQCD_F16S)
+        return set_err(c, LQCD_ERR_ARG, "static Dhat: precision %d is not a stencil precision", (int)p);
     const size_t need = native_half_bytes(c, p) * (size_t)nrhs;
     if (need > kScratchBytes)
         return set_err(c, LQCD_ERR_ARG,

@@ -7,7 +7,7 @@ import torch
 
 from paper_1011_0911_gb300 import lqcd, synth
 from tests import util
-from tests.gpu_util import Pair, relerr, to_gpu
+from tests.gpu_util import Pair, relerr, rounded, to_gpu
 
 pytestmark = pytest.mark.gpu
 
@@ -28,7 +28,9 @@ def test_cgnr_8x4(p8):
     assert util.relerr(x, ref) < 1e-7
 
 
-@pytest.mark.parametrize("prec,tol", [(lqcd.F64, 1e-12), (lqcd.F32, 2e-5), (lqcd.F16S, 1e-2)],
+# per-application bounds of the precision targets (FP32 1e-6, FP16 + scale
+# 3e-3); measured on a GB300: FP32 1.3e-7 - 1.5e-7, F16S 5.1e-4 - 5.7e-4
+@pytest.mark.parametrize("prec,tol", [(lqcd.F64, 1e-12), (lqcd.F32, 1e-6), (lqcd.F16S, 3e-3)],
                          ids=["f64", "f32", "f16s"])
 @pytest.mark.parametrize("dims,bs", [((8, 8, 8, 8), (4, 4, 4, 4)), ((8, 4, 4, 8), (4, 4, 4, 4)),
                                      ((12, 8, 4, 4), (4, 4, 4, 4)), ((4, 4, 4, 4), (4, 4, 4, 4))],
@@ -38,7 +40,7 @@ def test_sap_parity(dims, bs, prec, tol, monkeypatch):
     12x8x4x4 has 3 blocks along time: same-colour blocks touch across the wrap.
     FP32 runs both block kernels (shared-memory resident and L1-cached)."""
     P = Pair(dims, kappa=0.1355)
-    eta = synth.gaussian_spinor(P.V, 2)
+    eta = rounded(synth.gaussian_spinor(P.V, 2), prec)   # the input as the library stores it
     ref = P.o.sap(eta, bs=bs, ncy=4, nmr=5)
     for generic in (("0", "1") if prec != lqcd.F64 else ("0",)):
         monkeypatch.setenv("LQCD_SAP_GENERIC", generic)
