@@ -54,9 +54,9 @@ __device__ __forceinline__ void bhop_dir(const Geom &g, const BlkG &B, int p_out
         load_spinor(in, Vh, ry, psi);
         project<double, MU, -1>(psi, h);
         load_link(U, Vh, p_out, MU, r, u);
-        su3_vec(u, h[0], w[0], sg);
-        su3_vec(u, h[1], w[1], sg);
-        accumulate<double, MU, -1>(acc, w);
+        su3_vec(u, h[0], w[0]);
+        su3_vec(u, h[1], w[1]);
+        accumulate<double, MU, -1, MU == 0>(acc, w, sg);
     }
     if (in_blk(g, B, x, MU, -1)) {
         const int rz = nbr_rank(g, x, MU, -1);
@@ -64,9 +64,9 @@ __device__ __forceinline__ void bhop_dir(const Geom &g, const BlkG &B, int p_out
         load_spinor(in, Vh, rz, psi);
         project<double, MU, +1>(psi, h);
         load_link(U, Vh, 1 - p_out, MU, rz, u);
-        su3dag_vec(u, h[0], w[0], sg);
-        su3dag_vec(u, h[1], w[1], sg);
-        accumulate<double, MU, +1>(acc, w);
+        su3dag_vec(u, h[0], w[0]);
+        su3dag_vec(u, h[1], w[1]);
+        accumulate<double, MU, +1, MU == 0>(acc, w, sg);
     }
 }
 

@@ -38,6 +38,22 @@ lqcd_status ws_get(lqcd_ctx *c, int slot, size_t bytes, void **out)
     return LQCD_OK;
 }
 
+void geom_init(Geom &g, const int L[4], int bc_t)
+{
+    long V = 1;
+    for (int i = 0; i < 4; i++) {
+        g.L[i] = L[i];
+        V *= L[i];
+    }
+    g.V = (int)V;
+    g.Vh = (int)(V / 2);
+    g.L3h = L[3] / 2;
+    g.bc_t = bc_t;
+    g.dL3h = make_fastdiv(g.L3h);
+    g.dL2 = make_fastdiv(L[2]);
+    g.dL1 = make_fastdiv(L[1]);
+}
+
 size_t native_half_bytes(const lqcd_ctx *c, lqcd_prec p)
 {
     long Vh = c->g.Vh;
@@ -293,11 +309,7 @@ lqcd_status lqcd_create(const lqcd_geom *geom, void *stream, lqcd_ctx **out)
     if (V > (1L << 29)) return LQCD_ERR_ARG;
     lqcd_ctx *c = new lqcd_ctx();
     c->geom = *geom;
-    for (int i = 0; i < 4; i++) c->g.L[i] = L[i];
-    c->g.V = (int)V;
-    c->g.Vh = (int)(V / 2);
-    c->g.L3h = L[3] / 2;
-    c->g.bc_t = geom->antiperiodic_t ? -1 : 1;
+    geom_init(c->g, L, geom->antiperiodic_t ? -1 : 1);
     c->stream = (cudaStream_t)stream;
     c->prof_on = getenv("LQCD_PROFILE") && getenv("LQCD_PROFILE")[0] == '1';
     if (cudaMalloc(&c->red, 4096 * 2 * 64 * sizeof(double)) != cudaSuccess ||

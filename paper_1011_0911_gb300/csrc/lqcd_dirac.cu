@@ -86,11 +86,15 @@ __device__ __forceinline__ void hop_site(const HopArgs<SP, LK, CL> &a, int r, in
     }
 }
 
+// one-dimensional grid: CTA b covers site tile b / ngy and field block b % ngy,
+// so the CTAs of all fields of a site tile run next to each other and share
+// its links and clover term through L1/L2
 template <class R, class SP, class LK, class CL, int MODE, int VAR>
-__global__ void __launch_bounds__(Var<VAR>::T, Var<VAR>::B) k_hop(HopArgs<SP, LK, CL> a)
+__global__ void __launch_bounds__(Var<VAR>::T, Var<VAR>::B) k_hop(HopArgs<SP, LK, CL> a, int ngy)
 {
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    const int k = blockIdx.y * blockDim.y + threadIdx.y;
+    const int gy = blockIdx.x % ngy, tile = blockIdx.x / ngy;
+    const int r = tile * blockDim.x + threadIdx.x;
+    const int k = gy * blockDim.y + threadIdx.y;
     if (r >= a.g.Vh || k >= a.nrhs) return;
     hop_site<R, SP, LK, CL, MODE>(a, r, k);
 }
@@ -112,12 +116,15 @@ __global__ void __launch_bounds__(256) k_hop_batch(const HopArgs<SP, LK, CL> *ar
 template <class R, class SP, class LK, class CL, int MODE>
 lqcd_status launch_var(lqcd_ctx *c, int var, dim3 b, const HopArgs<SP, LK, CL> &a)
 {
-    dim3 grid(div_up(c->g.Vh, b.x), div_up(a.nrhs, b.y));
+    const int ngy = div_up(a.nrhs, b.y);
+    const long nb = (long)div_up(c->g.Vh, b.x) * ngy;
+    if (nb > 0x7fffffffL) return set_err(c, LQCD_ERR_ARG, "stencil: grid of %ld CTAs", nb);
+    const int grid = (int)nb;
     switch (var) {
-        case 0: k_hop<R, SP, LK, CL, MODE, 0><<<grid, b, 0, c->stream>>>(a); break;
-        case 1: k_hop<R, SP, LK, CL, MODE, 1><<<grid, b, 0, c->stream>>>(a); break;
-        case 2: k_hop<R, SP, LK, CL, MODE, 2><<<grid, b, 0, c->stream>>>(a); break;
-        default: k_hop<R, SP, LK, CL, MODE, 3><<<grid, b, 0, c->stream>>>(a); break;
+        case 0: k_hop<R, SP, LK, CL, MODE, 0><<<grid, b, 0, c->stream>>>(a, ngy); break;
+        case 1: k_hop<R, SP, LK, CL, MODE, 1><<<grid, b, 0, c->stream>>>(a, ngy); break;
+        case 2: k_hop<R, SP, LK, CL, MODE, 2><<<grid, b, 0, c->stream>>>(a, ngy); break;
+        default: k_hop<R, SP, LK, CL, MODE, 3><<<grid, b, 0, c->stream>>>(a, ngy); break;
     }
     c->n_kernel_launches++;
     LQCD_LAUNCH_CHECK(c);
@@ -184,11 +191,11 @@ std::vector<TuneChoice> hop_sm_candidates(int nrhs)
 std::vector<TuneChoice> hop_mr_candidates(int nrhs)
 {
     std::vector<TuneChoice> v;
-    for (int nr : {2}) {
+    for (int nr : {2, 3}) {
         if (nr > nrhs) continue;
         const int groups = (nrhs + nr - 1) / nr;
         std::vector<int> tys;
-        for (int t : {1, 2, groups})
+        for (int t : {1, 2, (groups + 1) / 2, groups})
             if (t >= 1 && t <= groups && std::find(tys.begin(), tys.end(), t) == tys.end()) tys.push_back(t);
         for (int var = 0; var < NVAR_MR; var++)
             for (int ty : tys)
@@ -236,8 +243,8 @@ lqcd_status launch_hop(lqcd_ctx *c, int p_out, const SP *in_other, long in_rs, c
     const int prec = sizeof(R) == 8 ? 0 : (std::is_same<SP, h16s>::value ? 2 : 1);
     constexpr bool has_alt = std::is_same<R, float>::value && MODE != MODE_HOP;
     const int force = hop_force_kind(has_alt, nrhs);
-    static const char *kname[3] = {"k_hop3_hop", "k_hop3_mr", "k_hop3_sm"};
-    std::string key = tune_key(c, force >= 0 ? kname[force] : "k_hop3", MODE, prec, nrhs);
+    static const char *kname[3] = {"k_hop4_hop", "k_hop4_mr", "k_hop4_sm"};
+    std::string key = tune_key(c, force >= 0 ? kname[force] : "k_hop4", MODE, prec, nrhs);
     TuneChoice tc;
     if (!tune_lookup(key, &tc)) {
         tc = TuneChoice();

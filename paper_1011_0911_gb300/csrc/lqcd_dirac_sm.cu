@@ -87,18 +87,18 @@ __device__ __forceinline__ void sm_hop_dir(const SmStage<TS> &S, int s, const SP
         load_spinor(in, Vh, S.nbr[MU][s], psi);
         project<float, MU, -1>(psi, h);
         sm_link<TS>(S, MU, s, u);
-        su3_vec(u, h[0], w[0], sg);
-        su3_vec(u, h[1], w[1], sg);
-        accumulate<float, MU, -1>(acc, w);
+        su3_vec(u, h[0], w[0]);
+        su3_vec(u, h[1], w[1]);
+        accumulate<float, MU, -1, MU == 0>(acc, w, sg);
     }
     {
         const float sg = MU == 0 ? S.sg[1][s] : 1.f;
         load_spinor(in, Vh, S.nbr[4 + MU][s], psi);
         project<float, MU, +1>(psi, h);
         sm_link<TS>(S, 4 + MU, s, u);
-        su3dag_vec(u, h[0], w[0], sg);
-        su3dag_vec(u, h[1], w[1], sg);
-        accumulate<float, MU, +1>(acc, w);
+        su3dag_vec(u, h[0], w[0]);
+        su3dag_vec(u, h[1], w[1]);
+        accumulate<float, MU, +1, MU == 0>(acc, w, sg);
     }
 }
 
@@ -119,11 +119,13 @@ struct VarSM<2> {
 };
 
 template <class SP, class LK, class CL, int MODE, int TS, int VAR>
-__global__ void __launch_bounds__(VarSM<VAR>::T, VarSM<VAR>::B) k_hop_sm(HopArgs<SP, LK, CL> a)
+__global__ void __launch_bounds__(VarSM<VAR>::T, VarSM<VAR>::B) k_hop_sm(HopArgs<SP, LK, CL> a, int ngy)
 {
     __shared__ SmStage<TS> S;
     const long Vh = a.g.Vh;
-    const int r0 = blockIdx.x * TS;
+    // one-dimensional grid, the field blocks of a site tile next to each other
+    const int gy = blockIdx.x % ngy;
+    const int r0 = (blockIdx.x / ngy) * TS;
     const int tid = threadIdx.y * TS + threadIdx.x, nthr = TS * blockDim.y;
     // ---- stage the operator of the tile's sites
     for (int w = tid; w < 8 * TS; w += nthr) {
@@ -150,7 +152,7 @@ __global__ void __launch_bounds__(VarSM<VAR>::T, VarSM<VAR>::B) k_hop_sm(HopArgs
     __syncthreads();
     // ---- one thread per (site, field)
     const int s = threadIdx.x, r = r0 + s;
-    const int k = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k = gy * blockDim.y + threadIdx.y;
     if (r >= Vh || k >= a.nrhs) return;
     const SP *in = a.in_other + k * a.in_rs;
     Spinor<float> acc;
@@ -188,12 +190,12 @@ __global__ void __launch_bounds__(VarSM<VAR>::T, VarSM<VAR>::B) k_hop_sm(HopArgs
 }
 
 template <class SP, class LK, class CL, int MODE, int TS>
-void launch_ts(int var, dim3 grid, dim3 b, cudaStream_t st, const HopArgs<SP, LK, CL> &a)
+void launch_ts(int var, int grid, dim3 b, int ngy, cudaStream_t st, const HopArgs<SP, LK, CL> &a)
 {
     switch (var) {
-        case 0: k_hop_sm<SP, LK, CL, MODE, TS, 0><<<grid, b, 0, st>>>(a); break;
-        case 1: k_hop_sm<SP, LK, CL, MODE, TS, 1><<<grid, b, 0, st>>>(a); break;
-        default: k_hop_sm<SP, LK, CL, MODE, TS, 2><<<grid, b, 0, st>>>(a); break;
+        case 0: k_hop_sm<SP, LK, CL, MODE, TS, 0><<<grid, b, 0, st>>>(a, ngy); break;
+        case 1: k_hop_sm<SP, LK, CL, MODE, TS, 1><<<grid, b, 0, st>>>(a, ngy); break;
+        default: k_hop_sm<SP, LK, CL, MODE, TS, 2><<<grid, b, 0, st>>>(a, ngy); break;
     }
 }
 
@@ -202,11 +204,13 @@ void launch_ts(int var, dim3 grid, dim3 b, cudaStream_t st, const HopArgs<SP, LK
 template <class R, class SP, class LK, class CL, int MODE>
 lqcd_status launch_hop_sm(lqcd_ctx *c, int var, dim3 b, const HopArgs<SP, LK, CL> &a)
 {
-    dim3 grid(div_up(c->g.Vh, b.x), div_up(a.nrhs, b.y));
+    const int ngy = div_up(a.nrhs, b.y);
+    const long nb = (long)div_up(c->g.Vh, b.x) * ngy;
+    if (nb > 0x7fffffffL) return set_err(c, LQCD_ERR_ARG, "staged stencil: grid of %ld CTAs", nb);
     if (b.x == 16)
-        launch_ts<SP, LK, CL, MODE, 16>(var, grid, b, c->stream, a);
+        launch_ts<SP, LK, CL, MODE, 16>(var, (int)nb, b, ngy, c->stream, a);
     else if (b.x == 32)
-        launch_ts<SP, LK, CL, MODE, 32>(var, grid, b, c->stream, a);
+        launch_ts<SP, LK, CL, MODE, 32>(var, (int)nb, b, ngy, c->stream, a);
     else
         return set_err(c, LQCD_ERR_ARG, "staged stencil: tile of %d sites", (int)b.x);
     c->n_kernel_launches++;

@@ -88,9 +88,7 @@ __device__ __forceinline__ void f16s_link(const uint2 *U, long Vh, int p, int mu
         u[(2 * q) / 3][(2 * q) % 3] = f16s_h2c(t.x, 1.f);
         u[(2 * q + 1) / 3][(2 * q + 1) % 3] = f16s_h2c(t.y, 1.f);
     }
-    u[2][0] = conjx(u[0][1] * u[1][2] - u[0][2] * u[1][1]);
-    u[2][1] = conjx(u[0][2] * u[1][0] - u[0][0] * u[1][2]);
-    u[2][2] = conjx(u[0][0] * u[1][1] - u[0][1] * u[1][0]);
+    su3_third_row(u);
 }
 
 // the 36 reals of clover block blk (FP16 copy)

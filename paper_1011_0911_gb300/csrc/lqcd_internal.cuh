@@ -47,24 +47,75 @@ __device__ __forceinline__ cx<R> cmulc(cx<R> a, cx<R> b)
     return {a.re * b.re + a.im * b.im, a.re * b.im - a.im * b.re};
 }
 
+// a * b + c with a single rounding
+__device__ __forceinline__ float fmx(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fmx(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+// third row of an SU(3) matrix from the first two, u2 = (u0 x u1)^*, each real
+// part one product and three fused multiply-adds
+template <class R>
+__device__ __forceinline__ void su3_third_row(cx<R> u[3][3])
+{
+#pragma unroll
+    for (int j = 0; j < 3; j++) {
+        const int k = (j + 1) % 3, l = (j + 2) % 3;
+        const cx<R> a = u[0][k], b = u[1][l], c = u[0][l], d = u[1][k];
+        // conj(a b - c d)
+        R re = a.re * b.re;
+        re = fmx(-a.im, b.im, re);
+        re = fmx(-c.re, d.re, re);
+        re = fmx(c.im, d.im, re);
+        R im = -a.re * b.im;
+        im = fmx(-a.im, b.re, im);
+        im = fmx(c.re, d.im, im);
+        im = fmx(c.im, d.re, im);
+        u[2][j] = mk(re, im);
+    }
+}
+
 // ------------------------------------------------------------------ geometry
+// Division of a non-negative 31-bit n by an invariant d >= 1 as a multiply-high,
+// an add and a shift (Granlund & Montgomery, "Division by invariant integers
+// using multiplication", 1994, round-up method): with l = ceil(log2 d) and
+// m = floor(2^32 (2^l - d) / d) + 1, n / d = (mulhi(m, n) + n) >> l exactly for
+// 0 <= n < 2^31 (mulhi(m, n) < n, so the sum does not overflow 32 bits).
+struct FastDiv {
+    unsigned m;
+    int l;
+};
+inline FastDiv make_fastdiv(int d)
+{
+    int l = 0;
+    while ((1u << l) < (unsigned)d) l++;
+    const unsigned long long m =
+        ((1ull << 32) * ((1ull << l) - (unsigned long long)d)) / (unsigned long long)d + 1;
+    return FastDiv{(unsigned)m, l};
+}
+__device__ __forceinline__ int fast_div(const FastDiv &f, int n)
+{
+    return (int)((__umulhi(f.m, (unsigned)n) + (unsigned)n) >> f.l);
+}
+
 struct Geom {
     int L[4];      // L[0] = T
     int V, Vh;
     int L3h;       // L3 / 2
     int bc_t;      // -1 antiperiodic fermion field in time, +1 periodic
+    FastDiv dL3h, dL2, dL1;   // divisions by L3h, L[2], L[1]
 };
+// fills the derived fields of a geometry from its extents
+void geom_init(Geom &g, const int L[4], int bc_t);
 
 // coordinates of the site of parity p and rank r (site = 2r + b)
 __device__ __forceinline__ void rank_coords(const Geom &g, int p, int r, int x[4])
 {
-    int row = r / g.L3h;
-    int x3h = r - row * g.L3h;
-    int t = row / g.L[2];
+    const int row = fast_div(g.dL3h, r);
+    const int x3h = r - row * g.L3h;
+    const int t = fast_div(g.dL2, row);
     x[2] = row - t * g.L[2];
-    x[0] = t / g.L[1];
+    x[0] = fast_div(g.dL1, t);
     x[1] = t - x[0] * g.L[1];
-    int b = (p + x[0] + x[1] + x[2]) & 1;
+    const int b = (p + x[0] + x[1] + x[2]) & 1;
     x[3] = 2 * x3h + b;
 }
 __device__ __forceinline__ int coords_rank(const Geom &g, const int x[4])

@@ -144,9 +144,7 @@ __device__ __forceinline__ void pt_gather(const Geom &g, const float4 *U, const 
                 u[(2 * q) / 3][(2 * q) % 3] = mk(t.x, t.y);
                 u[(2 * q + 1) / 3][(2 * q + 1) % 3] = mk(t.z, t.w);
             }
-            u[2][0] = conjx(u[0][1] * u[1][2] - u[0][2] * u[1][1]);
-            u[2][1] = conjx(u[0][2] * u[1][0] - u[0][0] * u[1][2]);
-            u[2][2] = conjx(u[0][0] * u[1][1] - u[0][1] * u[1][0]);
+            su3_third_row(u);
         }
         const bool fwd = d & 1;
         const int y = ok ? S.nbr[d][s] : 0;

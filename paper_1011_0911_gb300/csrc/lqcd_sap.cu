@@ -110,9 +110,7 @@ __device__ __forceinline__ void glink(const float4 *U, long Vh, int p, int mu, l
         u[(2 * q) / 3][(2 * q) % 3] = mk(t.x, t.y);
         u[(2 * q + 1) / 3][(2 * q + 1) % 3] = mk(t.z, t.w);
     }
-    u[2][0] = conjx(u[0][1] * u[1][2] - u[0][2] * u[1][1]);
-    u[2][1] = conjx(u[0][2] * u[1][0] - u[0][0] * u[1][2]);
-    u[2][2] = conjx(u[0][0] * u[1][1] - u[0][1] * u[1][0]);
+    su3_third_row(u);
 }
 __device__ __forceinline__ void gload(const h16s *f, long Vh, long r, cx<float> v[12]) { f16s_load<false>(f, Vh, r, v); }
 __device__ __forceinline__ void gadd(h16s *f, long Vh, long r, const cx<float> v[12])
@@ -605,9 +603,7 @@ __device__ __forceinline__ void s_link(const SM &S, int mu, int ls, cx<float> u[
         u[(2 * q) / 3][(2 * q) % 3] = mk(a.x, a.y);
         u[(2 * q + 1) / 3][(2 * q + 1) % 3] = mk(a.z, a.w);
     }
-    u[2][0] = conjx(u[0][1] * u[1][2] - u[0][2] * u[1][1]);
-    u[2][1] = conjx(u[0][2] * u[1][0] - u[0][0] * u[1][2]);
-    u[2][2] = conjx(u[0][0] * u[1][1] - u[0][1] * u[1][0]);
+    su3_third_row(u);
 }
 // one chirality block h of the clover matrix applied to v[6]; the block is
 // read from shared memory (local site ls) or from global memory (rank grank)

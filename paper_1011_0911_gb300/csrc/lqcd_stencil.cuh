@@ -110,9 +110,7 @@ __device__ __forceinline__ void load_link(const float4 *__restrict__ U, long Vh,
         u[e0 / 3][e0 % 3] = mk(v.x, v.y);
         u[e1 / 3][e1 % 3] = mk(v.z, v.w);
     }
-    u[2][0] = conjx(u[0][1] * u[1][2] - u[0][2] * u[1][1]);
-    u[2][1] = conjx(u[0][2] * u[1][0] - u[0][0] * u[1][2]);
-    u[2][2] = conjx(u[0][0] * u[1][1] - u[0][1] * u[1][0]);
+    su3_third_row(u);
 }
 
 __device__ __forceinline__ void load_link(const uint2 *__restrict__ U, long Vh, int p, int mu, int r,
@@ -173,7 +171,7 @@ __device__ __forceinline__ void load_herm(const uint2 *__restrict__ A, long Vh, 
     for (int i = 0; i < 15; i++) h.o[i] = mk(v[6 + 2 * i], v[7 + 2 * i]);
 }
 
-// out[6] = H in[6]
+// out[6] = H in[6]; every product enters its sum through a fused multiply-add
 template <class R>
 __device__ __forceinline__ void herm_apply(const Herm6<R> &h, const cx<R> in[6], cx<R> out[6])
 {
@@ -184,10 +182,25 @@ __device__ __forceinline__ void herm_apply(const Herm6<R> &h, const cx<R> in[6],
     for (int i = 0; i < 6; i++)
 #pragma unroll
         for (int j = i + 1; j < 6; j++) {
-            out[i] = out[i] + h.o[k] * in[j];
-            out[j] = out[j] + cmulc(h.o[k], in[i]);
-            k++;
+            const cx<R> o = h.o[k++];
+            out[i].re = fmx(o.re, in[j].re, out[i].re);   // out_i += o in_j
+            out[i].re = fmx(-o.im, in[j].im, out[i].re);
+            out[i].im = fmx(o.re, in[j].im, out[i].im);
+            out[i].im = fmx(o.im, in[j].re, out[i].im);
+            out[j].re = fmx(o.re, in[i].re, out[j].re);   // out_j += conj(o) in_i
+            out[j].re = fmx(o.im, in[i].im, out[j].re);
+            out[j].im = fmx(o.re, in[i].im, out[j].im);
+            out[j].im = fmx(-o.im, in[i].re, out[j].im);
         }
+}
+// every entry of a packed Hermitian pair times an exact power of two
+template <class R>
+__device__ __forceinline__ void herm_scale(Herm6<R> &h, R f)
+{
+#pragma unroll
+    for (int i = 0; i < 6; i++) h.d[i] = f * h.d[i];
+#pragma unroll
+    for (int i = 0; i < 15; i++) h.o[i] = f * h.o[i];
 }
 
 template <class R, class CL>
@@ -234,15 +247,15 @@ __device__ __forceinline__ void project(const Spinor<R> &p, cx<R> h[2][3])
         }
     }
 }
-// acc += (w ; sgn * e_mu^dag w)
-template <class R, int MU, int SGN>
-__device__ __forceinline__ void accumulate(Spinor<R> &acc, const cx<R> w[2][3])
+// acc += sg (w ; sgn * e_mu^dag w).  SC: sg is the time-boundary sign (+-1),
+// folded into fused multiply-adds (exact, the same rounding as adding +-w);
+// otherwise sg is ignored and w is added.
+template <class R, int MU, int SGN, bool SC = false>
+__device__ __forceinline__ void accumulate(Spinor<R> &acc, const cx<R> w[2][3], R sg = R(1))
 {
 #pragma unroll
     for (int c = 0; c < 3; c++) {
-        acc.s[0][c] = acc.s[0][c] + w[0][c];
-        acc.s[1][c] = acc.s[1][c] + w[1][c];
-        cx<R> a, b;  // e^dag w
+        cx<R> a, b;  // sgn * e^dag w
         if (MU == 0) {  // e^dag = -1
             a = -w[0][c];
             b = -w[1][c];
@@ -257,31 +270,67 @@ __device__ __forceinline__ void accumulate(Spinor<R> &acc, const cx<R> w[2][3])
             b = timesmI(w[1][c]);
         }
         if (SGN < 0) {
-            acc.s[2][c] = acc.s[2][c] - a;
-            acc.s[3][c] = acc.s[3][c] - b;
+            a = -a;
+            b = -b;
+        }
+        if (SC) {
+            acc.s[0][c].re = fmx(sg, w[0][c].re, acc.s[0][c].re);
+            acc.s[0][c].im = fmx(sg, w[0][c].im, acc.s[0][c].im);
+            acc.s[1][c].re = fmx(sg, w[1][c].re, acc.s[1][c].re);
+            acc.s[1][c].im = fmx(sg, w[1][c].im, acc.s[1][c].im);
+            acc.s[2][c].re = fmx(sg, a.re, acc.s[2][c].re);
+            acc.s[2][c].im = fmx(sg, a.im, acc.s[2][c].im);
+            acc.s[3][c].re = fmx(sg, b.re, acc.s[3][c].re);
+            acc.s[3][c].im = fmx(sg, b.im, acc.s[3][c].im);
         } else {
+            acc.s[0][c] = acc.s[0][c] + w[0][c];
+            acc.s[1][c] = acc.s[1][c] + w[1][c];
             acc.s[2][c] = acc.s[2][c] + a;
             acc.s[3][c] = acc.s[3][c] + b;
         }
     }
 }
 
+// w = U h: each real part one product and five fused multiply-adds
 template <class R>
-__device__ __forceinline__ void su3_vec(const cx<R> u[3][3], const cx<R> h[3], cx<R> w[3], R sign)
+__device__ __forceinline__ void su3_vec(const cx<R> u[3][3], const cx<R> h[3], cx<R> w[3])
 {
 #pragma unroll
     for (int a = 0; a < 3; a++) {
-        cx<R> t = u[a][0] * h[0] + u[a][1] * h[1] + u[a][2] * h[2];
-        w[a] = sign * t;
+        R re = u[a][0].re * h[0].re;
+        re = fmx(-u[a][0].im, h[0].im, re);
+        re = fmx(u[a][1].re, h[1].re, re);
+        re = fmx(-u[a][1].im, h[1].im, re);
+        re = fmx(u[a][2].re, h[2].re, re);
+        re = fmx(-u[a][2].im, h[2].im, re);
+        R im = u[a][0].re * h[0].im;
+        im = fmx(u[a][0].im, h[0].re, im);
+        im = fmx(u[a][1].re, h[1].im, im);
+        im = fmx(u[a][1].im, h[1].re, im);
+        im = fmx(u[a][2].re, h[2].im, im);
+        im = fmx(u[a][2].im, h[2].re, im);
+        w[a] = mk(re, im);
     }
 }
+// w = U^dag h
 template <class R>
-__device__ __forceinline__ void su3dag_vec(const cx<R> u[3][3], const cx<R> h[3], cx<R> w[3], R sign)
+__device__ __forceinline__ void su3dag_vec(const cx<R> u[3][3], const cx<R> h[3], cx<R> w[3])
 {
 #pragma unroll
     for (int a = 0; a < 3; a++) {
-        cx<R> t = cmulc(u[0][a], h[0]) + cmulc(u[1][a], h[1]) + cmulc(u[2][a], h[2]);
-        w[a] = sign * t;
+        R re = u[0][a].re * h[0].re;
+        re = fmx(u[0][a].im, h[0].im, re);
+        re = fmx(u[1][a].re, h[1].re, re);
+        re = fmx(u[1][a].im, h[1].im, re);
+        re = fmx(u[2][a].re, h[2].re, re);
+        re = fmx(u[2][a].im, h[2].im, re);
+        R im = u[0][a].re * h[0].im;
+        im = fmx(-u[0][a].im, h[0].re, im);
+        im = fmx(u[1][a].re, h[1].im, im);
+        im = fmx(-u[1][a].im, h[1].re, im);
+        im = fmx(u[2][a].re, h[2].im, im);
+        im = fmx(-u[2][a].im, h[2].re, im);
+        w[a] = mk(re, im);
     }
 }
 
@@ -299,9 +348,9 @@ __device__ __forceinline__ void hop_dir(const Geom &g, int p_out, int r, const i
         load_spinor(in, Vh, ry, psi);
         project<R, MU, -1>(psi, h);
         load_link(U, Vh, p_out, MU, r, u);
-        su3_vec(u, h[0], w[0], sg);
-        su3_vec(u, h[1], w[1], sg);
-        accumulate<R, MU, -1>(acc, w);
+        su3_vec(u, h[0], w[0]);
+        su3_vec(u, h[1], w[1]);
+        accumulate<R, MU, -1, MU == 0>(acc, w, sg);
     }
     // backward: (1 + g_mu) U_mu(x - mu)^dag psi(x - mu)
     {
@@ -310,9 +359,9 @@ __device__ __forceinline__ void hop_dir(const Geom &g, int p_out, int r, const i
         load_spinor(in, Vh, rz, psi);
         project<R, MU, +1>(psi, h);
         load_link(U, Vh, 1 - p_out, MU, rz, u);
-        su3dag_vec(u, h[0], w[0], sg);
-        su3dag_vec(u, h[1], w[1], sg);
-        accumulate<R, MU, +1>(acc, w);
+        su3dag_vec(u, h[0], w[0]);
+        su3dag_vec(u, h[1], w[1]);
+        accumulate<R, MU, +1, MU == 0>(acc, w, sg);
     }
 }
 
