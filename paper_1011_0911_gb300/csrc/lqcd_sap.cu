@@ -17,6 +17,7 @@
 
 #include "lqcd_f16s.cuh"
 #include "lqcd_internal.cuh"
+#include "lqcd_stencil.cuh"
 
 namespace {
 
@@ -167,6 +168,19 @@ __device__ __forceinline__ void gclov(const float4 *A, long Vh, long r, int blk,
     for (int i = 0; i < 15; i++) o[i] = mk(v[6 + 2 * i], v[7 + 2 * i]);
 }
 
+// w = H v for a packed Hermitian 6x6 block (diagonal d, upper entries o),
+// every product entering its sum through a fused multiply-add
+template <class R>
+__device__ __forceinline__ void herm6_apply(const R d[6], const cx<R> o[15], const cx<R> v[6], cx<R> w[6])
+{
+    stencil::Herm6<R> h;
+#pragma unroll
+    for (int i = 0; i < 6; i++) h.d[i] = d[i];
+#pragma unroll
+    for (int i = 0; i < 15; i++) h.o[i] = o[i];
+    stencil::herm_apply(h, v, w);
+}
+
 template <class R, class CL>
 __device__ __forceinline__ void clov_apply(const CL *A, long Vh, long r, const cx<R> in[12], cx<R> out[12])
 {
@@ -175,19 +189,7 @@ __device__ __forceinline__ void clov_apply(const CL *A, long Vh, long r, const c
         R d[6];
         cx<R> o[15];
         gclov(A, Vh, r, blk, d, o);
-        const cx<R> *v = in + 6 * blk;
-        cx<R> *w = out + 6 * blk;
-#pragma unroll
-        for (int i = 0; i < 6; i++) w[i] = d[i] * v[i];
-        int k = 0;
-#pragma unroll
-        for (int i = 0; i < 6; i++)
-#pragma unroll
-            for (int j = i + 1; j < 6; j++) {
-                w[i] = w[i] + o[k] * v[j];
-                w[j] = w[j] + cmulc(o[k], v[i]);
-                k++;
-            }
+        herm6_apply(d, o, in + 6 * blk, out + 6 * blk);
     }
 }
 
@@ -232,20 +234,16 @@ __device__ __forceinline__ void proj_apply(int mu, int sgn, const cx<R> psi[12],
         }
     }
 #pragma unroll
-    for (int s = 0; s < 2; s++)
-#pragma unroll
-        for (int a = 0; a < 3; a++) {
-            cx<R> t;
-            if (!dag)
-                t = u[a][0] * h[s][0] + u[a][1] * h[s][1] + u[a][2] * h[s][2];
-            else
-                t = cmulc(u[0][a], h[s][0]) + cmulc(u[1][a], h[s][1]) + cmulc(u[2][a], h[s][2]);
-            w[s][a] = sign * t;
-        }
+    for (int s = 0; s < 2; s++) {
+        if (!dag)
+            stencil::su3_vec(u, h[s], w[s]);
+        else
+            stencil::su3dag_vec(u, h[s], w[s]);
+    }
+    // acc += sign (w ; -+ e_mu^dag w), the boundary sign (+-1) folded into
+    // fused multiply-adds
 #pragma unroll
     for (int c = 0; c < 3; c++) {
-        acc[c] = acc[c] + w[0][c];
-        acc[3 + c] = acc[3 + c] + w[1][c];
         cx<R> a, b;  // e_mu^dag w
         switch (mu) {
             case 0: a = -w[0][c]; b = -w[1][c]; break;
@@ -254,12 +252,17 @@ __device__ __forceinline__ void proj_apply(int mu, int sgn, const cx<R> psi[12],
             default: a = timesI(w[0][c]); b = timesmI(w[1][c]); break;
         }
         if (sgn < 0) {
-            acc[6 + c] = acc[6 + c] - a;
-            acc[9 + c] = acc[9 + c] - b;
-        } else {
-            acc[6 + c] = acc[6 + c] + a;
-            acc[9 + c] = acc[9 + c] + b;
+            a = -a;
+            b = -b;
         }
+        acc[c].re = fmx(sign, w[0][c].re, acc[c].re);
+        acc[c].im = fmx(sign, w[0][c].im, acc[c].im);
+        acc[3 + c].re = fmx(sign, w[1][c].re, acc[3 + c].re);
+        acc[3 + c].im = fmx(sign, w[1][c].im, acc[3 + c].im);
+        acc[6 + c].re = fmx(sign, a.re, acc[6 + c].re);
+        acc[6 + c].im = fmx(sign, a.im, acc[6 + c].im);
+        acc[9 + c].re = fmx(sign, b.re, acc[9 + c].re);
+        acc[9 + c].im = fmx(sign, b.im, acc[9 + c].im);
     }
 }
 
@@ -624,18 +627,12 @@ __device__ __forceinline__ void s_clover_half(const SM &S, int ls, const CL *A, 
         a[4 * q + 2] = t.z;
         a[4 * q + 3] = t.w;
     }
+    stencil::Herm6<float> hm;
 #pragma unroll
-    for (int i = 0; i < 6; i++) w[i] = a[i] * v[i];
-    int k = 0;
+    for (int i = 0; i < 6; i++) hm.d[i] = a[i];
 #pragma unroll
-    for (int i = 0; i < 6; i++)
-#pragma unroll
-        for (int j = i + 1; j < 6; j++) {
-            cx<float> o = mk(a[6 + 2 * k], a[7 + 2 * k]);
-            w[i] = w[i] + o * v[j];
-            w[j] = w[j] + cmulc(o, v[i]);
-            k++;
-        }
+    for (int i = 0; i < 15; i++) hm.o[i] = mk(a[6 + 2 * i], a[7 + 2 * i]);
+    stencil::herm_apply(hm, v, w);
 }
 
 // half of the in-block hop sum at site (l, x) from the smem field src of the
