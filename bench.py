@@ -48,11 +48,11 @@ def dhat_bytes_per_site(prec: str, nrhs: int) -> int:
 
 
 # ncu DRAM bytes (read + write) of one Dhat application per even site, FP32 with
-# 12 fields, from the 32x16^3 capture summarised in profiles/; valid for the
-# kernels as they were captured (k_hop DHAT1 + k_hop_mr DHAT2, NR = 2)
-TRAFFIC_F32_12_PER_SITE = 565.6e6 / 65536
-TRAFFIC_NOTE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of k_hop<DHAT1> + k_hop_mr<DHAT2> at "
-                "32x16^3 x 12 fields (565.6 MB), scaled by the even-site count")
+# 12 fields, from the full-size 48x24^3 capture summarised in profiles/ (mean of
+# two applications; valid for the FMA-chain stencil kernels it was taken of)
+TRAFFIC_F32_12_PER_SITE = 2558.6e6 / 331776
+TRAFFIC_NOTE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of the tuned DHAT1 + DHAT2 stencil kernels "
+                "at 48x24^3 x 12 fields (2558.6 MB per application, 1.086 x algorithmic)")
 
 
 def traffic_of(prec, nrhs, Vh):
@@ -777,7 +777,7 @@ def main():
             "e2e": {"value": e2e_val, "unit": "GFLOP/s", "ms_per_step": e2e_ms,
                     "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
                     "path": "lqcd_apply_Dhat (canonical fields) + pinned host copies"},
-            "roofline": {"kernel": "Dhat = k_hop<DHAT1> + k_hop<DHAT2>", "bound": "hbm",
+            "roofline": {"kernel": "Dhat = DHAT1 + DHAT2 stencil kernels (k_hop / k_hop_mr, form and shape chosen by the autotuner)", "bound": "hbm",
                          "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
                          "traffic": traffic_of(args.prec, nrhs, Vh),

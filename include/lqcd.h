@@ -176,6 +176,25 @@ LQCD_API lqcd_status lqcd_apply_D_native(lqcd_ctx *ctx, lqcd_prec prec, const vo
 LQCD_API lqcd_status lqcd_apply_Dhat_native_static(lqcd_ctx *ctx, lqcd_prec prec, const void *in_dev,
                                                    void *out_dev, int nrhs);
 
+/* ---------------------------------------------------------------- tuner */
+
+/* Autotuner of launch shapes and kernel forms (the paper has no counterpart;
+ * the kernels' results do not depend on the choice).  The first call with a
+ * new key -- kernel, mode, precision, number of right-hand sides, lattice
+ * extents, GPU name -- times every candidate (stencil: occupancy variant,
+ * CTA shape, fields per thread, kernel form; SAP: clover staged in shared
+ * memory or read through L1, timed over the sweeps of the first
+ * application; batched solver: tile size) with CUDA events on the context's
+ * stream, keeps the fastest and appends it to the cache file
+ * $LQCD_TUNE_CACHE (default $HOME/.cache/lqcd_tune.json; one line per key:
+ * "key": [variant, tx, ty, microseconds, fields per thread, kind]), so later
+ * processes skip the search.  Such a first call synchronises the stream and
+ * must not be inside a stream capture.  LQCD_TUNE=0 disables the search
+ * (defaults are used); LQCD_TUNE_VERBOSE=1 prints every timed candidate on
+ * stderr.  lqcd_tune_reset forgets the choices held in memory; the next
+ * lookup reads the cache file again.  Always LQCD_OK. */
+LQCD_API lqcd_status lqcd_tune_reset(void);
+
 /* -------------------------------------------------------------------- SAP */
 
 typedef struct {

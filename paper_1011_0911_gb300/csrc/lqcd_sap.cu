@@ -18,6 +18,7 @@
 #include "lqcd_f16s.cuh"
 #include "lqcd_internal.cuh"
 #include "lqcd_stencil.cuh"
+#include "lqcd_tune.h"
 
 namespace {
 
@@ -966,11 +967,14 @@ __global__ void __launch_bounds__(2 * SAPS_NH, sap_ctas<P, SA>()) k_sap_block_s(
     sap_block_s_body<P, SA>(a, blockIdx.x, blockIdx.y);
 }
 
-// LQCD_SAP_STAGE_A=1 stages the clover term in shared memory (one CTA per SM)
-bool sap_stage_clover()
+// LQCD_SAP_STAGE_A = 0 | 1 forces the clover term through L1 or staged in
+// shared memory (test instrumentation); otherwise the autotuner chooses.
+// Returns -1 when not forced.
+int sap_stage_forced()
 {
     const char *e = getenv("LQCD_SAP_STAGE_A");
-    return e && e[0] == '1';
+    if (!e || !*e) return -1;
+    return e[0] == '1' ? 1 : 0;
 }
 
 // r(x) -= sum of the hops into x from neighbours y that lie in another block
@@ -1188,14 +1192,48 @@ lqcd_status sap_run(lqcd_ctx *c, const SapPlan &P_, int ncy, int nmr, const void
         }
         resident = Pl.B.nh <= SAPS_NH && (2 * Pl.B.nh) % 32 == 0 && !sap_force_generic();
     }
+    // clover term staged in shared memory (stage = 1, one CTA per SM) or read
+    // through L1 (stage = 0): identical arithmetic, chosen by timing.  Without
+    // a recorded choice the sweeps of this application alternate between the
+    // two forms (in-flight tuning: every sweep is part of the result, so the
+    // search costs no extra work) and the faster one is recorded.
+    int stage = 0;
+    bool tuning = false;
+    std::string key;
+    float best_us[2] = {1e30f, 1e30f};
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    if (P != LQCD_F64 && resident) {
+        const int forced = sap_stage_forced();
+        if (forced >= 0) {
+            stage = forced;
+        } else {
+            key = tune_key(c, (std::string("k_sap_block_s/b") + std::to_string(Pl.bs[0]) + "x" +
+                               std::to_string(Pl.bs[1]) + "x" + std::to_string(Pl.bs[2]) + "x" +
+                               std::to_string(Pl.bs[3])).c_str(),
+                           0, P, nrhs);
+            TuneChoice tc;
+            if (tune_lookup(key, &tc)) {
+                stage = tc.variant;
+            } else if (tune_enabled() && ncy * (Pl.count[1] > 0 ? 2 : 1) >= 4) {
+                tuning = true;
+                LQCD_CUDA_CHECK(c, cudaEventCreate(&ev[0]));
+                LQCD_CUDA_CHECK(c, cudaEventCreate(&ev[1]));
+            }
+        }
+    }
     // the residual is not needed after the last sweep
     int last_col = Pl.count[1] > 0 ? 1 : 0;
+    int sweep = 0;
     for (int cyc = 0; cyc < ncy; cyc++)
         for (int col = 0; col < 2; col++) {
             if (Pl.count[col] == 0) continue;
             a.blocks = Pl.blocks_dev + (col == 0 ? 0 : Pl.count[0]);
+            if (tuning) {
+                stage = (sweep + 1) & 1;   // sweep 0 (cold caches) uses stage 1, then alternate
+                cudaEventRecord(ev[0], c->stream);
+            }
             if constexpr (P != LQCD_F64) {
-                if (resident && sap_stage_clover())
+                if (resident && stage)
                     k_sap_block_s<P, true>
                         <<<dim3(Pl.count[col], nrhs), 2 * Pl.B.nh, sizeof(SapSmem<P, true>), c->stream>>>(a);
                 else if (resident)
@@ -1208,11 +1246,31 @@ lqcd_status sap_run(lqcd_ctx *c, const SapPlan &P_, int ncy, int nmr, const void
             }
             c->n_kernel_launches++;
             LQCD_LAUNCH_CHECK(c);
+            if (tuning) {
+                cudaEventRecord(ev[1], c->stream);
+                LQCD_CUDA_CHECK(c, cudaEventSynchronize(ev[1]));
+                float ms = 0;
+                cudaEventElapsedTime(&ms, ev[0], ev[1]);
+                if (sweep > 0) best_us[stage] = std::min(best_us[stage], 1000.f * ms);
+                if (tune_verbose())
+                    fprintf(stderr, "tune %s: stage=%d sweep %d %.1f us\n", key.c_str(), stage, sweep, 1000.f * ms);
+            }
+            sweep++;
             if (cyc == ncy - 1 && col == last_col) continue;
             k_sap_face<P><<<dim3(div_up(2L * c->g.Vh, 128), nrhs), 128, 0, c->stream>>>(a, col);
             c->n_kernel_launches++;
             LQCD_LAUNCH_CHECK(c);
         }
+    if (tuning) {
+        cudaEventDestroy(ev[0]);
+        cudaEventDestroy(ev[1]);
+        TuneChoice tc;
+        tc.variant = best_us[1] < best_us[0] ? 1 : 0;
+        tc.tx = 2 * Pl.B.nh;
+        tc.ty = 1;
+        tc.us = best_us[tc.variant];
+        tune_store(key, tc);
+    }
     return LQCD_OK;
 }
 
@@ -1355,7 +1413,10 @@ lqcd_status sap_batch_run(lqcd_ctx *hc, SapBatch *b, const int *active)
                              (int)sizeof(SapSmem<P, false>));
         attr = true;
     }
-    const bool sa = sap_stage_clover();
+    // the batched sweeps are replayed from captured graphs, so no in-flight
+    // tuning here: the clover term goes through L1 (two to three CTAs per SM,
+    // the work queue's balance) unless the staged form is forced
+    const bool sa = sap_stage_forced() == 1;
     const auto *args = (const SapArgs<P> *)b->args;
     const int last_col = b->nblk[1] > 0 ? 1 : 0;
     for (int cyc = 0; cyc < b->ncy; cyc++)

@@ -1,7 +1,9 @@
-// Autotuner for launch shapes.  A kernel family registers candidate launch
-// configurations; the first call with a new key (kernel, mode, precision,
-// lattice, nrhs, GPU) times every candidate on the call's own operands with
-// CUDA events and keeps the fastest.  Choices persist in a small JSON file
+// Autotuner for launch shapes and kernel forms.  A kernel family registers
+// candidate launch configurations; the first call with a new key (kernel, mode,
+// precision, lattice, nrhs, GPU) times every candidate on the call's own
+// operands with CUDA events and keeps the fastest.  Kernels that update their
+// operands in place (the SAP block sweeps) are timed in flight instead: the
+// sweeps of the first application alternate between the candidate forms.  Choices persist in a small JSON file
 // ($LQCD_TUNE_CACHE, default $HOME/.cache/lqcd_tune.json) so later processes
 // skip the search.  Kernels whose results do not depend on the launch shape
 // (no reductions) are the only ones tuned, so tuning never changes numerics.
@@ -154,10 +156,10 @@ lqcd_status tune_time(lqcd_ctx *c, const std::function<lqcd_status()> &launch, i
     return LQCD_OK;
 }
 
-extern "C" lqcd_status lqcd_tune_reset(void)
+extern "C" LQCD_API lqcd_status lqcd_tune_reset(void)
 {
     std::lock_guard<std::mutex> lk(g_mu);
     g_cache.clear();
-    g_loaded = true;
+    g_loaded = false;   // the next lookup reads the cache file again
     return LQCD_OK;
 }

@@ -131,6 +131,7 @@ def lib():
             "lqcd_solve_W": [P, C.POINTER(SolverParams), D, P, P, I, C.POINTER(SolveInfo)],
             "lqcd_apply_Dhat_block": [P, C.POINTER(I), P, P],
             "lqcd_block_solve": [P, C.POINTER(BlockParams), P, P, C.POINTER(I), C.POINTER(D), C.POINTER(I)],
+            "lqcd_tune_reset": [],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -158,6 +159,12 @@ def lib():
         L.lqcd_batch_stats.restype = C.c_int
         _lib = L
     return _lib
+
+
+def tune_reset() -> None:
+    """Forget the autotuner's in-memory choices (the next lookup re-reads the
+    cache file named by LQCD_TUNE_CACHE)."""
+    lib().lqcd_tune_reset()
 
 
 def _ptr(t: torch.Tensor):
