@@ -404,6 +404,54 @@ LQCD_API lqcd_status lqcd_apply_Dhat_block(lqcd_ctx *ctx, const int bs[4], const
 LQCD_API lqcd_status lqcd_block_solve(lqcd_ctx *ctx, const lqcd_block_params *p, const double *eta_dev,
                                       double *psi_dev, int *iters, double *relres, int *status);
 
+/* ----------------------------------------------- MD forces and leapfrog step */
+/* The molecular-dynamics part of the two-flavour HMC (Sec. 2, Eq. 4), FP64.
+ * A link moves along U_mu(x) -> exp(eps T_a) U_mu(x), T_a = i lambda_a / 2
+ * (Gell-Mann lambda_a); every gradient is dS/d eps written to a caller-owned
+ * device array g[site][mu][a] of V x 4 x 8 doubles (lexicographic sites; the
+ * MD force is -g).  The context must hold the gauge field and its clover
+ * term (lqcd_set_gauge, lqcd_clover_invert); otherwise LQCD_ERR_STATE. */
+
+/* g = Re <Y, (dD/d eps) X> for every link and generator (hop and clover
+ * terms of D, Eq. 1); X, Y: canonical full FP64 fields. */
+LQCD_API lqcd_status lqcd_force_dD(lqcd_ctx *ctx, const double *X_dev, const double *Y_dev, double *g_dev);
+/* g = d log|det A_parity| / d eps = sum over the sites of that parity of
+ * Re tr(A^-1 dA) (the clover determinant of Eq. 4: S gets -2 log|det A_oo|). */
+LQCD_API lqcd_status lqcd_force_logdet(lqcd_ctx *ctx, int parity, double *g_dev);
+/* Wilson gauge action S_g = beta sum_P (1 - Re tr U_P / 3) (host scalar,
+ * synchronises) and its gradient. */
+LQCD_API lqcd_status lqcd_gauge_action(lqcd_ctx *ctx, double beta, double *S_host);
+LQCD_API lqcd_status lqcd_force_gauge(lqcd_ctx *ctx, double beta, double *g_dev);
+/* Gradient of the pseudofermion action |Dhat^-1 phi_e|^2 (Eq. 2, 4):
+ * -2 Re <y_e, dDhat x_e> with x_e = Dhat^-1 phi_e, y_e = Dhat^-dag x_e, both
+ * solved with the given solver parameters (info: host array of 2 entries or
+ * NULL); phi_e: canonical FP64 even field.  A solve that does not reach its
+ * tolerance returns its status (g is still written). */
+LQCD_API lqcd_status lqcd_force_pf(lqcd_ctx *ctx, const lqcd_solver_params *p, const double *phi_e_dev,
+                                   double *g_dev, lqcd_solve_info *info);
+
+typedef struct {
+    double beta;                 /* Wilson gauge coupling */
+    double dt;                   /* leapfrog step size */
+    int nsteps;                  /* leapfrog steps */
+    lqcd_solver_params solver;   /* the solves of the pseudofermion force */
+} lqcd_md_params;
+
+/* Total gradient of S = S_g + |Dhat^-1 phi_e|^2 - 2 log|det A_oo| (the
+ * even-odd factorised two-flavour action with the clover term, Eq. 2 and 4)
+ * at the context's gauge field; S_host (may be NULL) receives S. */
+LQCD_API lqcd_status lqcd_md_gradient(lqcd_ctx *ctx, const lqcd_md_params *p, const double *phi_e_dev,
+                                      double *g_dev, double *S_host);
+/* nsteps leapfrog steps of size dt (the integrator of Sec. 2):
+ *   p -= dt/2 g;  U <- exp(dt P) U (P = sum_a p^a T_a);  p -= dt/2 g.
+ * U_dev: canonical links (V x 4 x 3 x 3 complex), which must be the field the
+ * context holds on entry; on return U_dev and the context hold the evolved
+ * field with its clover term rebuilt (same kappa, c_sw).  p_dev: momenta
+ * V x 4 x 8 doubles, updated in place.  The exponential is a Taylor series
+ * after scaling and squaring; the links are not re-unitarised.  Synchronises. */
+LQCD_API lqcd_status lqcd_md_leapfrog(lqcd_ctx *ctx, const lqcd_md_params *p, double *U_dev, double *p_dev,
+                                      const double *phi_e_dev);
+
 /* ------------------------------------------------ batched multi-lattice solve */
 /* Several independent lattices (each its own context: gauge field, kappa,
  * clover term) solved together with the SAP-preconditioned flexible GCR of

@@ -337,6 +337,8 @@ lqcd_status clover_build(lqcd_ctx *c, double kappa, double csw, double *ld_e, do
     if (ld_o) *ld_o = h_sums[1];
     c->kappa = kappa;
     c->csw = csw;
+    c->logdet_e = h_sums[0];
+    c->logdet_o = h_sums[1];
     if (h_sing) {
         c->have_clover = false;
         return set_err(c, LQCD_ERR_SINGULAR_CLOVER, "%d singular 6x6 clover blocks", h_sing);

@@ -157,12 +157,13 @@ struct lqcd_ctx {
     uint2 *A16[2] = {nullptr, nullptr}, *Ai16[2] = {nullptr, nullptr};    // [18][Vh], FP16
     bool have_clover = false;
     double kappa = 0, csw = 0;
+    double logdet_e = 0, logdet_o = 0;   // log|det A| of each parity, from the last clover build
     // device scratch for reductions
     double *red = nullptr;        // partial sums
     double *red_out = nullptr;    // final reduction results (device)
     double *red_host = nullptr;   // pinned host mirror
     // named temporary buffers, grown on demand
-    Workspace ws[24];
+    Workspace ws[24];   // indexed by the WS_ slots below
     DflState *dfl = nullptr;
     NetState *net = nullptr;
     ChronoState *chrono = nullptr;
@@ -240,6 +241,10 @@ enum {
     WS_NET_FALLBACK,
     WS_HASEN,
     WS_PHI64,       // F64 preconditioner output converted into FP32 Krylov vectors
+    WS_MD_OMEGA,    // per-site clover force weights (MD forces)
+    WS_MD_SCRATCH,  // per-site partial sums (gauge action)
+    WS_MD_FIELDS,   // pseudofermion force fields
+    WS_MD_GRAD,     // MD gradient of the leapfrog step
 };
 lqcd_status ws_get(lqcd_ctx *c, int slot, size_t bytes, void **out);
 

@@ -60,6 +60,10 @@ class SolveInfo(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class MDParams(C.Structure):
+    _fields_ = [("beta", C.c_double), ("dt", C.c_double), ("nsteps", C.c_int), ("solver", SolverParams)]
+
+
 class BlockParams(C.Structure):
     _fields_ = [("bs", C.c_int * 4), ("tol", C.c_double), ("nmx", C.c_int)]
 
@@ -132,6 +136,13 @@ def lib():
             "lqcd_apply_Dhat_block": [P, C.POINTER(I), P, P],
             "lqcd_block_solve": [P, C.POINTER(BlockParams), P, P, C.POINTER(I), C.POINTER(D), C.POINTER(I)],
             "lqcd_tune_reset": [],
+            "lqcd_force_dD": [P, P, P, P],
+            "lqcd_force_logdet": [P, I, P],
+            "lqcd_gauge_action": [P, D, C.POINTER(D)],
+            "lqcd_force_gauge": [P, D, P],
+            "lqcd_force_pf": [P, C.POINTER(SolverParams), P, P, C.POINTER(SolveInfo)],
+            "lqcd_md_gradient": [P, C.POINTER(MDParams), P, P, C.POINTER(D)],
+            "lqcd_md_leapfrog": [P, C.POINTER(MDParams), P, P, P],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -431,6 +442,66 @@ class Context:
         if check:
             self._check(st, "solve_dhat_guess")
         return psi, [i.as_dict() for i in info], st
+
+    # ------------------------------------------------- MD forces (Sec. 2, Eq. 4)
+    def _grad(self):
+        return torch.empty((self.V, 4, 8), dtype=torch.float64, device="cuda")
+
+    def force_dD(self, X: torch.Tensor, Y: torch.Tensor) -> torch.Tensor:
+        """Re <Y, dD X> per link and generator, (V, 4, 8) float64."""
+        X = X.to(torch.complex128).contiguous()
+        Y = Y.to(torch.complex128).contiguous()
+        g = self._grad()
+        self._check(lib().lqcd_force_dD(self._h, _ptr(X), _ptr(Y), _ptr(g)), "force_dD")
+        return g
+
+    def force_logdet(self, parity: int) -> torch.Tensor:
+        g = self._grad()
+        self._check(lib().lqcd_force_logdet(self._h, parity, _ptr(g)), "force_logdet")
+        return g
+
+    def gauge_action(self, beta: float) -> float:
+        S = C.c_double(0)
+        self._check(lib().lqcd_gauge_action(self._h, beta, C.byref(S)), "gauge_action")
+        return S.value
+
+    def force_gauge(self, beta: float) -> torch.Tensor:
+        g = self._grad()
+        self._check(lib().lqcd_force_gauge(self._h, beta, _ptr(g)), "force_gauge")
+        return g
+
+    @staticmethod
+    def md_solver(solver=SOLVER_SAP_GCR, tol=1e-12, nkv=16, nmx=4096, bs=(4, 4, 4, 4), ncy=4, nmr=5, sap_prec=F64,
+                  inner=F64, krylov=F64) -> SolverParams:
+        return SolverParams(solver, nkv, nmx, tol, sap_params(bs, ncy, nmr, sap_prec), inner, krylov)
+
+    def force_pf(self, phi_e: torch.Tensor, sp: SolverParams = None):
+        """Gradient of |Dhat^-1 phi_e|^2; returns (g, [info of the two solves])."""
+        phi_e = phi_e.to(torch.complex128).contiguous()
+        sp = sp or self.md_solver()
+        g = self._grad()
+        info = (SolveInfo * 2)()
+        self._check(lib().lqcd_force_pf(self._h, C.byref(sp), _ptr(phi_e), _ptr(g), info), "force_pf")
+        return g, [i.as_dict() for i in info]
+
+    def md_gradient(self, phi_e: torch.Tensor, beta: float, sp: SolverParams = None):
+        """(gradient of S = S_g + |Dhat^-1 phi|^2 - 2 log|det A_oo|, S)."""
+        phi_e = phi_e.to(torch.complex128).contiguous()
+        mp = MDParams(beta, 0.0, 0, sp or self.md_solver())
+        g = self._grad()
+        S = C.c_double(0)
+        self._check(lib().lqcd_md_gradient(self._h, C.byref(mp), _ptr(phi_e), _ptr(g), C.byref(S)), "md_gradient")
+        return g, S.value
+
+    def md_leapfrog(self, U: torch.Tensor, p: torch.Tensor, phi_e: torch.Tensor, beta: float, dt: float,
+                    nsteps: int, sp: SolverParams = None):
+        """nsteps leapfrog steps; U (canonical links, the context's field) and p
+        ((V, 4, 8) float64 momenta) are updated in place."""
+        assert U.dtype == torch.complex128 and U.is_contiguous()
+        assert p.dtype == torch.float64 and p.is_contiguous()
+        phi_e = phi_e.to(torch.complex128).contiguous()
+        mp = MDParams(beta, dt, nsteps, sp or self.md_solver())
+        self._check(lib().lqcd_md_leapfrog(self._h, C.byref(mp), _ptr(U), _ptr(p), _ptr(phi_e)), "md_leapfrog")
 
     def chrono_reset(self, nkeep: int):
         self._check(lib().lqcd_chrono_reset(self._h, nkeep), "chrono_reset")
