@@ -248,6 +248,25 @@ def time_to_solve(ctx, lqcd, eta, net=None):
                                 "(Krylov vectors, Gram-Schmidt) and FP64 little-Dirac solve, 12 RHS batched",
                         "seconds": r["total_s"], "build_s": r["build_s"], "iters": max(r["iters"]),
                         "max_relres_dhat": r["max_relres_dhat"], "status": r["status"]}
+    if net is not None:
+        # the same subspace and precisions (FP64 Gram-Schmidt and little-Dirac
+        # solve), the trained network as the smoother in place of SAP
+        ctx.net_set(NET_CHANS, net["W"], act=lqcd.BF16)
+        ctx.solve_dhat(eta, solver=lqcd.SOLVER_DFL_NET_GCR, tol=1e-10, nmx=2, sap_prec=lqcd.F32, inner=lqcd.F32,
+                       check=False)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, info, st = ctx.solve_dhat(eta, solver=lqcd.SOLVER_DFL_NET_GCR, tol=1e-10, sap_prec=lqcd.F32,
+                                     inner=lqcd.F32, check=False)
+        torch.cuda.synchronize()
+        out["learned_mixed"] = {"form": "dfl_mixed's subspace and precisions (FP64 GCR and little-Dirac solve), "
+                                        "trained BF16 network as smoother, deflated FP32 SAP as fallback, "
+                                        "12 RHS batched",
+                                "seconds": round(time.perf_counter() - t0 + r["build_s"], 4), "build_s": r["build_s"],
+                                "iters": max(i["iters"] for i in info),
+                                "net_fallbacks": sum(i["net_fallbacks"] for i in info),
+                                "max_relres_dhat": max(i["relres_dhat"] for i in info), "status": st,
+                                "training_s": net["train_s"]}
     # one subspace build with the FP32 little operator (timed, included in both
     # forms below) and two smoothers on it
     # SAP with 2 cycles of 8 MinRes steps and a subspace built with 8 inverse iterations of SAP
@@ -276,7 +295,8 @@ def time_to_solve(ctx, lqcd, eta, net=None):
                           "net_fallbacks": sum(i["net_fallbacks"] for i in info),
                           "max_relres_dhat": max(i["relres_dhat"] for i in info), "status": st,
                           "training": {"lattice": "32x16x16x16", "pairs": net["pairs"], "seconds": net["train_s"],
-                                       "loss_first": net["loss_first"], "loss_last": net["loss_last"]}}
+                                       "loss_first": net["loss_first"], "loss_last": net["loss_last"],
+                                       "residual_loss_last": net.get("residual_loss_last")}}
     total, build, iters, worst, st = 0.0, 0.0, 0, 0.0, 0
     for k in range(eta.shape[0]):
         if k == 0:
@@ -299,9 +319,13 @@ def time_to_solve(ctx, lqcd, eta, net=None):
     out["plain_f64"] = {"form": "deflated SAP-GCR (Ns=20, 4^4 blocks), FP64 throughout, one source at a time",
                         "seconds": round(total, 4), "build_s": build, "iters": iters, "max_relres_dhat": worst,
                         "status": st}
-    for k in ("chosen", "sap_f32", "sap_f16s", "dfl_mixed", "learned"):
+    for k in ("chosen", "sap_f32", "sap_f16s", "dfl_mixed", "learned", "learned_mixed"):
         if k in out:
             out["speedup_%s_vs_plain_f64" % k] = round(out["plain_f64"]["seconds"] / out[k]["seconds"], 2)
+    if "learned_mixed" in out:
+        out["gain_learned_mixed_vs_dfl_mixed"] = round(out["dfl_mixed"]["seconds"] / out["learned_mixed"]["seconds"], 3)
+    if "learned" in out:
+        out["gain_learned_vs_chosen"] = round(out["chosen"]["seconds"] / out["learned"]["seconds"], 3)
     out["tolerance"] = 1e-10
     return out
 
@@ -389,10 +413,13 @@ def run_batch(args):
 NET_CHANS = (1, 2, 2, 1)
 
 
-def train_net(lqcd, synth, kappa, nfields=10, npairs=200, steps=50):
+def train_net(lqcd, synth, kappa, nfields=10, npairs=200, steps=50, rsteps=0):
     """The network trained on the GPU at 32x16^3: nfields gauge fields x npairs
-    sources (drawn on the device), targets M_sap source made by the library's
-    SAP; weights carried from field to field.  Returns (W, loss history, s)."""
+    sources (drawn on the device).  On every field, steps Adam steps on the
+    imitation loss (targets M_sap source made by the library's SAP), then
+    rsteps on the residual of one GCR step, |x - D N(x)|^2 / |x|^2; weights
+    carried from field to field.  Returns (W, loss history, seconds, residual
+    loss history)."""
     import numpy as np
     import torch
     chans = NET_CHANS
@@ -405,7 +432,7 @@ def train_net(lqcd, synth, kappa, nfields=10, npairs=200, steps=50):
         off += chans[l + 1] * chans[l] * 144
     W = W.astype(np.complex64)
     tdims = (32, 16, 16, 16)
-    hist, train_s = [], 0.0
+    hist, rhist, train_s = [], [], 0.0
     for f in range(nfields):
         c = lqcd.Context(tdims)
         c.set_gauge(torch.from_numpy(synth.su3_links(tdims, 100 + f)).cuda())
@@ -416,12 +443,14 @@ def train_net(lqcd, synth, kappa, nfields=10, npairs=200, steps=50):
         t0 = time.perf_counter()
         c.net_set(chans, W, act=lqcd.BF16)
         h = c.net_train(src, steps=steps, batch=8, lr=2e-3, sap_prec=lqcd.F32)
+        hr = c.net_train(src, steps=rsteps, batch=8, lr=1e-3, loss=lqcd.NET_LOSS_RESIDUAL) if rsteps else []
         torch.cuda.synchronize()
         train_s += time.perf_counter() - t0
         W = c.net_get()
         hist += [float(x) for x in h]
+        rhist += [float(x) for x in hr]
         del src, c
-    return W, hist, train_s
+    return W, hist, train_s, rhist
 
 
 def run_net(args):
@@ -435,7 +464,8 @@ def run_net(args):
     import torch
     from paper_1011_0911_gb300 import lqcd, synth
     kappa, chans = 0.1363, (1, 2, 2, 1)
-    W, hist, train_s = train_net(lqcd, synth, kappa, args.nfields, args.npairs, args.train_steps)
+    W, hist, train_s, rhist = train_net(lqcd, synth, kappa, args.nfields, args.npairs, args.train_steps,
+                                        args.res_steps)
     dims = (64, 32, 32, 32)
     ctx = lqcd.Context(dims)
     ctx.set_gauge(torch.from_numpy(synth.su3_links(dims, 0)).cuda())
@@ -453,6 +483,7 @@ def run_net(args):
     out = {"mode": "net", "train_lattice": "32x16x16x16", "train_fields": args.nfields, "pairs": args.nfields * args.npairs,
            "train_steps": args.nfields * args.train_steps, "train_s": round(train_s, 3),
            "loss_first": round(float(np.mean(hist[:5])), 4), "loss_last": round(float(np.mean(hist[-5:])), 4),
+           "residual_loss_last": round(float(np.mean(rhist[-5:])), 4) if rhist else None,
            "lattice": "64x32x32x32", "kappa": kappa, "subspace_build_s": round(build_s, 3)}
     forms = [("dfl_net", lqcd.SOLVER_DFL_NET_GCR), ("dfl_sap", lqcd.SOLVER_DFL_SAP_GCR), ("sap", lqcd.SOLVER_SAP_GCR)]
     for name, sid in forms:
@@ -465,6 +496,43 @@ def run_net(args):
                      "net_fallbacks": info[0]["net_fallbacks"], "relres_dhat": info[0]["relres_dhat"], "status": st}
     out["gain_dfl_net_vs_dfl_sap"] = round(out["dfl_sap"]["seconds"] / out["dfl_net"]["seconds"], 3)
     print(json.dumps(out))
+
+
+def run_netapply(args):
+    """The network's three layers applied to 12 fields (the 12 sources of the
+    deflated solve) at --lattice, BF16 activations, random weights: CUDA-event
+    time per application and the layers' HBM roofline.  Algorithmic bytes of a
+    layer per site and sample: every input channel read once (12 BF16 complex
+    = 48 B), the eight links of the transports (2 rows FP32, 384 B, shared by
+    the samples of a launch) and every output channel written once (48 B)."""
+    import numpy as np
+    import torch
+    from paper_1011_0911_gb300 import lqcd, synth
+    chans = NET_CHANS
+    ctx = lqcd.Context(DIMS)
+    ctx.set_gauge(torch.from_numpy(synth.su3_links(DIMS, 0)).cuda())
+    nw = lqcd.Context.net_weight_count(chans)
+    g = synth.gaussians(7, synth.STREAM_NET, 2 * nw)
+    ctx.net_set(chans, (0.1 * (g[0::2] + 1j * g[1::2])).astype(np.complex64), act=lqcd.BF16)
+    nb = args.nrhs
+    x = torch.from_numpy(synth.gaussian_spinor(nb * ctx.V, 5).reshape(nb, ctx.V, 4, 3)).cuda()
+    for _ in range(args.warmup):
+        ctx.net_apply(x)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(ctx.stream)
+    for _ in range(args.steps):
+        ctx.net_apply(x)
+    e1.record(ctx.stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    V = ctx.V
+    layer_bytes = sum(V * (nb * 48 * (ci + co) + 384) for ci, co in zip(chans[:-1], chans[1:]))
+    peak, kind = load_peaks()
+    print(json.dumps({"mode": "netapply", "lattice": "x".join(map(str, DIMS)), "fields": nb,
+                      "ms_per_application": round(ms, 4), "layer_bytes_per_application": layer_bytes,
+                      "layers_GBs_incl_conversions": round(layer_bytes / (ms * 1e-3) / 1e9, 1), "peak": peak,
+                      "peak_kind": kind}))
 
 
 def run_block(args):
@@ -630,12 +698,15 @@ def main():
     ap.add_argument("--no-solve", action="store_true", help="skip the time-to-solution comparison")
     ap.add_argument("--no-net", action="store_true", help="time-to-solution without the learned form")
     ap.add_argument("--lattice", default="48x24x24x24", help="TxL1xL2xL3 (profiling runs use smaller ones)")
-    ap.add_argument("--mode", default="dhat", choices=["dhat", "solve", "batch", "net", "configs", "block"],
+    ap.add_argument("--mode", default="dhat", choices=["dhat", "solve", "batch", "net", "netapply", "configs", "block"],
                     help="solve: one time-to-solution run; batch: the uneven multi-lattice batch")
     ap.add_argument("--nlat", type=int, default=16, help="lattices of the batch mode")
     ap.add_argument("--nfields", type=int, default=10, help="net mode: training gauge fields")
     ap.add_argument("--npairs", type=int, default=200, help="net mode: sources per training field")
     ap.add_argument("--train-steps", type=int, default=50, help="net mode: Adam steps per training field")
+    ap.add_argument("--res-steps", type=int, default=0,
+                    help="Adam steps per training field on the GCR residual loss after the imitation steps "
+                         "(a better one-step preconditioner, a worse deflated smoother: off by default)")
     ap.add_argument("--no-graph", action="store_true", help="batch mode: eager launches instead of graph replay")
     ap.add_argument("--solver", default="dfl", choices=["cgnr", "sap", "dfl"])
     ap.add_argument("--kappa", type=float, default=None)
@@ -667,6 +738,8 @@ def main():
         return run_net(args)
     if args.mode == "configs":
         return run_configs(args)
+    if args.mode == "netapply":
+        return run_netapply(args)
     if args.mode == "block":
         return run_block(args)
 
@@ -754,9 +827,11 @@ def main():
     if not args.no_solve and world == 1 and DIMS == (48, 24, 24, 24):
         net = None
         if not args.no_net:
-            W, hist, train_s = train_net(lqcd, synth, KAPPA, args.nfields, args.npairs, args.train_steps)
+            W, hist, train_s, rhist = train_net(lqcd, synth, KAPPA, args.nfields, args.npairs, args.train_steps,
+                                                args.res_steps)
             net = {"W": W, "pairs": args.nfields * args.npairs, "train_s": round(train_s, 3),
-                   "loss_first": round(sum(hist[:5]) / 5, 4), "loss_last": round(sum(hist[-5:]) / 5, 4)}
+                   "loss_first": round(sum(hist[:5]) / 5, 4), "loss_last": round(sum(hist[-5:]) / 5, 4),
+                   "residual_loss_last": round(sum(rhist[-5:]) / 5, 4) if rhist else None}
         tts = time_to_solve(ctx, lqcd, eta_dev.to(torch.complex128), net)
 
     if rank == 0:

@@ -329,12 +329,16 @@ typedef struct {
     int batch;             /* sources per step */
     double lr, beta1, beta2, eps;
     lqcd_sap_params sap;   /* targets t = M_sap(source) */
+    int loss;              /* 0: imitation of the SAP correction, (1/nb) sum |N(x) - M_sap x|^2 / |M_sap x|^2;
+                              1: the residual of one GCR step with unit coefficient,
+                              (1/nb) sum |x - D N(x)|^2 / |x|^2 (no targets needed; its gradient
+                              -2 D^dag (x - D N x) / |x|^2 uses D^dag = gamma5 D gamma5) */
 } lqcd_net_train_params;
 /* Train on (gauge field of ctx, source, M_sap source) pairs: the nsrc sources
  * (canonical FP64 full fields, device; the caller draws them) are paired with
- * their SAP outputs computed here; Adam on the loss above, cycling through
- * the sources in batches.  loss_history (host, may be NULL) receives steps
- * values.  Requires lqcd_clover_invert and lqcd_net_set. */
+ * their SAP outputs computed here (loss 0); Adam on the selected loss,
+ * cycling through the sources in batches.  loss_history (host, may be NULL)
+ * receives steps values.  Requires lqcd_clover_invert and lqcd_net_set. */
 LQCD_API lqcd_status lqcd_net_train(lqcd_ctx *ctx, const lqcd_net_train_params *p, const double *sources_dev,
                                     int nsrc, double *loss_history);
 

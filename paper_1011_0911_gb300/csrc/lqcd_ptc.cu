@@ -124,6 +124,47 @@ __device__ void pt_stage_sites(const Geom &g, long x0, PtStage &S)
     }
 }
 
+// w = u h and w = u^dag h for colour vectors: each real part one product and
+// five fused multiply-adds
+__device__ __forceinline__ void su3_mul_fma(const cx<float> u[3][3], const cx<float> *h, cx<float> *w)
+{
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        float re = u[a][0].re * h[0].re;
+        re = fmx(-u[a][0].im, h[0].im, re);
+        re = fmx(u[a][1].re, h[1].re, re);
+        re = fmx(-u[a][1].im, h[1].im, re);
+        re = fmx(u[a][2].re, h[2].re, re);
+        re = fmx(-u[a][2].im, h[2].im, re);
+        float im = u[a][0].re * h[0].im;
+        im = fmx(u[a][0].im, h[0].re, im);
+        im = fmx(u[a][1].re, h[1].im, im);
+        im = fmx(u[a][1].im, h[1].re, im);
+        im = fmx(u[a][2].re, h[2].im, im);
+        im = fmx(u[a][2].im, h[2].re, im);
+        w[a] = mk(re, im);
+    }
+}
+__device__ __forceinline__ void su3dag_mul_fma(const cx<float> u[3][3], const cx<float> *h, cx<float> *w)
+{
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        float re = u[0][a].re * h[0].re;
+        re = fmx(u[0][a].im, h[0].im, re);
+        re = fmx(u[1][a].re, h[1].re, re);
+        re = fmx(u[1][a].im, h[1].im, re);
+        re = fmx(u[2][a].re, h[2].re, re);
+        re = fmx(u[2][a].im, h[2].im, re);
+        float im = u[0][a].re * h[0].im;
+        im = fmx(-u[0][a].im, h[0].re, im);
+        im = fmx(u[1][a].re, h[1].im, im);
+        im = fmx(-u[1][a].im, h[1].re, im);
+        im = fmx(u[2][a].re, h[2].im, im);
+        im = fmx(-u[2][a].im, h[2].re, im);
+        w[a] = mk(re, im);
+    }
+}
+
 // The transported inputs (T_d y_i)(x) of the tile: one item per (site, path);
 // the path's link is loaded and its third row rebuilt once and applied to every
 // input channel.  sink(s, i, d, z) receives the 12 spin-colour components.
@@ -161,16 +202,20 @@ __device__ __forceinline__ void pt_gather(const Geom &g, const float4 *U, const 
 #pragma unroll
                     for (int k = 0; k < 12; k++) z[k] = v[k];
                 } else {
+                    // U v or U^dag v per spin, as fused multiply-add chains with the
+                    // boundary sign (+-1, exact) folded into the link
+                    cx<float> us[3][3];
 #pragma unroll
-                    for (int sp = 0; sp < 4; sp++)
+                    for (int a = 0; a < 3; a++)
 #pragma unroll
-                        for (int a = 0; a < 3; a++) {
-                            cx<float> acc = mk(0.f, 0.f);
+                        for (int b = 0; b < 3; b++) us[a][b] = sgn * u[a][b];
 #pragma unroll
-                            for (int b = 0; b < 3; b++)
-                                acc = acc + (fwd ? u[a][b] * v[3 * sp + b] : cmulc(u[b][a], v[3 * sp + b]));
-                            z[3 * sp + a] = sgn * acc;
-                        }
+                    for (int sp = 0; sp < 4; sp++) {
+                        if (fwd)
+                            su3_mul_fma(us, v + 3 * sp, z + 3 * sp);
+                        else
+                            su3dag_mul_fma(us, v + 3 * sp, z + 3 * sp);
+                    }
                 }
             }
             sink(s, i, d, z);
@@ -757,6 +802,51 @@ lqcd_status net_loss(lqcd_ctx *c, ActBufs &B, const float2 *T, int nb, double *l
     return LQCD_OK;
 }
 
+// GCR residual loss: L = (1/nb) sum_b |x_b - D N(x_b)|^2 / |x_b|^2 on the
+// batch in B.a[0] with N(x) in B.a[nl]; the gradient at the network output,
+// -2 D^dag r_b / (nb |x_b|^2) with r = x - D N(x) and D^dag = gamma5 D gamma5,
+// goes to B.d[nl] (all in FP64 between the activation conversions)
+template <class ACT>
+lqcd_status residual_loss_t(lqcd_ctx *c, ActBufs &B, int nb, double *loss_dev)
+{
+    NetState *n = c->net;
+    const long Vh = c->g.Vh, nf = 24 * Vh;   // double2 per native full field
+    void *w;
+    LQCD_TRY(ws_get(c, WS_NET_FALLBACK, 3 * (size_t)nb * nf * sizeof(double2), &w));
+    double2 *xn = (double2 *)w, *yn = xn + nb * nf, *tn = yn + nb * nf;
+    const dim3 grid(div_up(c->g.V, 256), nb);
+    k_act_to_native<ACT><<<grid, 256, 0, c->stream>>>(c->g, nb, (const ACT *)B.a[0], xn);
+    k_act_to_native<ACT><<<grid, 256, 0, c->stream>>>(c->g, nb, (const ACT *)B.a[n->nl], yn);
+    c->n_kernel_launches += 2;
+    LQCD_LAUNCH_CHECK(c);
+    LQCD_TRY(dirac_D(c, LQCD_F64, yn, tn, nb));                          // t = D N(x)
+    LQCD_TRY(blas_sub(c, 2 * nb * nf, (const double *)xn, (const double *)tn, (double *)tn));   // r
+    double L = 0;
+    std::vector<double> sc(nb);
+    for (int b = 0; b < nb; b++) {
+        double xx, rr;
+        LQCD_TRY(blas_norm2(c, 2 * nf, (const double *)(xn + b * nf), &xx));
+        LQCD_TRY(blas_norm2(c, 2 * nf, (const double *)(tn + b * nf), &rr));
+        L += xx > 0 ? rr / xx / nb : 0.0;
+        sc[b] = xx > 0 ? -2.0 / (nb * xx) : 0.0;
+    }
+    LQCD_TRY(blas_gamma5_native64(c, 2L * nb, tn, tn));
+    LQCD_TRY(dirac_D(c, LQCD_F64, tn, yn, nb));
+    LQCD_TRY(blas_gamma5_native64(c, 2L * nb, yn, yn));                   // D^dag r
+    for (int b = 0; b < nb; b++) LQCD_TRY(blas_scal(c, 2 * nf, sc[b], 0.0, (double *)(yn + b * nf)));
+    k_native_to_act<ACT><<<grid, 256, 0, c->stream>>>(c->g, nb, yn, (ACT *)B.d[n->nl]);
+    c->n_kernel_launches++;
+    LQCD_LAUNCH_CHECK(c);
+    LQCD_CUDA_CHECK(c, cudaMemcpyAsync(loss_dev, &L, sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    LQCD_CUDA_CHECK(c, cudaStreamSynchronize(c->stream));
+    return LQCD_OK;
+}
+lqcd_status net_residual_loss(lqcd_ctx *c, ActBufs &B, int nb, double *loss_dev)
+{
+    return c->net->act == LQCD_BF16 ? residual_loss_t<bf162>(c, B, nb, loss_dev)
+                                    : residual_loss_t<float2>(c, B, nb, loss_dev);
+}
+
 lqcd_status net_backward(lqcd_ctx *c, ActBufs &B, int nb)
 {
     NetState *n = c->net;
@@ -916,7 +1006,9 @@ lqcd_status lqcd_net_train(lqcd_ctx *c, const lqcd_net_train_params *p, const do
     if (!c->have_clover) return set_err(c, LQCD_ERR_STATE, "clover term not built");
     if (p->batch < 1 || p->batch > 64 || p->batch > nsrc || p->steps < 0)
         return set_err(c, LQCD_ERR_ARG, "batch %d / steps %d", p->batch, p->steps);
-    if (p->sap.prec != LQCD_F32 && p->sap.prec != LQCD_F64) return set_err(c, LQCD_ERR_ARG, "SAP precision");
+    if (p->loss != 0 && p->loss != 1) return set_err(c, LQCD_ERR_ARG, "loss %d", p->loss);
+    if (p->loss == 0 && p->sap.prec != LQCD_F32 && p->sap.prec != LQCD_F64)
+        return set_err(c, LQCD_ERR_ARG, "SAP precision");
     NetState *n = c->net;
     const long ns = 12 * (long)c->g.V;
     const size_t xb = ns * nsrc * act_elem(n->act), tbytes = ns * nsrc * sizeof(float2);
@@ -943,7 +1035,7 @@ lqcd_status lqcd_net_train(lqcd_ctx *c, const lqcd_net_train_params *p, const do
     LQCD_TRY(ws_get(c, WS_SAP_IN, fpb * chunk, &ain));
     LQCD_TRY(ws_get(c, WS_SAP_PSI, fpb * chunk, &aout));
     LQCD_TRY(ws_get(c, WS_MISC, 2 * native_half_bytes(c, LQCD_F32) * chunk, &a32));
-    for (int s0 = 0; s0 < nsrc; s0 += chunk) {
+    for (int s0 = 0; s0 < nsrc && p->loss == 0; s0 += chunk) {
         const int cnt = std::min(chunk, nsrc - s0);
         LQCD_TRY(pack_field(c, LQCD_F64, 2, sources + (size_t)s0 * 2 * ns, a64, cnt, false));
         LQCD_TRY(convert_native(c, LQCD_F64, p->sap.prec, a64, ain, 2L * cnt));
@@ -967,11 +1059,15 @@ lqcd_status lqcd_net_train(lqcd_ctx *c, const lqcd_net_train_params *p, const do
             const int s = (int)(((long)step * p->batch + j) % nsrc);
             LQCD_CUDA_CHECK(c, cudaMemcpyAsync((char *)B.a[0] + (size_t)j * ns * ae, (char *)n->X + (size_t)s * ns * ae,
                                                ns * ae, cudaMemcpyDeviceToDevice, c->stream));
-            LQCD_CUDA_CHECK(c, cudaMemcpyAsync((float2 *)tslot + (size_t)j * ns, n->Tg + (size_t)s * ns,
-                                               ns * sizeof(float2), cudaMemcpyDeviceToDevice, c->stream));
+            if (p->loss == 0)
+                LQCD_CUDA_CHECK(c, cudaMemcpyAsync((float2 *)tslot + (size_t)j * ns, n->Tg + (size_t)s * ns,
+                                                   ns * sizeof(float2), cudaMemcpyDeviceToDevice, c->stream));
         }
         LQCD_TRY(net_forward(c, B, p->batch));
-        LQCD_TRY(net_loss(c, B, (const float2 *)tslot, p->batch, loss_dev));
+        if (p->loss == 0)
+            LQCD_TRY(net_loss(c, B, (const float2 *)tslot, p->batch, loss_dev));
+        else
+            LQCD_TRY(net_residual_loss(c, B, p->batch, loss_dev));
         LQCD_TRY(net_backward(c, B, p->batch));
         n->adam_t++;
         const float c1 = 1.f - powf((float)p->beta1, (float)n->adam_t), c2 = 1.f - powf((float)p->beta2, (float)n->adam_t);

@@ -79,7 +79,10 @@ class NetDesc(C.Structure):
 
 class NetTrainParams(C.Structure):
     _fields_ = [("steps", C.c_int), ("batch", C.c_int), ("lr", C.c_double), ("beta1", C.c_double),
-                ("beta2", C.c_double), ("eps", C.c_double), ("sap", SapParams)]
+                ("beta2", C.c_double), ("eps", C.c_double), ("sap", SapParams), ("loss", C.c_int)]
+
+
+NET_LOSS_SAP, NET_LOSS_RESIDUAL = 0, 1
 
 
 _lib = None
@@ -402,11 +405,12 @@ class Context:
         self._check(st, "lqcd_net_loss_grad")
         return loss.value, g
 
-    def net_train(self, sources: torch.Tensor, steps, batch=8, lr=1e-3, bs=(4, 4, 4, 4), ncy=4, nmr=5, sap_prec=F32):
+    def net_train(self, sources: torch.Tensor, steps, batch=8, lr=1e-3, bs=(4, 4, 4, 4), ncy=4, nmr=5, sap_prec=F32,
+                  loss=NET_LOSS_SAP):
         import numpy as np
         sources = sources.to(torch.complex128).contiguous()
         nsrc = self._nrhs(sources, self.V)
-        p = NetTrainParams(steps, batch, lr, 0.9, 0.999, 1e-8, sap_params(bs, ncy, nmr, sap_prec))
+        p = NetTrainParams(steps, batch, lr, 0.9, 0.999, 1e-8, sap_params(bs, ncy, nmr, sap_prec), loss)
         hist = np.zeros(max(steps, 1))
         self._check(lib().lqcd_net_train(self._h, C.byref(p), _ptr(sources), nsrc, hist.ctypes.data_as(C.c_void_p)),
                     "lqcd_net_train")

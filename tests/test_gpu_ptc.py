@@ -119,22 +119,21 @@ def test_net_set_rejects_bad_shapes():
         P.ctx.net_apply(torch.zeros((1, P.V, 4, 3), dtype=torch.complex128).cuda())
 
 
-def one_step_residual(ctx, eta, phi):
-    """|eta - D phi| / |eta| for each field."""
-    r = eta - ctx.apply_D(phi)
-    return (torch.linalg.vector_norm(r.reshape(len(eta), -1), dim=1) /
-            torch.linalg.vector_norm(eta.reshape(len(eta), -1), dim=1)).cpu().numpy()
-
-
-def scalar_residual(ctx, eta):
-    """min over alpha of |eta - alpha D eta| / |eta|: the best scaled identity."""
-    De = ctx.apply_D(eta)
+def gcr_step_residual(ctx, eta, phi):
+    """Residual after one GCR step from zero with direction phi:
+    min over complex alpha of |eta - alpha D phi| / |eta|, per field."""
+    Dp = ctx.apply_D(phi)
     out = []
     for b in range(len(eta)):
-        e, d = eta[b].reshape(-1), De[b].reshape(-1)
+        e, d = eta[b].reshape(-1), Dp[b].reshape(-1)
         a = torch.vdot(d, e) / torch.vdot(d, d)
         out.append((torch.linalg.vector_norm(e - a * d) / torch.linalg.vector_norm(e)).item())
     return np.array(out)
+
+
+def sap_step_residual(P, eta, ncy, nmr):
+    phi = torch.stack([P.ctx.sap(eta[b], ncy=ncy, nmr=nmr, prec=lqcd.F32) for b in range(len(eta))])
+    return gcr_step_residual(P.ctx, eta, phi)
 
 
 @pytest.fixture(scope="module")
@@ -154,14 +153,34 @@ def test_training_reduces_loss(trained):
     assert hist[-10:].mean() < 0.7 * hist[:4].mean(), (hist[:4], hist[-10:])
 
 
-def test_trained_net_gain(trained):
-    """On sources it has not seen, the trained network is a better one-step
-    preconditioner of D than the best multiple of the identity."""
-    P, _ = trained
+def test_trained_net_gain_over_sap():
+    """What the trained network gains over the method without it (SAP), one
+    GCR step on sources it has not seen.  Cost of one application to one field
+    at 32x16^3 through the same entry points, measured on a GB300: network
+    0.236 ms, SAP with 1 cycle x 1 / 2 / 3 MinRes steps 0.186 / 0.207 / 0.230
+    ms, 2 x 2 0.348 ms.
+      - trained on the SAP corrections (imitation): better than the cheaper
+        SAP 1 x 1 (measured 0.288 vs 0.334);
+      - then trained on the residual of one GCR step, |x - D N(x)|^2 / |x|^2:
+        better than SAP of equal cost, 1 x 3 (measured 0.231 vs 0.259);
+      - SAP with two cycles stays far ahead (measured 0.099), and inside the
+        deflated solve no network variant beats the SAP smoother."""
+    P = Pair((8, 8, 8, 8), kappa=0.1355, csw=1.9)
+    P.ctx.net_set(CHANS, rand_weights(CHANS, 14, scale=0.02, ident=0.7), act=lqcd.BF16)
+    src = torch.from_numpy(sources(P.V, 16, 100)).cuda()
+    P.ctx.net_train(src, steps=120, batch=4, lr=4e-3, sap_prec=lqcd.F32)
     eta = torch.from_numpy(sources(P.V, 4, 500)).cuda()
-    r_net = one_step_residual(P.ctx, eta, P.ctx.net_apply(eta))
-    r_id = scalar_residual(P.ctx, eta)
-    assert np.all(r_net < 0.9 * r_id), (r_net, r_id)
+    r_imit = gcr_step_residual(P.ctx, eta, P.ctx.net_apply(eta))
+    r_sap11 = sap_step_residual(P, eta, 1, 1)
+    assert np.all(r_imit < 0.95 * r_sap11), (r_imit, r_sap11)
+    hist = P.ctx.net_train(src, steps=200, batch=4, lr=2e-3, loss=lqcd.NET_LOSS_RESIDUAL)
+    assert hist[-5:].mean() < 0.7 * hist[:2].mean()   # measured 0.053 after 0.094
+    r_res = gcr_step_residual(P.ctx, eta, P.ctx.net_apply(eta))
+    assert np.all(r_res < r_imit)
+    r_sap13 = sap_step_residual(P, eta, 1, 3)
+    assert np.all(r_res < 0.95 * r_sap13), (r_res, r_sap13)
+    r_sap22 = sap_step_residual(P, eta, 2, 2)
+    assert np.all(r_sap22 < 0.6 * r_res), (r_sap22, r_res)
 
 
 @pytest.mark.parametrize("inner", [lqcd.F64, lqcd.F32], ids=["f64-krylov", "f32-krylov"])
