@@ -194,6 +194,15 @@ def solve_once(ctx, lqcd, eta, solver, inner, Ns=20, ninv=8, ctol=1e-2, seed=100
     return res, psi
 
 
+# solver parameters of every deflated form of the time-to-solution table (the
+# forms differ only in precision and batching): Ns = 20 subspace fields built by
+# 6 inverse iterations of SAP with 6 cycles x 4 MinRes steps, SAP smoother with
+# 1 cycle x 4 MinRes steps, little-Dirac GCR of 64 steps with Krylov length 32,
+# chosen by timing whole 12-source solves at 48x24^3 (bench.py --mode solve with
+# --ninv/--bncy/--bnmr/--ncy/--nmr/--cnmx/--cnkv)
+DFL_NINV, DFL_BUILD_SAP, DFL_SAP, DFL_CNMX, DFL_CNKV = 6, (6, 4), (1, 4), 64, 32
+
+
 def time_to_solve(ctx, lqcd, eta, net=None):
     """Time-to-solution of Dhat psi = eta for the 12 sources to a true relative
     residual <= 1e-10 (checked in FP64), subspace builds included:
@@ -218,18 +227,20 @@ def time_to_solve(ctx, lqcd, eta, net=None):
     for spr, inner in ((lqcd.F32, lqcd.F32), (lqcd.F16S, lqcd.F32), (lqcd.F64, lqcd.F64)):
         ctx.solve_dhat(eta, solver=lqcd.SOLVER_SAP_GCR, tol=1e-10, nmx=2, sap_prec=spr, inner=inner, check=False)
     v0 = torch.from_numpy(synth.gaussian_spinor(20 * ctx.V, 100, synth.STREAM_SUBSPACE).reshape(20, ctx.V, 4, 3)).cuda()
+    sncy, snmr = DFL_SAP
     for prec in (lqcd.F64, lqcd.F32):
-        ctx.dfl_build(v0, bs=(4, 4, 4, 4), ninv=1, ncy=4, nmr=4, prec=prec, coarse_tol=1e-2, coarse_nmx=64,
-                      coarse_prec=prec)
+        ctx.dfl_build(v0, bs=(4, 4, 4, 4), ninv=1, ncy=DFL_BUILD_SAP[0], nmr=DFL_BUILD_SAP[1], prec=prec,
+                      coarse_tol=1e-2, coarse_nmx=DFL_CNMX, coarse_nkv=DFL_CNKV, coarse_prec=prec)
         e = one if prec == lqcd.F64 else eta
-        ctx.solve_dhat(e, solver=lqcd.SOLVER_DFL_SAP_GCR, tol=1e-10, nmx=2, sap_prec=prec, inner=prec, check=False)
+        ctx.solve_dhat(e, solver=lqcd.SOLVER_DFL_SAP_GCR, tol=1e-10, nmx=2, sap_prec=prec, inner=prec, check=False,
+                       ncy=sncy, nmr=snmr)
         if prec == lqcd.F32:
             ctx.solve_dhat(eta, solver=lqcd.SOLVER_DFL_SAP_GCR, tol=1e-10, nmx=2, sap_prec=lqcd.F16S, inner=prec,
-                           check=False, krylov=lqcd.F32)
+                           check=False, krylov=lqcd.F32, ncy=sncy, nmr=snmr)
         if prec == lqcd.F32 and net is not None:
             ctx.net_set(NET_CHANS, net["W"], act=lqcd.BF16)
             ctx.solve_dhat(eta, solver=lqcd.SOLVER_DFL_NET_GCR, tol=1e-10, nmx=2, sap_prec=prec, inner=prec,
-                           check=False, krylov=lqcd.F32)
+                           check=False, krylov=lqcd.F32, ncy=sncy, nmr=snmr)
     del v0
     torch.cuda.synchronize()
     r, _ = solve_once(ctx, lqcd, eta, "sap", "f32")
@@ -243,7 +254,9 @@ def time_to_solve(ctx, lqcd, eta, net=None):
                        "seconds": round(time.perf_counter() - t0, 4), "iters": max(i["iters"] for i in info),
                        "max_relres_dhat": max(i["relres_dhat"] for i in info), "status": st}
     # the workload's stated precisions: its own subspace build (FP64 little operator)
-    r, _ = solve_once(ctx, lqcd, eta, "dfl", "f32", Ns=20, ninv=8, ctol=1e-2, cnmx=64, cprec="f64")
+    dflp = dict(Ns=20, ninv=DFL_NINV, ctol=1e-2, cnmx=DFL_CNMX, cnkv=DFL_CNKV, ncy=sncy, nmr=snmr,
+                bncy=DFL_BUILD_SAP[0], bnmr=DFL_BUILD_SAP[1])
+    r, _ = solve_once(ctx, lqcd, eta, "dfl", "f32", cprec="f64", **dflp)
     out["dfl_mixed"] = {"form": "deflated SAP-GCR (Ns=20, 4^4 blocks), FP32 SAP/subspace/stencil, FP64 GCR "
                                 "(Krylov vectors, Gram-Schmidt) and FP64 little-Dirac solve, 12 RHS batched",
                         "seconds": r["total_s"], "build_s": r["build_s"], "iters": max(r["iters"]),
@@ -253,11 +266,11 @@ def time_to_solve(ctx, lqcd, eta, net=None):
         # solve), the trained network as the smoother in place of SAP
         ctx.net_set(NET_CHANS, net["W"], act=lqcd.BF16)
         ctx.solve_dhat(eta, solver=lqcd.SOLVER_DFL_NET_GCR, tol=1e-10, nmx=2, sap_prec=lqcd.F32, inner=lqcd.F32,
-                       check=False)
+                       check=False, ncy=sncy, nmr=snmr)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         _, info, st = ctx.solve_dhat(eta, solver=lqcd.SOLVER_DFL_NET_GCR, tol=1e-10, sap_prec=lqcd.F32,
-                                     inner=lqcd.F32, check=False)
+                                     inner=lqcd.F32, check=False, ncy=sncy, nmr=snmr)
         torch.cuda.synchronize()
         out["learned_mixed"] = {"form": "dfl_mixed's subspace and precisions (FP64 GCR and little-Dirac solve), "
                                         "trained BF16 network as smoother, deflated FP32 SAP as fallback, "
@@ -269,14 +282,11 @@ def time_to_solve(ctx, lqcd, eta, net=None):
                                 "training_s": net["train_s"]}
     # one subspace build with the FP32 little operator (timed, included in both
     # forms below) and two smoothers on it
-    # SAP with 2 cycles of 8 MinRes steps and a subspace built with 8 inverse iterations of SAP
-    # (4 cycles x 6 steps): the fastest of the settings measured for this form at 48x24^3
-    r, _ = solve_once(ctx, lqcd, eta, "dfl", "f32", Ns=20, ninv=8, ctol=1e-2, cnmx=64, cprec="f32",
-                      sap_prec=lqcd.F16S, krylov="f32", ncy=2, nmr=8, bncy=4, bnmr=6)
+    r, _ = solve_once(ctx, lqcd, eta, "dfl", "f32", cprec="f32", sap_prec=lqcd.F16S, krylov="f32", **dflp)
     build = r["build_s"]
-    out["chosen"] = {"form": "deflated SAP-GCR (Ns=20, 4^4 blocks), FP16 (per-site scale) SAP (2 cycles x 8 "
-                             "MinRes steps), FP32 subspace, stencil, little-Dirac solve and GCR Krylov vectors; "
-                             "FP64 residual, solution and restarts; 12 RHS batched",
+    out["chosen"] = {"form": "deflated SAP-GCR (Ns=20, 4^4 blocks), FP16 (per-site scale) SAP, FP32 subspace, "
+                             "stencil, little-Dirac solve and GCR Krylov vectors; FP64 residual, solution and "
+                             "restarts; 12 RHS batched",
                      "seconds": r["total_s"], "build_s": build, "iters": max(r["iters"]), "net_fallbacks": 0,
                      "max_relres_dhat": r["max_relres_dhat"], "status": r["status"]}
     if net is not None:
@@ -285,7 +295,7 @@ def time_to_solve(ctx, lqcd, eta, net=None):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         _, info, st = ctx.solve_dhat(eta, solver=lqcd.SOLVER_DFL_NET_GCR, tol=1e-10, sap_prec=lqcd.F32,
-                                     inner=lqcd.F32, check=False, krylov=lqcd.F32)
+                                     inner=lqcd.F32, check=False, krylov=lqcd.F32, ncy=sncy, nmr=snmr)
         torch.cuda.synchronize()
         out["learned"] = {"form": "deflated GCR (Ns=20), trained BF16 network as smoother, deflated FP32 SAP as "
                                   "fallback, the chosen form's FP32 subspace / little-Dirac solve / Krylov vectors, "
@@ -300,8 +310,7 @@ def time_to_solve(ctx, lqcd, eta, net=None):
     total, build, iters, worst, st = 0.0, 0.0, 0, 0.0, 0
     for k in range(eta.shape[0]):
         if k == 0:
-            r, _ = solve_once(ctx, lqcd, eta[k:k + 1].contiguous(), "dfl", "f64", Ns=20, ninv=8, ctol=1e-2,
-                              cnmx=64, cprec="f64")
+            r, _ = solve_once(ctx, lqcd, eta[k:k + 1].contiguous(), "dfl", "f64", cprec="f64", **dflp)
             build = r["build_s"]
             total += r["total_s"]
         else:   # the subspace is reused for the other sources
@@ -309,7 +318,7 @@ def time_to_solve(ctx, lqcd, eta, net=None):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             psi, info, s = ctx.solve_dhat(eta[k:k + 1].contiguous(), solver=sid, tol=1e-10, sap_prec=lqcd.F64,
-                                          inner=lqcd.F64, check=False)
+                                          inner=lqcd.F64, check=False, ncy=sncy, nmr=snmr)
             torch.cuda.synchronize()
             total += time.perf_counter() - t0
             r = {"iters": [info[0]["iters"]], "max_relres_dhat": info[0]["relres_dhat"], "status": s}
@@ -476,8 +485,8 @@ def run_net(args):
     v0 = torch.from_numpy(synth.gaussian_spinor(Ns * ctx.V, 100, synth.STREAM_SUBSPACE).reshape(Ns, ctx.V, 4, 3)).cuda()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    ctx.dfl_build(v0, bs=(4, 4, 4, 4), ninv=8, ncy=4, nmr=4, prec=lqcd.F32, coarse_tol=1e-2, coarse_nmx=64,
-                  coarse_prec=lqcd.F32)
+    ctx.dfl_build(v0, bs=(4, 4, 4, 4), ninv=DFL_NINV, ncy=DFL_BUILD_SAP[0], nmr=DFL_BUILD_SAP[1], prec=lqcd.F32,
+                  coarse_tol=1e-2, coarse_nmx=DFL_CNMX, coarse_nkv=DFL_CNKV, coarse_prec=lqcd.F32)
     torch.cuda.synchronize()
     build_s = time.perf_counter() - t0
     out = {"mode": "net", "train_lattice": "32x16x16x16", "train_fields": args.nfields, "pairs": args.nfields * args.npairs,
@@ -487,10 +496,12 @@ def run_net(args):
            "lattice": "64x32x32x32", "kappa": kappa, "subspace_build_s": round(build_s, 3)}
     forms = [("dfl_net", lqcd.SOLVER_DFL_NET_GCR), ("dfl_sap", lqcd.SOLVER_DFL_SAP_GCR), ("sap", lqcd.SOLVER_SAP_GCR)]
     for name, sid in forms:
-        ctx.solve_dhat(eta, solver=sid, tol=1e-10, sap_prec=lqcd.F32, inner=lqcd.F32, check=False)   # warm-up
+        # the deflated forms take the time-to-solution table's SAP smoother, plain SAP-GCR its own 4 x 5
+        sp = dict(ncy=DFL_SAP[0], nmr=DFL_SAP[1]) if sid != lqcd.SOLVER_SAP_GCR else dict(ncy=4, nmr=5)
+        ctx.solve_dhat(eta, solver=sid, tol=1e-10, sap_prec=lqcd.F32, inner=lqcd.F32, check=False, **sp)   # warm-up
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        _, info, st = ctx.solve_dhat(eta, solver=sid, tol=1e-10, sap_prec=lqcd.F32, inner=lqcd.F32, check=False)
+        _, info, st = ctx.solve_dhat(eta, solver=sid, tol=1e-10, sap_prec=lqcd.F32, inner=lqcd.F32, check=False, **sp)
         torch.cuda.synchronize()
         out[name] = {"seconds": round(time.perf_counter() - t0, 4), "iters": info[0]["iters"],
                      "net_fallbacks": info[0]["net_fallbacks"], "relres_dhat": info[0]["relres_dhat"], "status": st}
