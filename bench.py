@@ -155,7 +155,7 @@ KAPPA_OF = {(8, 8, 8, 8): 0.1355, (32, 16, 16, 16): 0.1357, (48, 24, 24, 24): 0.
 
 
 def solve_once(ctx, lqcd, eta, solver, inner, Ns=20, ninv=8, ctol=1e-2, seed=100, cnmx=4096, cnkv=16, cprec=None,
-               nkv=16, sap_prec=None, krylov=None, ncy=4, nmr=5, bncy=4, bnmr=4):
+               nkv=16, sap_prec=None, krylov=None, ncy=4, nmr=5, bncy=4, bnmr=4, bprec=None):
     """Time-to-solution of Dhat psi = eta (all fields of eta) to 1e-10 with the
     given solver; the subspace build is timed separately and included in total."""
     import torch
@@ -171,6 +171,7 @@ def solve_once(ctx, lqcd, eta, solver, inner, Ns=20, ninv=8, ctol=1e-2, seed=100
         t0 = time.perf_counter()
         cp = prec if cprec is None else (lqcd.F32 if cprec == "f32" else lqcd.F64)
         ctx.dfl_build(v0, bs=(4, 4, 4, 4), ninv=ninv, ncy=bncy, nmr=bnmr, prec=prec, coarse_tol=ctol,
+                      build_sap_prec=bprec,
                       coarse_nkv=cnkv, coarse_nmx=cnmx, coarse_prec=cp)
         torch.cuda.synchronize()
         build_s = time.perf_counter() - t0
@@ -282,9 +283,11 @@ def time_to_solve(ctx, lqcd, eta, net=None):
                                 "training_s": net["train_s"]}
     # one subspace build with the FP32 little operator (timed, included in both
     # forms below) and two smoothers on it
-    r, _ = solve_once(ctx, lqcd, eta, "dfl", "f32", cprec="f32", sap_prec=lqcd.F16S, krylov="f32", **dflp)
+    r, _ = solve_once(ctx, lqcd, eta, "dfl", "f32", cprec="f32", sap_prec=lqcd.F16S, krylov="f32", bprec=lqcd.F16S,
+                      **dflp)
     build = r["build_s"]
-    out["chosen"] = {"form": "deflated SAP-GCR (Ns=20, 4^4 blocks), FP16 (per-site scale) SAP, FP32 subspace, "
+    out["chosen"] = {"form": "deflated SAP-GCR (Ns=20, 4^4 blocks), FP16 (per-site scale) SAP in the solve and the "
+                             "subspace build, FP32 subspace, "
                              "stencil, little-Dirac solve and GCR Krylov vectors; FP64 residual, solution and "
                              "restarts; 12 RHS batched",
                      "seconds": r["total_s"], "build_s": build, "iters": max(r["iters"]), "net_fallbacks": 0,
@@ -352,6 +355,7 @@ def run_solve(args):
         res, _ = solve_once(ctx, lqcd, eta, args.solver, args.prec, Ns=args.Ns, ninv=args.ninv, ctol=args.ctol,
                             cnmx=args.cnmx, cnkv=args.cnkv, cprec=args.cprec, nkv=args.nkv,
                             krylov=args.krylov, ncy=args.ncy, nmr=args.nmr, bncy=args.bncy, bnmr=args.bnmr,
+                            bprec={"f16s": lqcd.F16S, "f32": lqcd.F32}.get(args.bprec),
                             sap_prec={"f16s": lqcd.F16S, "f32": lqcd.F32, "f64": lqcd.F64}.get(args.sap_prec))
     res["nkv"] = args.nkv
     res["ncy"], res["nmr"] = args.ncy, args.nmr
@@ -735,6 +739,8 @@ def main():
     ap.add_argument("--nmr", type=int, default=5, help="solve mode: MinRes steps per SAP block solve")
     ap.add_argument("--bncy", type=int, default=4, help="solve mode: SAP cycles in the subspace build")
     ap.add_argument("--bnmr", type=int, default=4, help="solve mode: SAP MinRes steps in the subspace build")
+    ap.add_argument("--bprec", default=None, choices=["f16s", "f32"],
+                    help="solve mode: precision of the subspace build's SAP (default: the subspace's)")
     ap.add_argument("--sap-prec", default=None, choices=["f16s", "f32", "f64"], help="solve mode: SAP precision")
     args = ap.parse_args()
     global DIMS

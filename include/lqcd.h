@@ -227,11 +227,16 @@ typedef struct {
                               Gram-Schmidt in float; GCR scalars and the sums of the
                               per-CTA partial inner products in FP64).  With LQCD_F32
                               coarse_tol must be >= 1e-6, else LQCD_ERR_ARG */
+    lqcd_prec build_sap_prec; /* LQCD_F16S: the inverse-iteration SAP of an FP32 subspace runs in
+                                 FP16 with per-site scale (each pass converts the fields to F16S
+                                 and back); any other value: the SAP runs in prec */
 } lqcd_dfl_params;
 
 /* Build the deflation subspace ("locally deflated" solver, Sec. 3-4,
  * Table 1): v_l <- M_sap v_l, normalised, ninv times; block Gram-Schmidt on
- * every block; little Dirac operator A_{(L k),(L' l)} = <phi^L_k, D phi^L'_l>.
+ * every block; little Dirac operator A_{(L k),(L' l)} = <phi^L_k, D phi^L'_l>
+ * (FP64 arithmetic for an FP64 subspace, FP32 products with FP64 sums over
+ * warps for an FP32 one).
  * v0_dev: Ns canonical FP64 full fields (the random start vectors; the
  * caller draws them).  Requires lqcd_clover_invert. */
 LQCD_API lqcd_status lqcd_dfl_build(lqcd_ctx *ctx, const lqcd_dfl_params *p, const double *v0_dev);

@@ -17,6 +17,7 @@
 #include <vector>
 
 #include "lqcd_internal.cuh"
+#include "lqcd_stencil.cuh"
 
 namespace {
 
@@ -318,6 +319,143 @@ __global__ void k_little_build(Geom g, DBlk B, const T *phi, int Ns, long fstrid
                 }
             }
             block_sum(d, 2 * kn, sh, res);
+            if (t < kn) Aint[(((long)b * 9 + j) * Ns + k0 + t) * Ns + l] = make_double2(res[2 * t], res[2 * t + 1]);
+            __syncthreads();
+        }
+    }
+}
+
+// FP32 hop: acc += sign (1 -+ g_mu) U psi (dag: U^dag), runtime direction
+__device__ __forceinline__ void hop1f(int mu, int sgn, const stencil::Spinor<float> &psi, const cx<float> u[3][3],
+                                      bool dag, float sign, stencil::Spinor<float> &acc)
+{
+    cx<float> h[2][3];
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        const cx<float> u0 = psi.s[0][c], u1 = psi.s[1][c], l0 = psi.s[2][c], l1 = psi.s[3][c];
+        cx<float> e0, e1;
+        switch (mu) {
+            case 0: e0 = -l0; e1 = -l1; break;
+            case 1: e0 = timesmI(l1); e1 = timesmI(l0); break;
+            case 2: e0 = -l1; e1 = l0; break;
+            default: e0 = timesmI(l0); e1 = timesI(l1); break;
+        }
+        h[0][c] = sgn < 0 ? u0 - e0 : u0 + e0;
+        h[1][c] = sgn < 0 ? u1 - e1 : u1 + e1;
+    }
+    cx<float> w[2][3];
+#pragma unroll
+    for (int sp = 0; sp < 2; sp++) {
+        if (dag)
+            stencil::su3dag_vec(u, h[sp], w[sp]);
+        else
+            stencil::su3_vec(u, h[sp], w[sp]);
+    }
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        cx<float> e0, e1;   // e_mu^dag w
+        switch (mu) {
+            case 0: e0 = -w[0][a]; e1 = -w[1][a]; break;
+            case 1: e0 = timesI(w[1][a]); e1 = timesI(w[0][a]); break;
+            case 2: e0 = w[1][a]; e1 = -w[0][a]; break;
+            default: e0 = timesI(w[0][a]); e1 = timesmI(w[1][a]); break;
+        }
+        if (sgn < 0) {
+            e0 = -e0;
+            e1 = -e1;
+        }
+        acc.s[0][a].re = fmx(sign, w[0][a].re, acc.s[0][a].re);
+        acc.s[0][a].im = fmx(sign, w[0][a].im, acc.s[0][a].im);
+        acc.s[1][a].re = fmx(sign, w[1][a].re, acc.s[1][a].re);
+        acc.s[1][a].im = fmx(sign, w[1][a].im, acc.s[1][a].im);
+        acc.s[2][a].re = fmx(sign, e0.re, acc.s[2][a].re);
+        acc.s[2][a].im = fmx(sign, e0.im, acc.s[2][a].im);
+        acc.s[3][a].re = fmx(sign, e1.re, acc.s[3][a].re);
+        acc.s[3][a].im = fmx(sign, e1.im, acc.s[3][a].im);
+    }
+}
+
+// The little Dirac build of an FP32 subspace in FP32 arithmetic: the FP32
+// operator (2-row links, FP32 clover), FP32 products and per-thread sums,
+// warp sums in float and the sum over warps in double.  The subspace itself is
+// FP32, so its entries carry FP32 accuracy either way; GB300's FP64 pipe made
+// the FP64 form of this kernel the largest single cost of the subspace build.
+__global__ void k_little_build32(Geom g, DBlk B, const float4 *phi, int Ns, long fstride, const float4 *U32,
+                                 const float4 *A0, const float4 *A1, double2 *Aint)
+{
+    extern __shared__ double sh[];
+    double *res = sh + 2 * RCHUNK * 32;
+    const int b = blockIdx.x, l = blockIdx.y, t = threadIdx.x;
+    BSite s;
+    bsite(g, B, b, t, s);
+    const long hs = fstride / 2;
+    const float4 *pl = phi + l * fstride;
+    for (int j = 0; j < 9; j++) {
+        stencil::Spinor<float> w;
+#pragma unroll
+        for (int sp = 0; sp < 4; sp++)
+#pragma unroll
+            for (int c = 0; c < 3; c++) w.s[sp][c] = mk(0.f, 0.f);
+        if (j == 0) {
+            stencil::Spinor<float> v;
+            stencil::load_spinor(pl + s.p * hs, g.Vh, (int)s.r, v);
+            stencil::clover_apply<float, float4>(s.p ? A1 : A0, g.Vh, (int)s.r, v, w);
+        }
+        stencil::Spinor<float> acc;
+#pragma unroll
+        for (int sp = 0; sp < 4; sp++)
+#pragma unroll
+            for (int c = 0; c < 3; c++) acc.s[sp][c] = mk(0.f, 0.f);
+        for (int mu = 0; mu < 4; mu++)
+            for (int d = -1; d <= 1; d += 2) {
+                const int jj = d > 0 ? 1 + 2 * mu : 2 + 2 * mu;
+                const int lm = s.l[mu] + d;
+                const bool inside = (lm >= 0 && lm < B.bs[mu]) || B.wrap[mu];
+                if ((j == 0) != inside) continue;
+                if (j != 0 && j != jj) continue;
+                int y[4] = {s.x[0], s.x[1], s.x[2], s.x[3]};
+                y[mu] = (y[mu] + d + g.L[mu]) % g.L[mu];
+                const int ry = coords_rank(g, y);
+                stencil::Spinor<float> v;
+                cx<float> u[3][3];
+                stencil::load_spinor(pl + (1 - s.p) * hs, g.Vh, ry, v);
+                if (d > 0) {
+                    const float sign = (mu == 0 && s.x[0] == g.L[0] - 1) ? (float)g.bc_t : 1.f;
+                    stencil::load_link(U32, g.Vh, s.p, mu, (int)s.r, u);
+                    hop1f(mu, -1, v, u, false, sign, acc);
+                } else {
+                    const float sign = (mu == 0 && s.x[0] == 0) ? (float)g.bc_t : 1.f;
+                    stencil::load_link(U32, g.Vh, 1 - s.p, mu, ry, u);
+                    hop1f(mu, +1, v, u, true, sign, acc);
+                }
+            }
+#pragma unroll
+        for (int sp = 0; sp < 4; sp++)
+#pragma unroll
+            for (int c = 0; c < 3; c++) {
+                w.s[sp][c].re = fmx(-0.5f, acc.s[sp][c].re, w.s[sp][c].re);
+                w.s[sp][c].im = fmx(-0.5f, acc.s[sp][c].im, w.s[sp][c].im);
+            }
+        for (int k0 = 0; k0 < Ns; k0 += RCHUNK) {
+            float dd[2 * RCHUNK];
+            const int kn = min(RCHUNK, Ns - k0);
+#pragma unroll
+            for (int i = 0; i < RCHUNK; i++) {
+                dd[2 * i] = dd[2 * i + 1] = 0.f;
+                if (i < kn) {
+                    stencil::Spinor<float> q;
+                    stencil::load_spinor(phi + (k0 + i) * fstride + s.p * hs, g.Vh, (int)s.r, q);
+#pragma unroll
+                    for (int sp = 0; sp < 4; sp++)
+#pragma unroll
+                        for (int c = 0; c < 3; c++) {
+                            const cx<float> a = q.s[sp][c], z = w.s[sp][c];
+                            dd[2 * i] = fmx(a.re, z.re, fmx(a.im, z.im, dd[2 * i]));
+                            dd[2 * i + 1] = fmx(a.re, z.im, fmx(-a.im, z.re, dd[2 * i + 1]));
+                        }
+                }
+            }
+            block_sum_f<2 * RCHUNK>(dd, 2 * kn, sh, res);
             if (t < kn) Aint[(((long)b * 9 + j) * Ns + k0 + t) * Ns + l] = make_double2(res[2 * t], res[2 * t + 1]);
             __syncthreads();
         }
@@ -1245,10 +1383,22 @@ lqcd_status lqcd_dfl_build(lqcd_ctx *c, const lqcd_dfl_params *p, const double *
     sp.prec = p->prec;
     void *tmp;
     LQCD_TRY(ws_get(c, WS_SAP_PSI, fbytes * p->Ns, &tmp));
+    const bool half_sap = p->prec == LQCD_F32 && p->build_sap_prec == LQCD_F16S;
+    void *h_in = nullptr, *h_out = tmp;   // an F16S field is smaller than an F32 one
+    if (half_sap) {
+        sp.prec = LQCD_F16S;
+        LQCD_TRY(ws_get(c, WS_SAP_IN, 2 * native_half_bytes(c, LQCD_F16S) * p->Ns, &h_in));
+    }
     for (int pass = 0; pass < p->ninv; pass++) {
         // all Ns vectors through one batched SAP application
-        LQCD_TRY(sap_apply(c, &sp, d->phi, tmp, p->Ns));
-        LQCD_CUDA_CHECK(c, cudaMemcpyAsync(d->phi, tmp, fbytes * p->Ns, cudaMemcpyDeviceToDevice, c->stream));
+        if (half_sap) {
+            LQCD_TRY(convert_native(c, LQCD_F32, LQCD_F16S, d->phi, h_in, 2L * p->Ns));
+            LQCD_TRY(sap_apply(c, &sp, h_in, h_out, p->Ns));
+            LQCD_TRY(convert_native(c, LQCD_F16S, LQCD_F32, h_out, d->phi, 2L * p->Ns));
+        } else {
+            LQCD_TRY(sap_apply(c, &sp, d->phi, tmp, p->Ns));
+            LQCD_CUDA_CHECK(c, cudaMemcpyAsync(d->phi, tmp, fbytes * p->Ns, cudaMemcpyDeviceToDevice, c->stream));
+        }
         for (int l = 0; l < p->Ns; l++) {
             void *vl = (char *)d->phi + l * fbytes;
             double n2;
@@ -1284,8 +1434,8 @@ lqcd_status lqcd_dfl_build(lqcd_ctx *c, const lqcd_dfl_params *p, const double *
         k_little_build<double2><<<grid, B.vol, sm2, c->stream>>>(c->g, B, (const double2 *)d->phi, p->Ns, fe,
                                                                 c->U64, c->A64[0], c->A64[1], d->Aint);
     else
-        k_little_build<float4><<<grid, B.vol, sm2, c->stream>>>(c->g, B, (const float4 *)d->phi, p->Ns, fe,
-                                                               c->U64, c->A64[0], c->A64[1], d->Aint);
+        k_little_build32<<<grid, B.vol, sm2, c->stream>>>(c->g, B, (const float4 *)d->phi, p->Ns, fe, c->U32,
+                                                          c->A32[0], c->A32[1], d->Aint);
     c->n_kernel_launches++;
     LQCD_LAUNCH_CHECK(c);
     // block-Jacobi preconditioner of the coarse solve: inverses of the diagonal blocks

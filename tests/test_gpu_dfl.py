@@ -51,6 +51,31 @@ def test_subspace_parity_fp32_build(ninv):
     assert relerr(phi, P.o.dfl_subspace()) < 1e-6
     rho = synth.gaussian_spinor(P.V, 31)
     assert relerr(P.ctx.dfl_project(to_gpu(rho)), P.o.dfl_project(rho)) < 1e-6
+    # the little operator of the FP32 subspace, built in FP32 arithmetic
+    assert util.relerr(dense_little(P, A.cpu().numpy()), P.o.dfl_little()) < 1e-5
+
+
+def dense_little(P, Ah):
+    """The dense little operator from its block-row form: entry j of block b
+    couples to the neighbour block reached by j (0: itself, 1 + 2mu: +mu, 2 + 2mu: -mu)."""
+    nblk, Ns = P.ctx.nblk, P.ctx.Ns
+    Ad = np.zeros((nblk * Ns, nblk * Ns), dtype=np.complex128)
+    nb = [L // 4 for L in P.dims]
+
+    def step(b, mu, d):
+        c = [0] * 4
+        u = b
+        for i in (3, 2, 1, 0):
+            c[i] = u % nb[i]
+            u //= nb[i]
+        c[mu] = (c[mu] + d) % nb[mu]
+        return c[3] + nb[3] * (c[2] + nb[2] * (c[1] + nb[1] * c[0]))
+
+    for b in range(nblk):
+        for j in range(9):
+            n = b if j == 0 else step(b, (j - 1) // 2, 1 if j % 2 == 1 else -1)
+            Ad[b * Ns:(b + 1) * Ns, n * Ns:(n + 1) * Ns] += Ah[b, j]
+    return Ad
 
 
 def test_little_operator_parity(built):
