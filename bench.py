@@ -155,7 +155,7 @@ KAPPA_OF = {(8, 8, 8, 8): 0.1355, (32, 16, 16, 16): 0.1357, (48, 24, 24, 24): 0.
 
 
 def solve_once(ctx, lqcd, eta, solver, inner, Ns=20, ninv=8, ctol=1e-2, seed=100, cnmx=4096, cnkv=16, cprec=None,
-               nkv=16, sap_prec=None, krylov=None, ncy=4, nmr=5, bncy=4, bnmr=4, bprec=None):
+               nkv=16, sap_prec=None, krylov=None, ncy=4, nmr=5, bncy=4, bnmr=4, bprec=None, ceo=False):
     """Time-to-solution of Dhat psi = eta (all fields of eta) to 1e-10 with the
     given solver; the subspace build is timed separately and included in total."""
     import torch
@@ -169,24 +169,27 @@ def solve_once(ctx, lqcd, eta, solver, inner, Ns=20, ninv=8, ctol=1e-2, seed=100
                               .reshape(Ns, ctx.V, 4, 3)).cuda()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
+        l0 = ctx.kernel_launches
         cp = prec if cprec is None else (lqcd.F32 if cprec == "f32" else lqcd.F64)
         ctx.dfl_build(v0, bs=(4, 4, 4, 4), ninv=ninv, ncy=bncy, nmr=bnmr, prec=prec, coarse_tol=ctol,
-                      build_sap_prec=bprec,
+                      build_sap_prec=bprec, coarse_eo=ceo,
                       coarse_nkv=cnkv, coarse_nmx=cnmx, coarse_prec=cp)
         torch.cuda.synchronize()
         build_s = time.perf_counter() - t0
         res.update({"Ns": Ns, "ninv": ninv, "build_sap": [bncy, bnmr], "coarse_tol": ctol, "coarse_nmx": cnmx,
-                    "coarse_nkv": cnkv,
-                    "coarse_prec": "f32" if cp == lqcd.F32 else "f64", "build_s": round(build_s, 4)})
+                    "coarse_nkv": cnkv, "coarse_eo": bool(ceo),
+                    "coarse_prec": "f32" if cp == lqcd.F32 else "f64", "build_s": round(build_s, 4),
+                    "build_launches": ctx.kernel_launches - l0})
     sid = {"cgnr": lqcd.SOLVER_CGNR, "sap": lqcd.SOLVER_SAP_GCR, "dfl": lqcd.SOLVER_DFL_SAP_GCR}[solver]
     t0 = time.perf_counter()
+    l0 = ctx.kernel_launches
     sp = prec if sap_prec is None else sap_prec
     kr = lqcd.F32 if krylov == "f32" else lqcd.F64
     psi, info, st = ctx.solve_dhat(eta, solver=sid, tol=1e-10, nmx=20000 if solver == "cgnr" else 4096,
                                    nkv=nkv, sap_prec=sp, inner=prec, check=False, krylov=kr, ncy=ncy, nmr=nmr)
     torch.cuda.synchronize()
     solve_s = time.perf_counter() - t0
-    res.update({"krylov": "f32" if kr == lqcd.F32 else "f64",
+    res.update({"krylov": "f32" if kr == lqcd.F32 else "f64", "solve_launches": ctx.kernel_launches - l0,
                 "status": st, "solve_s": round(solve_s, 4), "total_s": round(solve_s + build_s, 4),
                 "iters": [i["iters"] for i in info],
                 "max_relres_dhat": max(i["relres_dhat"] for i in info)})
@@ -198,10 +201,12 @@ def solve_once(ctx, lqcd, eta, solver, inner, Ns=20, ninv=8, ctol=1e-2, seed=100
 # solver parameters of every deflated form of the time-to-solution table (the
 # forms differ only in precision and batching): Ns = 20 subspace fields built by
 # 6 inverse iterations of SAP with 6 cycles x 4 MinRes steps, SAP smoother with
-# 1 cycle x 4 MinRes steps, little-Dirac GCR of 64 steps with Krylov length 32,
-# chosen by timing whole 12-source solves at 48x24^3 (bench.py --mode solve with
-# --ninv/--bncy/--bnmr/--ncy/--nmr/--cnmx/--cnkv)
+# 1 cycle x 4 MinRes steps, little-Dirac GCR of 64 steps with Krylov length 32
+# (32 steps in the even-odd form used with the FP32 little operator), chosen by
+# timing whole 12-source solves at 48x24^3 (bench.py --mode solve with
+# --ninv/--bncy/--bnmr/--ncy/--nmr/--cnmx/--cnkv/--ceo)
 DFL_NINV, DFL_BUILD_SAP, DFL_SAP, DFL_CNMX, DFL_CNKV = 6, (6, 4), (1, 4), 64, 32
+DFL_CEO, DFL_CNMX_EO = True, 32
 
 
 def time_to_solve(ctx, lqcd, eta, net=None):
@@ -231,7 +236,7 @@ def time_to_solve(ctx, lqcd, eta, net=None):
     sncy, snmr = DFL_SAP
     for prec in (lqcd.F64, lqcd.F32):
         ctx.dfl_build(v0, bs=(4, 4, 4, 4), ninv=1, ncy=DFL_BUILD_SAP[0], nmr=DFL_BUILD_SAP[1], prec=prec,
-                      coarse_tol=1e-2, coarse_nmx=DFL_CNMX, coarse_nkv=DFL_CNKV, coarse_prec=prec)
+                      coarse_tol=1e-2, coarse_nmx=DFL_CNMX, coarse_nkv=DFL_CNKV, coarse_prec=prec, coarse_eo=DFL_CEO)
         e = one if prec == lqcd.F64 else eta
         ctx.solve_dhat(e, solver=lqcd.SOLVER_DFL_SAP_GCR, tol=1e-10, nmx=2, sap_prec=prec, inner=prec, check=False,
                        ncy=sncy, nmr=snmr)
@@ -256,7 +261,7 @@ def time_to_solve(ctx, lqcd, eta, net=None):
                        "max_relres_dhat": max(i["relres_dhat"] for i in info), "status": st}
     # the workload's stated precisions: its own subspace build (FP64 little operator)
     dflp = dict(Ns=20, ninv=DFL_NINV, ctol=1e-2, cnmx=DFL_CNMX, cnkv=DFL_CNKV, ncy=sncy, nmr=snmr,
-                bncy=DFL_BUILD_SAP[0], bnmr=DFL_BUILD_SAP[1])
+                bncy=DFL_BUILD_SAP[0], bnmr=DFL_BUILD_SAP[1], ceo=DFL_CEO)
     r, _ = solve_once(ctx, lqcd, eta, "dfl", "f32", cprec="f64", **dflp)
     out["dfl_mixed"] = {"form": "deflated SAP-GCR (Ns=20, 4^4 blocks), FP32 SAP/subspace/stencil, FP64 GCR "
                                 "(Krylov vectors, Gram-Schmidt) and FP64 little-Dirac solve, 12 RHS batched",
@@ -284,7 +289,7 @@ def time_to_solve(ctx, lqcd, eta, net=None):
     # one subspace build with the FP32 little operator (timed, included in both
     # forms below) and two smoothers on it
     r, _ = solve_once(ctx, lqcd, eta, "dfl", "f32", cprec="f32", sap_prec=lqcd.F16S, krylov="f32", bprec=lqcd.F16S,
-                      **dflp)
+                      **dict(dflp, cnmx=DFL_CNMX_EO if DFL_CEO else DFL_CNMX))
     build = r["build_s"]
     out["chosen"] = {"form": "deflated SAP-GCR (Ns=20, 4^4 blocks), FP16 (per-site scale) SAP in the solve and the "
                              "subspace build, FP32 subspace, "
@@ -351,12 +356,16 @@ def run_solve(args):
     ctx.clover_invert(kappa, CSW)
     eta = torch.from_numpy(synth.gaussian_spinor(args.nrhs * ctx.Vh, 1).reshape(args.nrhs, ctx.Vh, 4, 3)).cuda()
     # the first pass tunes launch shapes and grows workspaces; the second is reported
-    for _ in range(2):
+    l0 = ctx.kernel_launches
+    for p in range(2):
+        if p == 1:
+            first_pass_launches = ctx.kernel_launches - l0
         res, _ = solve_once(ctx, lqcd, eta, args.solver, args.prec, Ns=args.Ns, ninv=args.ninv, ctol=args.ctol,
                             cnmx=args.cnmx, cnkv=args.cnkv, cprec=args.cprec, nkv=args.nkv,
                             krylov=args.krylov, ncy=args.ncy, nmr=args.nmr, bncy=args.bncy, bnmr=args.bnmr,
-                            bprec={"f16s": lqcd.F16S, "f32": lqcd.F32}.get(args.bprec),
+                            bprec={"f16s": lqcd.F16S, "f32": lqcd.F32}.get(args.bprec), ceo=args.ceo,
                             sap_prec={"f16s": lqcd.F16S, "f32": lqcd.F32, "f64": lqcd.F64}.get(args.sap_prec))
+    res["first_pass_launches"] = first_pass_launches
     res["nkv"] = args.nkv
     res["ncy"], res["nmr"] = args.ncy, args.nmr
     res["sap_prec"] = args.sap_prec or args.prec
@@ -490,7 +499,8 @@ def run_net(args):
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     ctx.dfl_build(v0, bs=(4, 4, 4, 4), ninv=DFL_NINV, ncy=DFL_BUILD_SAP[0], nmr=DFL_BUILD_SAP[1], prec=lqcd.F32,
-                  coarse_tol=1e-2, coarse_nmx=DFL_CNMX, coarse_nkv=DFL_CNKV, coarse_prec=lqcd.F32)
+                  coarse_tol=1e-2, coarse_nmx=DFL_CNMX_EO if DFL_CEO else DFL_CNMX, coarse_nkv=DFL_CNKV,
+                  coarse_prec=lqcd.F32, coarse_eo=DFL_CEO)
     torch.cuda.synchronize()
     build_s = time.perf_counter() - t0
     out = {"mode": "net", "train_lattice": "32x16x16x16", "train_fields": args.nfields, "pairs": args.nfields * args.npairs,
@@ -741,6 +751,8 @@ def main():
     ap.add_argument("--bnmr", type=int, default=4, help="solve mode: SAP MinRes steps in the subspace build")
     ap.add_argument("--bprec", default=None, choices=["f16s", "f32"],
                     help="solve mode: precision of the subspace build's SAP (default: the subspace's)")
+    ap.add_argument("--ceo", action="store_true",
+                    help="solve mode: even-odd (block-colour) form of the FP32 little-Dirac solve")
     ap.add_argument("--sap-prec", default=None, choices=["f16s", "f32", "f64"], help="solve mode: SAP precision")
     args = ap.parse_args()
     global DIMS

@@ -230,6 +230,10 @@ typedef struct {
     lqcd_prec build_sap_prec; /* LQCD_F16S: the inverse-iteration SAP of an FP32 subspace runs in
                                  FP16 with per-site scale (each pass converts the fields to F16S
                                  and back); any other value: the SAP runs in prec */
+    int coarse_eo;    /* nonzero: with the FP32 little operator and an even number (>= 2) of
+                         blocks in every direction, solve its even-odd (block-colour) Schur
+                         complement Dinv_e (A_ee - A_eo A_oo^-1 A_oe) and reconstruct the odd
+                         blocks; coarse_tol then applies to the Schur system */
 } lqcd_dfl_params;
 
 /* Build the deflation subspace ("locally deflated" solver, Sec. 3-4,

@@ -870,6 +870,113 @@ __global__ void k_fsub(long n, const float2 *a, const float2 *b, float2 *out)
     if (i < n) out[i] = make_float2(a[i].x - b[i].x, a[i].y - b[i].y);
 }
 
+// Even-odd little operator on block colours.  Coarse vectors of one colour
+// are compact: segment i (Ns entries) of a right-hand side belongs to block
+// rows[i]; a neighbour block n of the other colour sits at segment pos[n].
+//   out_i = xadd_i + sign * P_b sum_{j=1..8} A[b][j] in_{pos[nbr_j(b)]},  b = rows[i],
+// with P_b = Dinv[b] (use_dinv) or 1; xadd may be null.  One CTA per (row
+// block, chunk of rhs): the eight input segments are staged in shared memory
+// ([j][r][l], odd pitch), thread (k, r) forms the hop sum, which goes through
+// shared memory again when Dinv is applied.
+__global__ void __launch_bounds__(256) k_coarse_hop_eo(int Ns, long Nin, long Nout, int nrhs, int rc,
+                                                       const int *__restrict__ rows, const int *__restrict__ nbr,
+                                                       const int *__restrict__ pos, const float2 *__restrict__ A,
+                                                       const float2 *__restrict__ Dinv, int use_dinv,
+                                                       const float2 *__restrict__ in, const float2 *xadd, float sign,
+                                                       float2 *out)
+{
+    extern __shared__ __align__(16) unsigned char eo_raw[];
+    float2 *cs = reinterpret_cast<float2 *>(eo_raw);
+    const int i = blockIdx.x, b = rows[i], r0 = blockIdx.y * rc, nr = min(rc, nrhs - r0), P = Ns | 1;
+    float2 *hs = cs + 8 * rc * P;   // [r][k] hop sums, pitch P
+    in += r0 * Nin;
+    out += r0 * Nout;
+    if (xadd) xadd += r0 * Nout;
+    for (int e = threadIdx.x; e < 8 * nr * Ns; e += blockDim.x) {
+        const int l = e % Ns, jr = e / Ns, r = jr % nr, j = jr / nr;
+        cs[jr * P + l] = in[r * Nin + (long)pos[nbr[b * 9 + 1 + j]] * Ns + l];
+    }
+    __syncthreads();
+    for (int o = threadIdx.x; o < Ns * nr; o += blockDim.x) {
+        const int k = o / nr, r = o - k * nr;
+        float re = 0.f, im = 0.f;
+        const float2 *Mk = A + ((long)b * 9 * Ns + k) * Ns;
+        for (int j = 0; j < 8; j++) {
+            const float2 *row = Mk + (long)(j + 1) * Ns * Ns;
+            const float2 *x = cs + (j * nr + r) * P;
+#pragma unroll 4
+            for (int l = 0; l < Ns; l++) {
+                const float2 a = __ldg(row + l), y = x[l];
+                re = fmx(a.x, y.x, fmx(-a.y, y.y, re));
+                im = fmx(a.x, y.y, fmx(a.y, y.x, im));
+            }
+        }
+        if (use_dinv) {
+            hs[r * P + k] = make_float2(re, im);
+        } else {
+            const long oi = r * Nout + (long)i * Ns + k;
+            float2 base = xadd ? xadd[oi] : make_float2(0.f, 0.f);
+            out[oi] = make_float2(base.x + sign * re, base.y + sign * im);
+        }
+    }
+    if (!use_dinv) return;
+    __syncthreads();
+    for (int o = threadIdx.x; o < Ns * nr; o += blockDim.x) {
+        const int k = o / nr, r = o - k * nr;
+        float re = 0.f, im = 0.f;
+        const float2 *row = Dinv + ((long)b * Ns + k) * Ns;
+        const float2 *x = hs + r * P;
+#pragma unroll 4
+        for (int l = 0; l < Ns; l++) {
+            const float2 a = __ldg(row + l), y = x[l];
+            re = fmx(a.x, y.x, fmx(-a.y, y.y, re));
+            im = fmx(a.x, y.y, fmx(a.y, y.x, im));
+        }
+        const long oi = r * Nout + (long)i * Ns + k;
+        float2 base = xadd ? xadd[oi] : make_float2(0.f, 0.f);
+        out[oi] = make_float2(base.x + sign * re, base.y + sign * im);
+    }
+}
+// out_i = Dinv[rows[i]] in_i on compact colour vectors
+__global__ void __launch_bounds__(256) k_coarse_diag_eo(int Ns, long N, int nrhs, const int *__restrict__ rows,
+                                                        const float2 *__restrict__ Dinv, const float2 *__restrict__ in,
+                                                        float2 *out)
+{
+    const int i = blockIdx.x, b = rows[i], r = blockIdx.y;
+    const float2 *x = in + r * N + (long)i * Ns;
+    for (int k = threadIdx.x; k < Ns; k += blockDim.x) {
+        const float2 *row = Dinv + ((long)b * Ns + k) * Ns;
+        float re = 0.f, im = 0.f;
+        for (int l = 0; l < Ns; l++) {
+            const float2 a = __ldg(row + l), y = x[l];
+            re = fmx(a.x, y.x, fmx(-a.y, y.y, re));
+            im = fmx(a.x, y.y, fmx(a.y, y.x, im));
+        }
+        out[r * N + (long)i * Ns + k] = make_float2(re, im);
+    }
+}
+// compact colour segments <-> full coarse vectors (FP64 full, FP32 compact)
+__global__ void k_gather_col(int Ns, long Nfull, long Nc, int nrows, int nrhs, const int *rows, const double2 *full,
+                             float2 *comp)
+{
+    const long e = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    const int r = blockIdx.y;
+    if (e >= (long)nrows * Ns) return;
+    const int i = (int)(e / Ns), k = (int)(e % Ns);
+    const double2 v = full[r * Nfull + (long)rows[i] * Ns + k];
+    comp[r * Nc + e] = make_float2((float)v.x, (float)v.y);
+}
+__global__ void k_scatter_col(int Ns, long Nfull, long Nc, int nrows, int nrhs, const int *rows, const float2 *comp,
+                              double2 *full)
+{
+    const long e = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    const int r = blockIdx.y;
+    if (e >= (long)nrows * Ns) return;
+    const int i = (int)(e / Ns), k = (int)(e % Ns);
+    const float2 v = comp[r * Nc + e];
+    full[r * Nfull + (long)rows[i] * Ns + k] = make_double2(v.x, v.y);
+}
+
 }  // namespace
 
 struct DflState {
@@ -884,6 +991,12 @@ struct DflState {
     lqcd_dfl_params params;
     std::vector<int> nbr_host;
     long coarse_iters = 0, coarse_solves = 0;
+    // even-odd form of the little operator on block colours (every block count
+    // even, so the +-mu neighbours of a block have the other colour)
+    bool eo = false;
+    int ncol[2] = {0, 0};
+    int *blist = nullptr;   // device [ncol[0] colour-0 block ids, then ncol[1] colour-1 ids]
+    int *bpos = nullptr;    // device [nblk]: index of a block within its colour's list
 };
 
 void dfl_free(lqcd_ctx *c)
@@ -895,6 +1008,8 @@ void dfl_free(lqcd_ctx *c)
     cudaFree(c->dfl->Dinv);
     cudaFree(c->dfl->Aint32);
     cudaFree(c->dfl->Dinv32);
+    cudaFree(c->dfl->blist);
+    cudaFree(c->dfl->bpos);
     delete c->dfl;
     c->dfl = nullptr;
 }
@@ -1085,11 +1200,14 @@ __global__ void k_c_restart(int nrhs, CoarseScal *s, int *n_active)
 // inside a cycle gets zero updates for the rest of it.
 lqcd_status coarse_gcr32(lqcd_ctx *c, const double2 *b, double2 *x, int nrhs, double tol, int nkv, int nmx,
                          int *iters);
+lqcd_status coarse_gcr32_eo(lqcd_ctx *c, const double2 *b, double2 *x, int nrhs, double tol, int nkv, int nmx,
+                            int *iters);
 
 lqcd_status coarse_gcr(lqcd_ctx *c, const double2 *b, double2 *x, int nrhs, double tol, int nkv, int nmx,
                        int *iters)
 {
     DflState *d = c->dfl;
+    if (d->Aint32 && d->eo && d->params.coarse_eo) return coarse_gcr32_eo(c, b, x, nrhs, tol, nkv, nmx, iters);
     if (d->Aint32) return coarse_gcr32(c, b, x, nrhs, tol, nkv, nmx, iters);
     const long N = (long)d->B.nblk * d->Ns;
     const long n2 = 2 * N;
@@ -1248,6 +1366,142 @@ lqcd_status coarse_gcr32(lqcd_ctx *c, const double2 *b, double2 *x, int nrhs, do
     return active > 0 ? LQCD_ERR_NOT_CONVERGED : LQCD_OK;
 }
 
+// The little-Dirac solve in even-odd form (FP32 operator): with the block
+// colours e, o and the block-diagonal inverses Dinv,
+//   S' x_e = Dinv_e (b_e - A_eo Dinv_o b_o),  S' = 1 - Dinv_e A_eo Dinv_o A_oe,
+// solved by the same GCR (no further preconditioner) on the even blocks only,
+// then x_o = Dinv_o (b_o - A_oe x_e).  The vectors are half as long and the
+// Schur complement is better conditioned than the block-Jacobi preconditioned
+// operator; the tolerance applies to the Schur system's residual.
+lqcd_status coarse_gcr32_eo(lqcd_ctx *c, const double2 *b, double2 *x, int nrhs, double tol, int nkv, int nmx,
+                            int *iters)
+{
+    DflState *d = c->dfl;
+    const int Ns = d->Ns;
+    const long N = (long)d->B.nblk * Ns;
+    const int ne = d->ncol[0], no = d->ncol[1];
+    const long Ne = (long)ne * Ns, No = (long)no * Ns;
+    const int *rows_e = d->blist, *rows_o = d->blist + ne;
+    if (nkv < 1 || nkv > CG_K || nrhs > CG_R || nrhs * nkv > 2048)
+        return set_err(c, LQCD_ERR_ARG, "coarse nkv=%d nrhs=%d", nkv, nrhs);
+    const long bE = nrhs * Ne, bO = nrhs * No;
+    void *buf;
+    const size_t vec_bytes = ((size_t)(2 * nkv + 5) * bE + 3 * bO) * sizeof(float2);
+    LQCD_TRY(ws_get(c, WS_COARSE, vec_bytes + sizeof(CoarseScal) + 256, &buf));
+    float2 *P = (float2 *)buf, *Q = P + nkv * bE, *rho = Q + nkv * bE, *w = rho + bE, *xf = w + bE, *bf = xf + bE,
+           *be = bf + bE, *bo = be + bE, *to = bo + bO, *t2o = to + bO;
+    CoarseScal *S = (CoarseScal *)((char *)buf + ((vec_bytes + 255) / 256) * 256);
+    int *n_active_dev = (int *)c->red_out;
+    int *n_active_host = (int *)c->red_host;
+    double2 *partial = (double2 *)c->red;
+    const int nb = std::max(1, std::min<int>(std::max(8, 4 * 152 / nrhs), (int)((Ne + 255) / 256)));
+    const int ga = std::max(1, std::min<int>(4 * 152 / std::max(1, nrhs), (int)((Ne + 255) / 256)));
+    const int Pp = Ns | 1;
+    const int rc = std::max(1, std::min(nrhs, COARSE_SMEM / (int)(9 * Pp * sizeof(float2))));
+    const int hthreads = std::min(256, (Ns * rc + 31) / 32 * 32);
+    const size_t hsm = (size_t)9 * rc * Pp * sizeof(float2);
+    static bool attr = false;
+    if (!attr) {
+        LQCD_CUDA_CHECK(c, cudaFuncSetAttribute(k_coarse_hop_eo, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                COARSE_SMEM));
+        attr = true;
+    }
+    auto hop = [&](const int *rows, int nrows, long Nin, long Nout, const float2 *in, int dinv, const float2 *xadd,
+                   float sign, float2 *out) -> lqcd_status {
+        k_coarse_hop_eo<<<dim3(nrows, div_up(nrhs, rc)), hthreads, hsm, c->stream>>>(
+            Ns, Nin, Nout, nrhs, rc, rows, d->nbr, d->bpos, d->Aint32, d->Dinv32, dinv, in, xadd, sign, out);
+        c->n_kernel_launches++;
+        LQCD_LAUNCH_CHECK(c);
+        return LQCD_OK;
+    };
+    auto diag = [&](const int *rows, int nrows, long Nc, const float2 *in, float2 *out) -> lqcd_status {
+        k_coarse_diag_eo<<<dim3(nrows, nrhs), 32, 0, c->stream>>>(Ns, Nc, nrhs, rows, d->Dinv32, in, out);
+        c->n_kernel_launches++;
+        LQCD_LAUNCH_CHECK(c);
+        return LQCD_OK;
+    };
+    // q = S' v
+    auto apply = [&](const float2 *v, float2 *q) -> lqcd_status {
+        LQCD_TRY(hop(rows_o, no, Ne, No, v, 1, nullptr, 1.f, t2o));
+        return hop(rows_e, ne, No, Ne, t2o, 1, v, -1.f, q);
+    };
+    auto dots = [&](const float2 *A, long sa, const float2 *B, int k, double2 *out) -> lqcd_status {
+        for (int k0 = 0; k0 < k; k0 += FDOT_K) {
+            const int kn = std::min(FDOT_K, k - k0);
+            k_fdot_partial<<<dim3(nb, nrhs), 256, 0, c->stream>>>(Ne, A, sa, Ne, B, Ne, k0, kn, partial);
+            c->n_kernel_launches++;
+        }
+        k_fdot_final<<<dim3(k, nrhs), 128, 0, c->stream>>>(nb, k, partial, out);
+        c->n_kernel_launches++;
+        LQCD_LAUNCH_CHECK(c);
+        return LQCD_OK;
+    };
+    auto axpy = [&](int k, const double2 *cf, const float2 *X, long sa, float2 *y, float sign) -> lqcd_status {
+        k_fmulti_axpy<<<dim3(ga, nrhs), 256, 0, c->stream>>>(Ne, k, cf, X, sa, Ne, y, Ne, sign);
+        c->n_kernel_launches++;
+        LQCD_LAUNCH_CHECK(c);
+        return LQCD_OK;
+    };
+    // right-hand side of the Schur system
+    k_gather_col<<<dim3(div_up(Ne, 256), nrhs), 256, 0, c->stream>>>(Ns, N, Ne, ne, nrhs, rows_e, b, be);
+    k_gather_col<<<dim3(div_up(No, 256), nrhs), 256, 0, c->stream>>>(Ns, N, No, no, nrhs, rows_o, b, bo);
+    c->n_kernel_launches += 2;
+    LQCD_TRY(diag(rows_o, no, No, bo, to));                        // to = Dinv_o b_o
+    LQCD_TRY(hop(rows_e, ne, No, Ne, to, 0, be, -1.f, w));         // w = b_e - A_eo to
+    LQCD_TRY(diag(rows_e, ne, Ne, w, bf));                         // rhs = Dinv_e w
+    const int gn = div_up(bE, 256);
+    LQCD_CUDA_CHECK(c, cudaMemsetAsync(xf, 0, bE * sizeof(float2), c->stream));
+    LQCD_CUDA_CHECK(c, cudaMemcpyAsync(rho, bf, bE * sizeof(float2), cudaMemcpyDeviceToDevice, c->stream));
+    LQCD_TRY(dots(bf, 0, bf, 1, S->dots));
+    k_c_init<<<1, CG_R, 0, c->stream>>>(nrhs, tol * tol, S);
+    c->n_kernel_launches++;
+    int it = 0, active = nrhs;
+    while (active > 0 && it < nmx) {
+        int nk = 0;
+        for (int k = 0; k < nkv && it < nmx; k++) {
+            float2 *pk = P + k * bE, *qk = Q + k * bE;
+            LQCD_CUDA_CHECK(c, cudaMemcpyAsync(pk, rho, bE * sizeof(float2), cudaMemcpyDeviceToDevice, c->stream));
+            LQCD_TRY(apply(pk, qk));
+            if (k > 0) {
+                LQCD_TRY(dots(Q, bE, qk, k, S->dots));
+                k_c_gs<<<nrhs, k, 0, c->stream>>>(nrhs, k, S);
+                c->n_kernel_launches++;
+                LQCD_TRY(axpy(k, S->dots, Q, bE, qk, -1.f));
+            }
+            LQCD_TRY(dots(qk, rho - qk, qk, 2, S->dots));   // |q_k|^2 and <rho, q_k>
+            k_c_norm<<<1, CG_R, 0, c->stream>>>(nrhs, k, S);
+            c->n_kernel_launches++;
+            LQCD_TRY(axpy(1, S->cfR, qk, 0, rho, -1.f));
+            LQCD_TRY(axpy(1, S->cfS, qk, 0, qk, 1.f));
+            it++;
+            nk = k + 1;
+        }
+        k_c_backsub<<<1, CG_R, 0, c->stream>>>(nrhs, nk, S);
+        c->n_kernel_launches++;
+        LQCD_TRY(axpy(nk, S->alpha, P, bE, xf, 1.f));
+        LQCD_TRY(apply(xf, w));
+        k_fsub<<<gn, 256, 0, c->stream>>>(bE, bf, w, rho);
+        c->n_kernel_launches++;
+        LQCD_TRY(dots(rho, 0, rho, 1, S->dots));
+        k_c_restart<<<1, CG_R, 0, c->stream>>>(nrhs, S, n_active_dev);
+        c->n_kernel_launches++;
+        LQCD_LAUNCH_CHECK(c);
+        LQCD_CUDA_CHECK(c, cudaMemcpyAsync(n_active_host, n_active_dev, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+        LQCD_CUDA_CHECK(c, cudaStreamSynchronize(c->stream));
+        active = *n_active_host;
+    }
+    // x_o = Dinv_o (b_o - A_oe x_e) = to - Dinv_o A_oe x_e; back to the full FP64 vector
+    LQCD_TRY(hop(rows_o, no, Ne, No, xf, 1, to, -1.f, t2o));
+    k_scatter_col<<<dim3(div_up(Ne, 256), nrhs), 256, 0, c->stream>>>(Ns, N, Ne, ne, nrhs, rows_e, xf, x);
+    k_scatter_col<<<dim3(div_up(No, 256), nrhs), 256, 0, c->stream>>>(Ns, N, No, no, nrhs, rows_o, t2o, x);
+    c->n_kernel_launches += 2;
+    LQCD_LAUNCH_CHECK(c);
+    d->coarse_iters += it;
+    d->coarse_solves += 1;
+    if (iters) *iters = it;
+    return active > 0 ? LQCD_ERR_NOT_CONVERGED : LQCD_OK;
+}
+
 lqcd_status precond_sap(lqcd_ctx *c, const lqcd_sap_params *sp, const double2 *rho, double2 *phi, int nrhs)
 {
     if (sp->prec == LQCD_F64) return sap_apply(c, sp, rho, phi, nrhs);
@@ -1368,6 +1622,34 @@ lqcd_status lqcd_dfl_build(lqcd_ctx *c, const lqcd_dfl_params *p, const double *
             }
     }
     LQCD_CUDA_CHECK(c, cudaMemcpy(d->nbr, d->nbr_host.data(), 9 * B.nblk * sizeof(int), cudaMemcpyHostToDevice));
+    // block colours for the even-odd little-Dirac solve
+    d->eo = true;
+    for (int mu = 0; mu < 4; mu++)
+        if (B.nb[mu] < 2 || B.nb[mu] % 2) d->eo = false;
+    if (d->eo) {
+        std::vector<int> lst[2], pos(B.nblk);
+        for (int b = 0; b < B.nblk; b++) {
+            int u = b, sum = 0;
+            for (int i = 3; i >= 0; i--) {
+                sum += u % B.nb[i];
+                u /= B.nb[i];
+            }
+            pos[b] = (int)lst[sum & 1].size();
+            lst[sum & 1].push_back(b);
+        }
+        d->ncol[0] = (int)lst[0].size();
+        d->ncol[1] = (int)lst[1].size();
+        std::vector<int> all(lst[0]);
+        all.insert(all.end(), lst[1].begin(), lst[1].end());
+        if (cudaMalloc(&d->blist, B.nblk * sizeof(int)) != cudaSuccess ||
+            cudaMalloc(&d->bpos, B.nblk * sizeof(int)) != cudaSuccess) {
+            cudaGetLastError();
+            dfl_free(c);
+            return set_err(c, LQCD_ERR_NOMEM, "deflation colour lists");
+        }
+        LQCD_CUDA_CHECK(c, cudaMemcpy(d->blist, all.data(), B.nblk * sizeof(int), cudaMemcpyHostToDevice));
+        LQCD_CUDA_CHECK(c, cudaMemcpy(d->bpos, pos.data(), B.nblk * sizeof(int), cudaMemcpyHostToDevice));
+    }
     // start vectors: canonical FP64 -> native storage precision
     void *t64;
     LQCD_TRY(ws_get(c, WS_PACK_IN, 2 * native_half_bytes(c, LQCD_F64), &t64));

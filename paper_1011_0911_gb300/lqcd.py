@@ -43,7 +43,7 @@ class SapParams(C.Structure):
 class DflParams(C.Structure):
     _fields_ = [("bs", C.c_int * 4), ("Ns", C.c_int), ("ninv", C.c_int), ("ncy", C.c_int), ("nmr", C.c_int),
                 ("prec", C.c_int), ("coarse_tol", C.c_double), ("coarse_nkv", C.c_int), ("coarse_nmx", C.c_int),
-                ("coarse_prec", C.c_int), ("build_sap_prec", C.c_int)]
+                ("coarse_prec", C.c_int), ("build_sap_prec", C.c_int), ("coarse_eo", C.c_int)]
 
 
 class SolverParams(C.Structure):
@@ -312,7 +312,7 @@ class Context:
 
     # ------------------------------------------------------------ deflation
     def dfl_build(self, v0: torch.Tensor, bs=(4, 4, 4, 4), ninv=4, ncy=4, nmr=4, prec=F32, coarse_tol=1e-8,
-                  coarse_nkv=16, coarse_nmx=4096, coarse_prec=F64, build_sap_prec=None):
+                  coarse_nkv=16, coarse_nmx=4096, coarse_prec=F64, build_sap_prec=None, coarse_eo=False):
         v0 = v0.to(torch.complex128).contiguous()
         Ns = v0.numel() // (12 * self.V)
         self.Ns = Ns
@@ -321,7 +321,7 @@ class Context:
             nb *= L // b
         self.nblk = nb
         p = DflParams((C.c_int * 4)(*bs), Ns, ninv, ncy, nmr, prec, coarse_tol, coarse_nkv, coarse_nmx, coarse_prec,
-                      prec if build_sap_prec is None else build_sap_prec)
+                      prec if build_sap_prec is None else build_sap_prec, int(bool(coarse_eo)))
         self._check(lib().lqcd_dfl_build(self._h, C.byref(p), _ptr(v0)), "lqcd_dfl_build")
 
     def dfl_export(self):

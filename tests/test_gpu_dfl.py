@@ -152,6 +152,53 @@ def test_dfl_requires_subspace_and_clover():
         P.ctx.dfl_build(to_gpu(_v0(P, 2)), bs=(3, 4, 4, 4))
 
 
+def test_fp32_coarse_solve_even_odd():
+    """Even-odd form of the FP32 little-Dirac solve (Schur complement on the
+    block colours, odd blocks reconstructed).  With the exported little
+    operator A split by block colour, the odd rows of the residual vanish and
+    the even rows are A_ee times the Schur-system residual, which reaches
+    coarse_tol relative to the Schur right-hand side
+    A_ee^-1 (b_e - A_eo A_oo^-1 b_o); the deflated solve reaches 1e-10."""
+    P = Pair((8, 8, 8, 8), kappa=0.1355)
+    v0 = _v0(P, NS)
+    P.ctx.dfl_build(to_gpu(v0), bs=(4, 4, 4, 4), ninv=2, ncy=2, nmr=4, prec=lqcd.F32, coarse_tol=1e-5,
+                    coarse_prec=lqcd.F32, coarse_eo=True)
+    _, Ah = P.ctx.dfl_export()
+    Ad = dense_little(P, Ah.cpu().numpy())
+    nblk, Ns = P.ctx.nblk, P.ctx.Ns
+    nb = [L // 4 for L in P.dims]
+    col = np.array([sum(np.unravel_index(b, nb)) % 2 for b in range(nblk)])
+    ev = np.repeat(col == 0, Ns)
+    od = ~ev
+    cc = np.ascontiguousarray(synth.gaussian_spinor(nblk * Ns, 34).reshape(-1)[:nblk * Ns])
+    x, it = P.ctx.dfl_coarse_solve(to_gpu(cc))
+    assert it > 0
+    x = x.cpu().numpy().reshape(-1)
+    r = cc - Ad @ x
+    assert np.linalg.norm(r[od]) <= 1e-5 * np.linalg.norm(cc)
+    Aee, Aeo = Ad[np.ix_(ev, ev)], Ad[np.ix_(ev, od)]
+    Aoo = Ad[np.ix_(od, od)]
+    rhs_s = np.linalg.solve(Aee, cc[ev] - Aeo @ np.linalg.solve(Aoo, cc[od]))
+    # The solver's stopping test evaluates x_e - Dinv_e A_eo Dinv_o A_oe x_e in
+    # FP32 with FP32 copies of A and of the diagonal-block inverses: the FP64
+    # Schur residual may differ from it by the forward error of that product,
+    # at most (1 + 4 * 9 Ns u) |Dinv_e| |A_eo| |Dinv_o| |A_oe| |x_e| * 4 * 9 Ns u
+    # (four stages of dot products of up to 9 Ns terms each).
+    u = 2.0 ** -24
+    g = 4 * 9 * Ns * u
+    chain = (np.linalg.norm(np.linalg.inv(Aee), 2) * np.linalg.norm(Aeo, 2) * np.linalg.norm(np.linalg.inv(Aoo), 2)
+             * np.linalg.norm(Ad[np.ix_(od, ev)], 2))
+    bound = 1e-5 * np.linalg.norm(rhs_s) + g * (1 + g) * (1 + chain) * np.linalg.norm(x[ev])
+    res_s = np.linalg.norm(np.linalg.solve(Aee, r[ev]))
+    assert res_s <= bound, (res_s, np.linalg.norm(rhs_s), chain, np.linalg.norm(x[ev]))
+    eta = np.stack([synth.gaussian_spinor(P.Vh, 40 + k) for k in range(3)])
+    psi, info, st = P.ctx.solve_dhat(to_gpu(eta), solver=lqcd.SOLVER_DFL_SAP_GCR, tol=1e-10, sap_prec=lqcd.F32,
+                                     inner=lqcd.F32, krylov=lqcd.F32)
+    assert st == 0
+    for k in range(3):
+        assert util.relerr(P.o.Dhat(psi[k].cpu().numpy()), eta[k]) <= 1e-10
+
+
 def test_fp32_coarse_solve():
     """FP32 little-Dirac solve (operator, Krylov vectors and Gram-Schmidt in
     float): the residual under the FP64 little operator of the oracle reaches
