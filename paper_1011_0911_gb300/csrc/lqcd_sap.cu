@@ -636,36 +636,89 @@ __device__ __forceinline__ void s_clover_half(const SM &S, int ls, const CL *A, 
     stencil::herm_apply(hm, v, w);
 }
 
+// projected hop of direction mu in either sense with the sense a runtime value:
+// sgn = -1 (forward, 1 - gamma_mu) or +1 (backward, 1 + gamma_mu), u already
+// the matrix to apply (U or U^dag).  The arithmetic of proj_apply with the
+// same sense: the signs enter as exact factors of fused multiply-adds, so the
+// two threads of a site pair (one per sense) run one instruction stream.
+template <int MU>
+__device__ __forceinline__ void proj_apply_rt(float sgn, const cx<float> psi[12], const cx<float> u[3][3], float sign,
+                                              cx<float> acc[12])
+{
+    cx<float> h[2][3], w[2][3];
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        const cx<float> u0 = psi[c], u1 = psi[3 + c], l0 = psi[6 + c], l1 = psi[9 + c];
+        cx<float> el0, el1;
+        switch (MU) {
+            case 0: el0 = -l0; el1 = -l1; break;
+            case 1: el0 = timesmI(l1); el1 = timesmI(l0); break;
+            case 2: el0 = -l1; el1 = l0; break;
+            default: el0 = timesmI(l0); el1 = timesI(l1); break;
+        }
+        h[0][c] = mk(fmx(sgn, el0.re, u0.re), fmx(sgn, el0.im, u0.im));
+        h[1][c] = mk(fmx(sgn, el1.re, u1.re), fmx(sgn, el1.im, u1.im));
+    }
+    stencil::su3_vec(u, h[0], w[0]);
+    stencil::su3_vec(u, h[1], w[1]);
+    const float ss = sign * sgn;
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        cx<float> a, b;
+        switch (MU) {
+            case 0: a = -w[0][c]; b = -w[1][c]; break;
+            case 1: a = timesI(w[1][c]); b = timesI(w[0][c]); break;
+            case 2: a = w[1][c]; b = -w[0][c]; break;
+            default: a = timesI(w[0][c]); b = timesmI(w[1][c]); break;
+        }
+        acc[c].re = fmx(sign, w[0][c].re, acc[c].re);
+        acc[c].im = fmx(sign, w[0][c].im, acc[c].im);
+        acc[3 + c].re = fmx(sign, w[1][c].re, acc[3 + c].re);
+        acc[3 + c].im = fmx(sign, w[1][c].im, acc[3 + c].im);
+        acc[6 + c].re = fmx(ss, a.re, acc[6 + c].re);
+        acc[6 + c].im = fmx(ss, a.im, acc[6 + c].im);
+        acc[9 + c].re = fmx(ss, b.re, acc[9 + c].re);
+        acc[9 + c].im = fmx(ss, b.im, acc[9 + c].im);
+    }
+}
+
 // half of the in-block hop sum at site (l, x) from the smem field src of the
 // other parity: h = 0 forward hops, h = 1 backward hops; then the pair's halves
 // are added so both threads hold the full sum S (before the -1/2).  own: the
 // site's index par * SAPS_NH + t in the link arrays; the neighbours' links sit
-// at (1 - par) * SAPS_NH + their half index.
+// at (1 - par) * SAPS_NH + their half index.  Both halves run the same
+// instructions (the sense, the link slot and U versus U^dag are selected per
+// lane), and a hop that leaves the block is computed with weight 0 from an
+// in-block slot instead of being skipped, so the warp never diverges here.
 template <class SM>
 __device__ __forceinline__ void s_hopsum(const Geom &g, const BlkGeom &B, const SM &S, int h, const int l[4],
                                          const int x[4], int own, const float4 (*src)[SAPS_NH], cx<float> acc[12])
 {
 #pragma unroll
     for (int i = 0; i < 12; i++) acc[i] = mk(0.f, 0.f);
+    const float sgn = h ? 1.f : -1.f;
+    const int d = h ? -1 : 1;
+    const int oth = own < SAPS_NH ? SAPS_NH : 0;
+    const int xt = h ? 0 : g.L[0] - 1;
     cx<float> u[3][3], v[12];
 #pragma unroll
     for (int mu = 0; mu < 4; mu++) {
-        if (h == 0) {
-            int ln = blk_nbr_lex(B, l, mu, +1);
-            if (ln >= 0) {
-                float sg = (mu == 0 && x[0] == g.L[0] - 1) ? float(g.bc_t) : 1.f;
-                s_link(S, mu, own, u);
-                s_spinor(src, ln >> 1, v);
-                proj_apply<float>(mu, -1, v, u, false, sg, acc);
-            }
-        } else {
-            int ln = blk_nbr_lex(B, l, mu, -1);
-            if (ln >= 0) {
-                float sg = (mu == 0 && x[0] == 0) ? float(g.bc_t) : 1.f;
-                s_link(S, mu, (own < SAPS_NH ? SAPS_NH : 0) + (ln >> 1), u);
-                s_spinor(src, ln >> 1, v);
-                proj_apply<float>(mu, +1, v, u, true, sg, acc);
-            }
+        const int ln = blk_nbr_lex(B, l, mu, d);
+        const int n = ln >= 0 ? ln >> 1 : 0;
+        float sg = (mu == 0 && x[0] == xt) ? float(g.bc_t) : 1.f;
+        sg = ln >= 0 ? sg : 0.f;
+        s_link(S, mu, h ? oth + n : own, u);
+        cx<float> m[3][3];
+#pragma unroll
+        for (int a = 0; a < 3; a++)
+#pragma unroll
+            for (int k = 0; k < 3; k++) m[a][k] = h ? mk(u[k][a].re, -u[k][a].im) : u[a][k];
+        s_spinor(src, n, v);
+        switch (mu) {
+            case 0: proj_apply_rt<0>(sgn, v, m, sg, acc); break;
+            case 1: proj_apply_rt<1>(sgn, v, m, sg, acc); break;
+            case 2: proj_apply_rt<2>(sgn, v, m, sg, acc); break;
+            default: proj_apply_rt<3>(sgn, v, m, sg, acc); break;
         }
     }
 #pragma unroll
