@@ -86,7 +86,32 @@ __global__ void __launch_bounds__(RED_THREADS) k_bdot_partial(long n, const doub
     double re[DOT_CHUNK], im[DOT_CHUNK];
 #pragma unroll
     for (int i = 0; i < DOT_CHUNK; i++) re[i] = im[i] = 0;
-    for (long j = blockIdx.x * (long)blockDim.x + threadIdx.x; j < n; j += (long)gridDim.x * blockDim.x) {
+    const long st = (long)gridDim.x * blockDim.x;
+    long j = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (kn <= 2) {
+        // few vectors: four grid-strided elements per pass, their loads issued
+        // together (one element per pass leaves too few loads in flight to
+        // cover the memory latency)
+        for (; j + 3 * st < n; j += 4 * st) {
+            double2 b[4], a0[4], a1[4];
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                b[u] = Br[j + u * st];
+                a0[u] = Ar[k0 * sa + j + u * st];
+                if (kn == 2) a1[u] = Ar[(k0 + 1) * sa + j + u * st];
+            }
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                re[0] += a0[u].x * b[u].x + a0[u].y * b[u].y;
+                im[0] += a0[u].x * b[u].y - a0[u].y * b[u].x;
+                if (kn == 2) {
+                    re[1] += a1[u].x * b[u].x + a1[u].y * b[u].y;
+                    im[1] += a1[u].x * b[u].y - a1[u].y * b[u].x;
+                }
+            }
+        }
+    }
+    for (; j < n; j += st) {
         double2 b = Br[j];
 #pragma unroll
         for (int i = 0; i < DOT_CHUNK; i++)

@@ -527,6 +527,143 @@ __global__ void k_project(Geom g, DBlk B, const T *phi, int Ns, long fstride, co
     }
 }
 
+// FP32-subspace forms of the two kernels above with a group of PJ_R
+// right-hand sides per CTA (the groups of one block in consecutive CTAs), so
+// the block's subspace vectors are read once per group instead of once per
+// right-hand side.  Two threads per site, one per chirality half (six colour-
+// spin components): a thread holds its half of the PJ_R input fields.
+constexpr int PJ_R = 4;   // right-hand sides per CTA
+constexpr int PJ_K = 4;   // subspace vectors per reduction: PJ_K * PJ_R * 2 = 32 values
+static_assert(PJ_K * PJ_R * 2 == 32, "one value per lane in the warp reduction");
+
+// v[0..31] summed over the warp; on return v[0] of lane l holds the sum of
+// value l (a halving exchange: 31 shuffles for 32 values)
+__device__ __forceinline__ void warp_reduce_scatter32(float v[32])
+{
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const bool up = lane & o;
+#pragma unroll
+        for (int i = 0; i < o; i++) {
+            const float send = up ? v[i] : v[i + o];
+            const float keep = up ? v[i + o] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+        }
+    }
+}
+
+// c_r[b*Ns + k] = <phi_k|_b, in_r> for the PJ_R fields r0 .. r0 + PJ_R - 1;
+// blockDim.x = 2 B.vol (a multiple of 32, at most 1024)
+__global__ void __launch_bounds__(512, 1) k_project_h(Geom g, DBlk B, const float4 *__restrict__ phi, int Ns,
+                                                      long fstride, const double2 *__restrict__ in, double2 *c,
+                                                      int nrhs, long in_rs, long c_rs, int ngr)
+{
+    __shared__ float red[32][32];
+    const int b = blockIdx.x / ngr, r0 = (blockIdx.x % ngr) * PJ_R, nr = min(PJ_R, nrhs - r0);
+    const int vol = B.vol, hh = threadIdx.x >= vol ? 1 : 0, t = threadIdx.x - hh * vol;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const long Vh = g.Vh;
+    BSite s;
+    bsite(g, B, b, t, s);
+    float wf[PJ_R][12];
+#pragma unroll
+    for (int r = 0; r < PJ_R; r++) {
+        const double2 *src = in + (long)(r0 + min(r, nr - 1)) * in_rs + ((long)s.p * 12 + 6 * hh) * Vh + s.r;
+#pragma unroll
+        for (int cc = 0; cc < 6; cc++) {
+            const double2 v = src[cc * Vh];
+            wf[r][2 * cc] = r < nr ? (float)v.x : 0.f;
+            wf[r][2 * cc + 1] = r < nr ? (float)v.y : 0.f;
+        }
+    }
+    const long hs = fstride / 2;
+    for (int k0 = 0; k0 < Ns; k0 += PJ_K) {
+        float v[32];
+#pragma unroll
+        for (int kk = 0; kk < PJ_K; kk++) {
+            const int k = min(k0 + kk, Ns - 1);   // past the last vector: computed, never stored
+            const float4 *f = phi + k * fstride + s.p * hs + 3 * hh * Vh + s.r;
+            float4 q[3];
+#pragma unroll
+            for (int i = 0; i < 3; i++) q[i] = f[i * Vh];
+#pragma unroll
+            for (int r = 0; r < PJ_R; r++) {
+                float re = 0.f, im = 0.f;
+#pragma unroll
+                for (int i = 0; i < 3; i++) {
+                    const float *w4 = &wf[r][4 * i];
+                    re = fmx(q[i].x, w4[0], fmx(q[i].y, w4[1], fmx(q[i].z, w4[2], fmx(q[i].w, w4[3], re))));
+                    im = fmx(q[i].x, w4[1], fmx(-q[i].y, w4[0], fmx(q[i].z, w4[3], fmx(-q[i].w, w4[2], im))));
+                }
+                v[(kk * PJ_R + r) * 2] = re;
+                v[(kk * PJ_R + r) * 2 + 1] = im;
+            }
+        }
+        warp_reduce_scatter32(v);
+        red[warp][lane] = v[0];
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            double sum = 0;
+            for (int w = 0; w < nw; w++) sum += red[w][threadIdx.x];
+            const int kk = threadIdx.x / (2 * PJ_R), r = (threadIdx.x >> 1) % PJ_R, comp = threadIdx.x & 1;
+            if (k0 + kk < Ns && r < nr)
+                reinterpret_cast<double *>(c + (long)(r0 + r) * c_rs + (long)b * Ns + k0 + kk)[comp] = sum;
+        }
+        __syncthreads();
+    }
+}
+
+// out_r(x) = sum_k c_r[b(x)*Ns + k] phi_k(x) for PJ_R fields; a CTA covers
+// B.vol / nsplit sites of block b (two threads per site)
+__global__ void __launch_bounds__(256) k_expand_h(Geom g, DBlk B, const float4 *__restrict__ phi, int Ns, long fstride,
+                                                  const double2 *__restrict__ c, double2 *out, int nrhs, long c_rs,
+                                                  long out_rs, int ngr, int nsplit)
+{
+    __shared__ float2 cf[PJ_R][NS_MAX];
+    const int gr = blockIdx.x % ngr, bsp = blockIdx.x / ngr, b = bsp / nsplit, sp = bsp % nsplit;
+    const int r0 = gr * PJ_R, nr = min(PJ_R, nrhs - r0);
+    for (int i = threadIdx.x; i < PJ_R * Ns; i += blockDim.x) {
+        const int r = i / Ns, k = i - r * Ns;
+        const double2 v = r < nr ? c[(long)(r0 + r) * c_rs + (long)b * Ns + k] : make_double2(0.0, 0.0);
+        cf[r][k] = make_float2((float)v.x, (float)v.y);
+    }
+    __syncthreads();
+    const int per = B.vol / nsplit, hh = threadIdx.x >= per ? 1 : 0, t = sp * per + threadIdx.x - hh * per;
+    const long Vh = g.Vh, hs = fstride / 2;
+    BSite s;
+    bsite(g, B, b, t, s);
+    float acc[PJ_R][12];
+#pragma unroll
+    for (int r = 0; r < PJ_R; r++)
+#pragma unroll
+        for (int i = 0; i < 12; i++) acc[r][i] = 0.f;
+    for (int k = 0; k < Ns; k++) {
+        const float4 *f = phi + k * fstride + s.p * hs + 3 * hh * Vh + s.r;
+        float4 q[3];
+#pragma unroll
+        for (int i = 0; i < 3; i++) q[i] = f[i * Vh];
+#pragma unroll
+        for (int r = 0; r < PJ_R; r++) {
+            const float ar = cf[r][k].x, ai = cf[r][k].y;
+#pragma unroll
+            for (int i = 0; i < 3; i++) {
+                acc[r][4 * i] = fmx(ar, q[i].x, fmx(-ai, q[i].y, acc[r][4 * i]));
+                acc[r][4 * i + 1] = fmx(ar, q[i].y, fmx(ai, q[i].x, acc[r][4 * i + 1]));
+                acc[r][4 * i + 2] = fmx(ar, q[i].z, fmx(-ai, q[i].w, acc[r][4 * i + 2]));
+                acc[r][4 * i + 3] = fmx(ar, q[i].w, fmx(ai, q[i].z, acc[r][4 * i + 3]));
+            }
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < PJ_R; r++)
+        if (r < nr) {
+            double2 *dst = out + (long)(r0 + r) * out_rs + ((long)s.p * 12 + 6 * hh) * Vh + s.r;
+#pragma unroll
+            for (int cc = 0; cc < 6; cc++) dst[cc * Vh] = make_double2(acc[r][2 * cc], acc[r][2 * cc + 1]);
+        }
+}
+
 // out_r(x) = sum_k c_r[b(x)*Ns + k] phi_k(x)  (out_r: native F64 full fields,
 // stride out_rs; c_r stride c_rs; CTA order as in k_project)
 template <class T>
@@ -774,7 +911,7 @@ __global__ void k_to_double2(long n, const float2 *in, double2 *out)
 // FP32 coarse-vector BLAS (the coarse solve with the FP32 operator): per-CTA
 // partial dots accumulated in float, partials and their fixed-order sum in
 // double.  partial[(r*nb + b)*32 + i] for vector i of rhs r.
-constexpr int FDOT_K = 8;
+constexpr int FDOT_K = 16;
 __global__ void __launch_bounds__(256) k_fdot_partial(long n, const float2 *__restrict__ A, long sa, long fa,
                                                       const float2 *__restrict__ B, long fb, int k0, int kn,
                                                       double2 *partial)
@@ -798,6 +935,7 @@ __global__ void __launch_bounds__(256) k_fdot_partial(long n, const float2 *__re
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int i = 0; i < FDOT_K; i++) {
+        if (i >= kn) break;   // kn is the same for the whole CTA
         float x = re[i], m = im[i];
         for (int o = 16; o > 0; o >>= 1) {
             x += __shfl_down_sync(0xffffffffu, x, o);
@@ -937,6 +1075,114 @@ __global__ void __launch_bounds__(256) k_coarse_hop_eo(int Ns, long Nin, long No
         out[oi] = make_float2(base.x + sign * re, base.y + sign * im);
     }
 }
+// The same operation with eight warps per row block, warp j taking the hop
+// to neighbour j with lane k owning row k of the block (Ns <= 32) and all (up
+// to CW_R) right-hand sides of the pass in registers.  Every matrix entry is
+// loaded once per launch, coalesced from the column-major copies
+// AT [b][j-1][l][k] and DT [b][l][k]; the input segment of neighbour j sits in
+// shared memory as [l][r] (one broadcast read per pair of right-hand sides).
+// The eight partial sums are added in the order j = 1 .. 8, then Dinv is
+// applied by thread (k, r).  Short dependent chains per warp (Ns loads of one
+// matrix) and 8 warps per row block keep enough loads in flight.
+constexpr int CW_R = 12;   // right-hand sides per pass
+__global__ void __launch_bounds__(256) k_coarse_hop_eo_j(int Ns, long Nin, long Nout, int nrhs,
+                                                         const int *__restrict__ rows, const int *__restrict__ nbr,
+                                                         const int *__restrict__ pos, const float2 *__restrict__ AT,
+                                                         const float2 *__restrict__ DT, int use_dinv,
+                                                         const float2 *__restrict__ in, const float2 *xadd,
+                                                         float sign, float2 *out)
+{
+    extern __shared__ __align__(16) unsigned char eoj_raw[];
+    float2 *sm = reinterpret_cast<float2 *>(eoj_raw);
+    const int j = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int i = blockIdx.x, b = rows[i], r0 = blockIdx.y * CW_R, nr = min(CW_R, nrhs - r0);
+    const int tile = Ns * CW_R;
+    float2 *xj = sm + j * tile;     // input segment of neighbour j, then its partial sum
+    float2 *hs = sm + 8 * tile;     // hop sum [k][r] for the Dinv stage
+    in += r0 * Nin;
+    out += r0 * Nout;
+    if (xadd) xadd += r0 * Nout;
+    const long seg = (long)pos[nbr[b * 9 + 1 + j]] * Ns;
+    if (lane < Ns)
+#pragma unroll
+        for (int r = 0; r < CW_R; r++)
+            xj[lane * CW_R + r] = r < nr ? in[r * Nin + seg + lane] : make_float2(0.f, 0.f);
+    __syncwarp();
+    float re[CW_R], im[CW_R];
+#pragma unroll
+    for (int r = 0; r < CW_R; r++) re[r] = im[r] = 0.f;
+    if (lane < Ns) {
+        const float2 *Aj = AT + ((long)b * 8 + j) * Ns * Ns + lane;
+#pragma unroll 4
+        for (int l = 0; l < Ns; l++) {
+            const float2 a = __ldg(Aj + l * Ns);
+            const float4 *y4 = reinterpret_cast<const float4 *>(xj + l * CW_R);
+#pragma unroll
+            for (int q = 0; q < CW_R / 2; q++) {
+                const float4 y = y4[q];
+                re[2 * q] = fmx(a.x, y.x, fmx(-a.y, y.y, re[2 * q]));
+                im[2 * q] = fmx(a.x, y.y, fmx(a.y, y.x, im[2 * q]));
+                re[2 * q + 1] = fmx(a.x, y.z, fmx(-a.y, y.w, re[2 * q + 1]));
+                im[2 * q + 1] = fmx(a.x, y.w, fmx(a.y, y.z, im[2 * q + 1]));
+            }
+        }
+    }
+    __syncwarp();
+    if (lane < Ns)
+#pragma unroll
+        for (int r = 0; r < CW_R; r++) xj[lane * CW_R + r] = make_float2(re[r], im[r]);
+    __syncthreads();
+    for (int o = threadIdx.x; o < tile; o += blockDim.x) {
+        float2 t = sm[o];
+#pragma unroll
+        for (int jj = 1; jj < 8; jj++) {
+            const float2 u = sm[jj * tile + o];
+            t.x += u.x;
+            t.y += u.y;
+        }
+        const int k = o / CW_R, r = o - k * CW_R;
+        if (use_dinv) {
+            hs[o] = t;
+        } else if (r < nr) {
+            const long oi = r * Nout + (long)i * Ns + k;
+            const float2 base = xadd ? xadd[oi] : make_float2(0.f, 0.f);
+            out[oi] = make_float2(base.x + sign * t.x, base.y + sign * t.y);
+        }
+    }
+    if (!use_dinv) return;
+    __syncthreads();
+    for (int o = threadIdx.x; o < tile; o += blockDim.x) {
+        const int k = o / CW_R, r = o - k * CW_R;
+        if (r >= nr) continue;
+        const float2 *D = DT + (long)b * Ns * Ns + k;
+        float dre = 0.f, dim = 0.f;
+#pragma unroll 4
+        for (int l = 0; l < Ns; l++) {
+            const float2 a = __ldg(D + l * Ns), y = hs[l * CW_R + r];
+            dre = fmx(a.x, y.x, fmx(-a.y, y.y, dre));
+            dim = fmx(a.x, y.y, fmx(a.y, y.x, dim));
+        }
+        const long oi = r * Nout + (long)i * Ns + k;
+        const float2 base = xadd ? xadd[oi] : make_float2(0.f, 0.f);
+        out[oi] = make_float2(base.x + sign * dre, base.y + sign * dim);
+    }
+}
+// column-major FP32 copies of the eight hopping matrices and of the diagonal
+// block inverses: AT[b][j-1][l][k] = A[b][j][k][l], DT[b][l][k] = Dinv[b][k][l]
+__global__ void k_coarse_transpose(int nblk, int Ns, const double2 *A, const double2 *Dinv, float2 *AT, float2 *DT)
+{
+    const long n2 = (long)Ns * Ns, e = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (e >= (long)nblk * 9 * n2) return;
+    const long b = e / (9 * n2);
+    const int j = (int)(e / n2 % 9), l = (int)(e % n2 / Ns), k = (int)(e % Ns);
+    if (j == 0) {
+        const double2 v = Dinv[(b * Ns + k) * Ns + l];
+        DT[b * n2 + (long)l * Ns + k] = make_float2((float)v.x, (float)v.y);
+    } else {
+        const double2 v = A[((b * 9 + j) * Ns + k) * Ns + l];
+        AT[(b * 8 + j - 1) * n2 + (long)l * Ns + k] = make_float2((float)v.x, (float)v.y);
+    }
+}
 // out_i = Dinv[rows[i]] in_i on compact colour vectors
 __global__ void __launch_bounds__(256) k_coarse_diag_eo(int Ns, long N, int nrhs, const int *__restrict__ rows,
                                                         const float2 *__restrict__ Dinv, const float2 *__restrict__ in,
@@ -988,6 +1234,7 @@ struct DflState {
     double2 *Aint = nullptr;
     double2 *Dinv = nullptr;   // [nblk][Ns][Ns] inverses of the diagonal blocks
     float2 *Aint32 = nullptr, *Dinv32 = nullptr;   // FP32 copies (coarse_prec == LQCD_F32)
+    float2 *AT32 = nullptr, *DT32 = nullptr;       // column-major FP32 copies (even-odd coarse solve, Ns <= 32)
     lqcd_dfl_params params;
     std::vector<int> nbr_host;
     long coarse_iters = 0, coarse_solves = 0;
@@ -1007,6 +1254,8 @@ void dfl_free(lqcd_ctx *c)
     cudaFree(c->dfl->Aint);
     cudaFree(c->dfl->Dinv);
     cudaFree(c->dfl->Aint32);
+    cudaFree(c->dfl->AT32);
+    cudaFree(c->dfl->DT32);
     cudaFree(c->dfl->Dinv32);
     cudaFree(c->dfl->blist);
     cudaFree(c->dfl->bpos);
@@ -1047,6 +1296,16 @@ template <class T>
 lqcd_status launch_project(lqcd_ctx *c, const double2 *in, double2 *cv, int nrhs)
 {
     DflState *d = c->dfl;
+    if (std::is_same<T, float4>::value && (2 * d->B.vol) % 32 == 0 && 2 * d->B.vol <= 1024) {
+        const long N = (long)d->B.nblk * d->Ns, nf = 24 * (long)c->g.Vh;
+        const int ngr = div_up(nrhs, PJ_R);
+        k_project_h<<<d->B.nblk * ngr, 2 * d->B.vol, 0, c->stream>>>(c->g, d->B, (const float4 *)d->phi, d->Ns,
+                                                                     field_elems(c, d->prec), in, cv, nrhs, nf, N,
+                                                                     ngr);
+        c->n_kernel_launches++;
+        LQCD_LAUNCH_CHECK(c);
+        return LQCD_OK;
+    }
     size_t sm = (2 * RCHUNK * 32 + 2 * RCHUNK) * sizeof(double);
     const long N = (long)d->B.nblk * d->Ns, nf = 24 * (long)c->g.Vh;
     k_project<T><<<d->B.nblk * nrhs, d->B.vol, sm, c->stream>>>(c->g, d->B, (const T *)d->phi, d->Ns,
@@ -1059,6 +1318,16 @@ template <class T>
 lqcd_status launch_expand(lqcd_ctx *c, const double2 *cv, double2 *out, int nrhs)
 {
     DflState *d = c->dfl;
+    const int nsplit = d->B.vol % 64 == 0 ? std::max(1, d->B.vol / 128) : 0;
+    if (std::is_same<T, float4>::value && nsplit > 0 && 2 * (d->B.vol / nsplit) <= 256) {
+        const long N = (long)d->B.nblk * d->Ns, nf = 24 * (long)c->g.Vh;
+        const int ngr = div_up(nrhs, PJ_R);
+        k_expand_h<<<d->B.nblk * nsplit * ngr, 2 * (d->B.vol / nsplit), 0, c->stream>>>(
+            c->g, d->B, (const float4 *)d->phi, d->Ns, field_elems(c, d->prec), cv, out, nrhs, N, nf, ngr, nsplit);
+        c->n_kernel_launches++;
+        LQCD_LAUNCH_CHECK(c);
+        return LQCD_OK;
+    }
     const long N = (long)d->B.nblk * d->Ns, nf = 24 * (long)c->g.Vh;
     k_expand<T><<<d->B.nblk * nrhs, d->B.vol, 0, c->stream>>>(c->g, d->B, (const T *)d->phi, d->Ns,
                                                               field_elems(c, d->prec), cv, out, nrhs, N, nf);
@@ -1406,10 +1675,15 @@ lqcd_status coarse_gcr32_eo(lqcd_ctx *c, const double2 *b, double2 *x, int nrhs,
                                                 COARSE_SMEM));
         attr = true;
     }
+    const size_t wsm = (size_t)9 * Ns * CW_R * sizeof(float2);
     auto hop = [&](const int *rows, int nrows, long Nin, long Nout, const float2 *in, int dinv, const float2 *xadd,
                    float sign, float2 *out) -> lqcd_status {
-        k_coarse_hop_eo<<<dim3(nrows, div_up(nrhs, rc)), hthreads, hsm, c->stream>>>(
-            Ns, Nin, Nout, nrhs, rc, rows, d->nbr, d->bpos, d->Aint32, d->Dinv32, dinv, in, xadd, sign, out);
+        if (d->AT32)
+            k_coarse_hop_eo_j<<<dim3(nrows, div_up(nrhs, CW_R)), 256, wsm, c->stream>>>(
+                Ns, Nin, Nout, nrhs, rows, d->nbr, d->bpos, d->AT32, d->DT32, dinv, in, xadd, sign, out);
+        else
+            k_coarse_hop_eo<<<dim3(nrows, div_up(nrhs, rc)), hthreads, hsm, c->stream>>>(
+                Ns, Nin, Nout, nrhs, rc, rows, d->nbr, d->bpos, d->Aint32, d->Dinv32, dinv, in, xadd, sign, out);
         c->n_kernel_launches++;
         LQCD_LAUNCH_CHECK(c);
         return LQCD_OK;
@@ -1751,6 +2025,18 @@ lqcd_status lqcd_dfl_build(lqcd_ctx *c, const lqcd_dfl_params *p, const double *
         k_to_float2<<<div_up(nd, 256), 256, 0, c->stream>>>(nd, d->Dinv, d->Dinv32);
         c->n_kernel_launches += 2;
         LQCD_LAUNCH_CHECK(c);
+        if (d->eo && p->coarse_eo && p->Ns <= 32) {
+            if (cudaMalloc(&d->AT32, (na - nd) * sizeof(float2)) != cudaSuccess ||
+                cudaMalloc(&d->DT32, nd * sizeof(float2)) != cudaSuccess) {
+                cudaGetLastError();
+                dfl_free(c);
+                return set_err(c, LQCD_ERR_NOMEM, "FP32 little operator allocation");
+            }
+            k_coarse_transpose<<<div_up(na, 256), 256, 0, c->stream>>>(B.nblk, p->Ns, d->Aint, d->Dinv, d->AT32,
+                                                                       d->DT32);
+            c->n_kernel_launches++;
+            LQCD_LAUNCH_CHECK(c);
+        }
     } else if (p->coarse_prec != LQCD_F64) {
         dfl_free(c);
         return set_err(c, LQCD_ERR_ARG, "coarse precision %d", (int)p->coarse_prec);

@@ -51,6 +51,8 @@ def test_subspace_parity_fp32_build(ninv):
     assert relerr(phi, P.o.dfl_subspace()) < 1e-6
     rho = synth.gaussian_spinor(P.V, 31)
     assert relerr(P.ctx.dfl_project(to_gpu(rho)), P.o.dfl_project(rho)) < 1e-6
+    cc = np.ascontiguousarray(synth.gaussian_spinor(P.ctx.nblk * P.ctx.Ns, 32).reshape(-1)[:P.ctx.nblk * P.ctx.Ns])
+    assert relerr(P.ctx.dfl_expand(to_gpu(cc)), P.o.dfl_expand(cc)) < 1e-6
     # the little operator of the FP32 subspace, built in FP32 arithmetic
     assert util.relerr(dense_little(P, A.cpu().numpy()), P.o.dfl_little()) < 1e-5
 
@@ -191,11 +193,12 @@ def test_fp32_coarse_solve_even_odd():
     bound = 1e-5 * np.linalg.norm(rhs_s) + g * (1 + g) * (1 + chain) * np.linalg.norm(x[ev])
     res_s = np.linalg.norm(np.linalg.solve(Aee, r[ev]))
     assert res_s <= bound, (res_s, np.linalg.norm(rhs_s), chain, np.linalg.norm(x[ev]))
-    eta = np.stack([synth.gaussian_spinor(P.Vh, 40 + k) for k in range(3)])
+    # five sources: two groups of the batched projection / expansion (4 + 1)
+    eta = np.stack([synth.gaussian_spinor(P.Vh, 40 + k) for k in range(5)])
     psi, info, st = P.ctx.solve_dhat(to_gpu(eta), solver=lqcd.SOLVER_DFL_SAP_GCR, tol=1e-10, sap_prec=lqcd.F32,
                                      inner=lqcd.F32, krylov=lqcd.F32)
     assert st == 0
-    for k in range(3):
+    for k in range(5):
         assert util.relerr(P.o.Dhat(psi[k].cpu().numpy()), eta[k]) <= 1e-10
 
 
