@@ -255,6 +255,85 @@ __global__ void k_block_gs(Geom g, DBlk B, T *v, int Ns, long fstride, int *bad)
     }
 }
 
+// Block Gram-Schmidt of an FP32 subspace: classical Gram-Schmidt applied
+// twice per vector (twice is enough for vectors this far from dependent), the
+// products and warp sums in float and the sums over warps in double.  Three
+// block reductions per vector instead of one per pair, and no FP64
+// arithmetic per site (GB300's FP64 pipe bounds the FP64 form).  Like the
+// modified form it gives the block-wise QR with a positive diagonal, so the
+// two agree up to rounding.
+__global__ void k_block_gs32(Geom g, DBlk B, float4 *v, int Ns, long fstride, int *bad)
+{
+    extern __shared__ double sh[];                // [2 RCHUNK][32] warp sums
+    double *coef = sh + 2 * RCHUNK * 32;          // [2 NS_MAX] inner products of one pass
+    double *res = coef + 2 * NS_MAX;
+    const int b = blockIdx.x, t = threadIdx.x;
+    BSite s;
+    bsite(g, B, b, t, s);
+    const long hs = fstride / 2, Vh = g.Vh;
+    for (int l = 0; l < Ns; l++) {
+        float4 *vl = v + l * fstride + s.p * hs + s.r;
+        float w[24];
+#pragma unroll
+        for (int q = 0; q < 6; q++) {
+            const float4 a = vl[q * Vh];
+            w[4 * q] = a.x;
+            w[4 * q + 1] = a.y;
+            w[4 * q + 2] = a.z;
+            w[4 * q + 3] = a.w;
+        }
+        for (int pass = 0; pass < 2 && l > 0; pass++) {
+            // the l inner products, RCHUNK per block reduction, into coef
+            for (int k0 = 0; k0 < l; k0 += RCHUNK) {
+                const int kn = min(RCHUNK, l - k0);
+                float d[2 * RCHUNK];
+#pragma unroll
+                for (int i = 0; i < RCHUNK; i++) {
+                    d[2 * i] = d[2 * i + 1] = 0.f;
+                    if (i < kn) {
+                        const float4 *vk = v + (k0 + i) * fstride + s.p * hs + s.r;
+                        float re = 0.f, im = 0.f;
+#pragma unroll
+                        for (int q = 0; q < 6; q++) {
+                            const float4 a = vk[q * Vh];
+                            re = fmx(a.x, w[4 * q], fmx(a.y, w[4 * q + 1], fmx(a.z, w[4 * q + 2], fmx(a.w, w[4 * q + 3], re))));
+                            im = fmx(a.x, w[4 * q + 1], fmx(-a.y, w[4 * q], fmx(a.z, w[4 * q + 3], fmx(-a.w, w[4 * q + 2], im))));
+                        }
+                        d[2 * i] = re;
+                        d[2 * i + 1] = im;
+                    }
+                }
+                block_sum_f<2 * RCHUNK>(d, 2 * kn, sh, coef + 2 * k0);
+            }
+            for (int k = 0; k < l; k++) {
+                const float ar = (float)coef[2 * k], ai = (float)coef[2 * k + 1];
+                const float4 *vk = v + k * fstride + s.p * hs + s.r;
+#pragma unroll
+                for (int q = 0; q < 6; q++) {
+                    const float4 a = vk[q * Vh];
+                    w[4 * q] = fmx(-ar, a.x, fmx(ai, a.y, w[4 * q]));
+                    w[4 * q + 1] = fmx(-ar, a.y, fmx(-ai, a.x, w[4 * q + 1]));
+                    w[4 * q + 2] = fmx(-ar, a.z, fmx(ai, a.w, w[4 * q + 2]));
+                    w[4 * q + 3] = fmx(-ar, a.w, fmx(-ai, a.z, w[4 * q + 3]));
+                }
+            }
+        }
+        float n2[1] = {0.f};
+#pragma unroll
+        for (int i = 0; i < 24; i++) n2[0] = fmx(w[i], w[i], n2[0]);
+        block_sum_f<1>(n2, 1, sh, res);
+        double nn = res[0];
+        if (!(nn > 0)) {
+            if (t == 0) atomicAdd(bad, 1);
+            nn = 1;
+        }
+        const float inv = (float)(1.0 / sqrt(nn));
+#pragma unroll
+        for (int q = 0; q < 6; q++)
+            vl[q * Vh] = make_float4(inv * w[4 * q], inv * w[4 * q + 1], inv * w[4 * q + 2], inv * w[4 * q + 3]);
+    }
+}
+
 // little Dirac build for vector l = blockIdx.y: Aint[b][j][k][l] = <phi_k|_b, W_j>
 template <class T>
 __global__ void k_little_build(Geom g, DBlk B, const T *phi, int Ns, long fstride, const double2 *U,
@@ -1398,12 +1477,8 @@ __global__ void k_c_gs(int nrhs, int k, CoarseScal *s)
 }
 // from |q_k|^2 and <rho, q_k>: b_k, c_k, the coefficients of rho -= c_k q_k / b_k
 // and q_k *= 1/b_k, the updated |rho|^2 and the convergence flag
-__global__ void k_c_norm(int nrhs, int k, CoarseScal *s)
+__device__ __forceinline__ void c_norm_body(int r, int k, double q2, double2 rq, CoarseScal *s)
 {
-    int r = threadIdx.x;
-    if (r >= nrhs) return;
-    double q2 = s->dots[2 * r].x;
-    double2 rq = s->dots[2 * r + 1];
     double bk = sqrt(q2);
     bool ok = bk > 0 && isfinite(bk);
     if (s->active[r] && !ok) {
@@ -1423,6 +1498,26 @@ __global__ void k_c_norm(int nrhs, int k, CoarseScal *s)
         if (s->rr[r] <= s->tol2 * s->bn2[r]) s->active[r] = 0;
     }
 }
+__global__ void k_c_norm(int nrhs, int k, CoarseScal *s)
+{
+    int r = threadIdx.x;
+    if (r >= nrhs) return;
+    c_norm_body(r, k, s->dots[2 * r].x, s->dots[2 * r + 1], s);
+}
+// the same from the per-CTA partial sums of k_fgs_norm (summed in CTA order)
+__global__ void k_c_norm_p(int nrhs, int k, int nbp, const double2 *partial, CoarseScal *s)
+{
+    int r = threadIdx.x;
+    if (r >= nrhs) return;
+    double q2 = 0, rx = 0, ry = 0;
+    for (int b = 0; b < nbp; b++) {
+        const double2 *p = partial + ((long)r * nbp + b) * 32;
+        q2 += p[0].x;
+        rx += p[1].x;
+        ry += p[1].y;
+    }
+    c_norm_body(r, k, q2, make_double2(rx, ry), s);
+}
 // alpha_j = (c_j - sum_{i>j} a_ji alpha_i) / b_j
 __global__ void k_c_backsub(int nrhs, int nk, CoarseScal *s)
 {
@@ -1438,6 +1533,95 @@ __global__ void k_c_backsub(int nrhs, int nk, CoarseScal *s)
         }
         double bj = s->bk[r][j];
         al[j] = bj > 0 ? make_double2(sr / bj, si / bj) : make_double2(0, 0);
+    }
+}
+// One Gram-Schmidt step of the FP32 coarse GCR in one pass over q_k:
+//   q_k -= sum_{i<k} <q_i, q_k> q_i,
+// the coefficients summed by every CTA from the per-CTA partials of
+// k_fdot_partial (the same fixed order in every CTA; CTA 0 of each right-hand
+// side stores them as a[r][i][k]), then per-CTA partial sums of |q_k|^2 and
+// <rho, q_k> of the updated q_k into partial2 [(r*gridDim.x + b)*32 + 0, 1].
+__global__ void __launch_bounds__(256) k_fgs_norm(long n, int k, int nbp, const double2 *__restrict__ partial,
+                                                  CoarseScal *S, const float2 *__restrict__ Q, long sa, float2 *qk,
+                                                  const float2 *__restrict__ rho, double2 *partial2)
+{
+    const int r = blockIdx.y;
+    __shared__ float2 cs[CG_K];
+    __shared__ double sh[8][3];
+    if (k > 0) {
+        for (int i = threadIdx.x; i < k; i += blockDim.x) {
+            double x = 0, m = 0;
+            for (int b = 0; b < nbp; b++) {
+                const double2 v = partial[((long)r * nbp + b) * 32 + i];
+                x += v.x;
+                m += v.y;
+            }
+            if (blockIdx.x == 0) S->a[r][i][k] = make_double2(x, m);
+            cs[i] = make_float2((float)x, (float)m);
+        }
+        __syncthreads();
+    }
+    const float2 *Qr = Q + r * n, *pr = rho + r * n;
+    float2 *qr = qk + r * n;
+    float nq = 0.f, rx = 0.f, ry = 0.f;
+    for (long j = blockIdx.x * (long)blockDim.x + threadIdx.x; j < n; j += (long)gridDim.x * blockDim.x) {
+        float2 q = qr[j];
+        if (k > 0) {
+            float sr = 0.f, si = 0.f;
+            for (int i = 0; i < k; i++) {
+                const float2 a = Qr[i * sa + j];
+                const float cx = cs[i].x, cy = cs[i].y;
+                sr += cx * a.x - cy * a.y;
+                si += cx * a.y + cy * a.x;
+            }
+            q.x -= sr;
+            q.y -= si;
+            qr[j] = q;
+        }
+        const float2 p = pr[j];
+        nq += q.x * q.x + q.y * q.y;
+        rx += p.x * q.x + p.y * q.y;   // <rho, q> = sum conj(rho) q
+        ry += p.x * q.y - p.y * q.x;
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int o = 16; o > 0; o >>= 1) {
+        nq += __shfl_down_sync(0xffffffffu, nq, o);
+        rx += __shfl_down_sync(0xffffffffu, rx, o);
+        ry += __shfl_down_sync(0xffffffffu, ry, o);
+    }
+    if (lane == 0) {
+        sh[warp][0] = nq;
+        sh[warp][1] = rx;
+        sh[warp][2] = ry;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0, bx = 0, by = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++) {
+            a += sh[w][0];
+            bx += sh[w][1];
+            by += sh[w][2];
+        }
+        double2 *o = partial2 + ((long)r * gridDim.x + blockIdx.x) * 32;
+        o[0] = make_double2(a, 0.0);
+        o[1] = make_double2(bx, by);
+    }
+}
+// rho -= cfR q_k, q_k *= 1/b_k (q_k += cfS q_k), and the next Krylov start
+// vector p_{k+1} = rho (pnext may be null)
+__global__ void k_fc_update(long n, const CoarseScal *S, float2 *qk, float2 *rho, float2 *pnext)
+{
+    const int r = blockIdx.y;
+    const float cr = (float)S->cfR[r].x, ci = (float)S->cfR[r].y, cs = (float)S->cfS[r].x;
+    float2 *qr = qk + r * n, *pr = rho + r * n, *nr = pnext ? pnext + r * n : nullptr;
+    for (long j = blockIdx.x * (long)blockDim.x + threadIdx.x; j < n; j += (long)gridDim.x * blockDim.x) {
+        const float2 q = qr[j];
+        float2 p = pr[j];
+        p.x = p.x + -1.f * (cr * q.x - ci * q.y);
+        p.y = p.y + -1.f * (cr * q.y + ci * q.x);
+        pr[j] = p;
+        if (nr) nr[j] = p;
+        qr[j] = make_float2(q.x + cs * q.x, q.y + cs * q.y);
     }
 }
 // true residual norm after a restart
@@ -1663,6 +1847,7 @@ lqcd_status coarse_gcr32_eo(lqcd_ctx *c, const double2 *b, double2 *x, int nrhs,
     int *n_active_dev = (int *)c->red_out;
     int *n_active_host = (int *)c->red_host;
     double2 *partial = (double2 *)c->red;
+    double2 *partial2 = partial + 4096 * 32;   // second half of the reduction buffer (4096 * 64 double2)
     const int nb = std::max(1, std::min<int>(std::max(8, 4 * 152 / nrhs), (int)((Ne + 255) / 256)));
     const int ga = std::max(1, std::min<int>(4 * 152 / std::max(1, nrhs), (int)((Ne + 255) / 256)));
     const int Pp = Ns | 1;
@@ -1732,21 +1917,24 @@ lqcd_status coarse_gcr32_eo(lqcd_ctx *c, const double2 *b, double2 *x, int nrhs,
     int it = 0, active = nrhs;
     while (active > 0 && it < nmx) {
         int nk = 0;
+        // a GCR step: the operator (two launches), the dots against the earlier
+        // q_i, one fused Gram-Schmidt + norm pass, the scalars, one fused update
+        // of rho, q_k and the next start vector
+        LQCD_CUDA_CHECK(c, cudaMemcpyAsync(P, rho, bE * sizeof(float2), cudaMemcpyDeviceToDevice, c->stream));
         for (int k = 0; k < nkv && it < nmx; k++) {
             float2 *pk = P + k * bE, *qk = Q + k * bE;
-            LQCD_CUDA_CHECK(c, cudaMemcpyAsync(pk, rho, bE * sizeof(float2), cudaMemcpyDeviceToDevice, c->stream));
             LQCD_TRY(apply(pk, qk));
-            if (k > 0) {
-                LQCD_TRY(dots(Q, bE, qk, k, S->dots));
-                k_c_gs<<<nrhs, k, 0, c->stream>>>(nrhs, k, S);
-                c->n_kernel_launches++;
-                LQCD_TRY(axpy(k, S->dots, Q, bE, qk, -1.f));
-            }
-            LQCD_TRY(dots(qk, rho - qk, qk, 2, S->dots));   // |q_k|^2 and <rho, q_k>
-            k_c_norm<<<1, CG_R, 0, c->stream>>>(nrhs, k, S);
-            c->n_kernel_launches++;
-            LQCD_TRY(axpy(1, S->cfR, qk, 0, rho, -1.f));
-            LQCD_TRY(axpy(1, S->cfS, qk, 0, qk, 1.f));
+            if (k > 0)
+                for (int k0 = 0; k0 < k; k0 += FDOT_K) {
+                    const int kn = std::min(FDOT_K, k - k0);
+                    k_fdot_partial<<<dim3(nb, nrhs), 256, 0, c->stream>>>(Ne, Q, bE, Ne, qk, Ne, k0, kn, partial);
+                    c->n_kernel_launches++;
+                }
+            k_fgs_norm<<<dim3(nb, nrhs), 256, 0, c->stream>>>(Ne, k, nb, partial, S, Q, bE, qk, rho, partial2);
+            k_c_norm_p<<<1, CG_R, 0, c->stream>>>(nrhs, k, nb, partial2, S);
+            k_fc_update<<<dim3(ga, nrhs), 256, 0, c->stream>>>(Ne, S, qk, rho, k + 1 < nkv ? pk + bE : nullptr);
+            c->n_kernel_launches += 3;
+            LQCD_LAUNCH_CHECK(c);
             it++;
             nk = k + 1;
         }
@@ -1973,7 +2161,8 @@ lqcd_status lqcd_dfl_build(lqcd_ctx *c, const lqcd_dfl_params *p, const double *
     if (p->prec == LQCD_F64)
         k_block_gs<double2><<<B.nblk, B.vol, sm, c->stream>>>(c->g, B, (double2 *)d->phi, p->Ns, fe, bad);
     else
-        k_block_gs<float4><<<B.nblk, B.vol, sm, c->stream>>>(c->g, B, (float4 *)d->phi, p->Ns, fe, bad);
+        k_block_gs32<<<B.nblk, B.vol, (2 * RCHUNK * 32 + 2 * NS_MAX + 2) * sizeof(double), c->stream>>>(
+            c->g, B, (float4 *)d->phi, p->Ns, fe, bad);
     c->n_kernel_launches++;
     LQCD_LAUNCH_CHECK(c);
     int hbad = 0;
