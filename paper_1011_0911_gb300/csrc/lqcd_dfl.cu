@@ -41,26 +41,10 @@ __device__ __forceinline__ void ld(const double2 *f, long Vh, long r, C v[12])
         v[c] = mk(t.x, t.y);
     }
 }
-__device__ __forceinline__ void ld(const float4 *f, long Vh, long r, C v[12])
-{
-#pragma unroll
-    for (int q = 0; q < 6; q++) {
-        float4 t = f[q * Vh + r];
-        v[2 * q] = mk((double)t.x, (double)t.y);
-        v[2 * q + 1] = mk((double)t.z, (double)t.w);
-    }
-}
 __device__ __forceinline__ void st(double2 *f, long Vh, long r, const C v[12])
 {
 #pragma unroll
     for (int c = 0; c < 12; c++) f[c * Vh + r] = make_double2(v[c].re, v[c].im);
-}
-__device__ __forceinline__ void st(float4 *f, long Vh, long r, const C v[12])
-{
-#pragma unroll
-    for (int q = 0; q < 6; q++)
-        f[q * Vh + r] = make_float4((float)v[2 * q].re, (float)v[2 * q].im, (float)v[2 * q + 1].re,
-                                    (float)v[2 * q + 1].im);
 }
 // block-local site t -> global coordinates, parity, rank
 struct BSite {
@@ -1091,70 +1075,8 @@ __global__ void k_fsub(long n, const float2 *a, const float2 *b, float2 *out)
 // are compact: segment i (Ns entries) of a right-hand side belongs to block
 // rows[i]; a neighbour block n of the other colour sits at segment pos[n].
 //   out_i = xadd_i + sign * P_b sum_{j=1..8} A[b][j] in_{pos[nbr_j(b)]},  b = rows[i],
-// with P_b = Dinv[b] (use_dinv) or 1; xadd may be null.  One CTA per (row
-// block, chunk of rhs): the eight input segments are staged in shared memory
-// ([j][r][l], odd pitch), thread (k, r) forms the hop sum, which goes through
-// shared memory again when Dinv is applied.
-__global__ void __launch_bounds__(256) k_coarse_hop_eo(int Ns, long Nin, long Nout, int nrhs, int rc,
-                                                       const int *__restrict__ rows, const int *__restrict__ nbr,
-                                                       const int *__restrict__ pos, const float2 *__restrict__ A,
-                                                       const float2 *__restrict__ Dinv, int use_dinv,
-                                                       const float2 *__restrict__ in, const float2 *xadd, float sign,
-                                                       float2 *out)
-{
-    extern __shared__ __align__(16) unsigned char eo_raw[];
-    float2 *cs = reinterpret_cast<float2 *>(eo_raw);
-    const int i = blockIdx.x, b = rows[i], r0 = blockIdx.y * rc, nr = min(rc, nrhs - r0), P = Ns | 1;
-    float2 *hs = cs + 8 * rc * P;   // [r][k] hop sums, pitch P
-    in += r0 * Nin;
-    out += r0 * Nout;
-    if (xadd) xadd += r0 * Nout;
-    for (int e = threadIdx.x; e < 8 * nr * Ns; e += blockDim.x) {
-        const int l = e % Ns, jr = e / Ns, r = jr % nr, j = jr / nr;
-        cs[jr * P + l] = in[r * Nin + (long)pos[nbr[b * 9 + 1 + j]] * Ns + l];
-    }
-    __syncthreads();
-    for (int o = threadIdx.x; o < Ns * nr; o += blockDim.x) {
-        const int k = o / nr, r = o - k * nr;
-        float re = 0.f, im = 0.f;
-        const float2 *Mk = A + ((long)b * 9 * Ns + k) * Ns;
-        for (int j = 0; j < 8; j++) {
-            const float2 *row = Mk + (long)(j + 1) * Ns * Ns;
-            const float2 *x = cs + (j * nr + r) * P;
-#pragma unroll 4
-            for (int l = 0; l < Ns; l++) {
-                const float2 a = __ldg(row + l), y = x[l];
-                re = fmx(a.x, y.x, fmx(-a.y, y.y, re));
-                im = fmx(a.x, y.y, fmx(a.y, y.x, im));
-            }
-        }
-        if (use_dinv) {
-            hs[r * P + k] = make_float2(re, im);
-        } else {
-            const long oi = r * Nout + (long)i * Ns + k;
-            float2 base = xadd ? xadd[oi] : make_float2(0.f, 0.f);
-            out[oi] = make_float2(base.x + sign * re, base.y + sign * im);
-        }
-    }
-    if (!use_dinv) return;
-    __syncthreads();
-    for (int o = threadIdx.x; o < Ns * nr; o += blockDim.x) {
-        const int k = o / nr, r = o - k * nr;
-        float re = 0.f, im = 0.f;
-        const float2 *row = Dinv + ((long)b * Ns + k) * Ns;
-        const float2 *x = hs + r * P;
-#pragma unroll 4
-        for (int l = 0; l < Ns; l++) {
-            const float2 a = __ldg(row + l), y = x[l];
-            re = fmx(a.x, y.x, fmx(-a.y, y.y, re));
-            im = fmx(a.x, y.y, fmx(a.y, y.x, im));
-        }
-        const long oi = r * Nout + (long)i * Ns + k;
-        float2 base = xadd ? xadd[oi] : make_float2(0.f, 0.f);
-        out[oi] = make_float2(base.x + sign * re, base.y + sign * im);
-    }
-}
-// The same operation with eight warps per row block, warp j taking the hop
+// with P_b = Dinv[b] (use_dinv) or 1; xadd may be null.
+// One CTA per row block, eight warps: warp j takes the hop
 // to neighbour j with lane k owning row k of the block (Ns <= 32) and all (up
 // to CW_R) right-hand sides of the pass in registers.  Every matrix entry is
 // loaded once per launch, coalesced from the column-major copies
@@ -1165,8 +1087,8 @@ __global__ void __launch_bounds__(256) k_coarse_hop_eo(int Ns, long Nin, long No
 // matrix) and 8 warps per row block keep enough loads in flight.
 constexpr int CW_R = 12;   // right-hand sides per pass
 __global__ void __launch_bounds__(256) k_coarse_hop_eo_j(int Ns, long Nin, long Nout, int nrhs,
-                                                         const int *__restrict__ rows, const int *__restrict__ nbr,
-                                                         const int *__restrict__ pos, const float2 *__restrict__ AT,
+                                                         const int *__restrict__ rows, const int *__restrict__ npos,
+                                                         const float2 *__restrict__ AT,
                                                          const float2 *__restrict__ DT, int use_dinv,
                                                          const float2 *__restrict__ in, const float2 *xadd,
                                                          float sign, float2 *out)
@@ -1181,7 +1103,7 @@ __global__ void __launch_bounds__(256) k_coarse_hop_eo_j(int Ns, long Nin, long 
     in += r0 * Nin;
     out += r0 * Nout;
     if (xadd) xadd += r0 * Nout;
-    const long seg = (long)pos[nbr[b * 9 + 1 + j]] * Ns;
+    const long seg = (long)npos[i * 8 + j] * Ns;
     if (lane < Ns)
 #pragma unroll
         for (int r = 0; r < CW_R; r++)
@@ -1192,17 +1114,24 @@ __global__ void __launch_bounds__(256) k_coarse_hop_eo_j(int Ns, long Nin, long 
     for (int r = 0; r < CW_R; r++) re[r] = im[r] = 0.f;
     if (lane < Ns) {
         const float2 *Aj = AT + ((long)b * 8 + j) * Ns * Ns + lane;
-#pragma unroll 4
-        for (int l = 0; l < Ns; l++) {
-            const float2 a = __ldg(Aj + l * Ns);
-            const float4 *y4 = reinterpret_cast<const float4 *>(xj + l * CW_R);
+        // the matrix column in groups of 8 entries, each group's loads issued together
+        for (int l0 = 0; l0 < Ns; l0 += 8) {
+            float2 av[8];
 #pragma unroll
-            for (int q = 0; q < CW_R / 2; q++) {
-                const float4 y = y4[q];
-                re[2 * q] = fmx(a.x, y.x, fmx(-a.y, y.y, re[2 * q]));
-                im[2 * q] = fmx(a.x, y.y, fmx(a.y, y.x, im[2 * q]));
-                re[2 * q + 1] = fmx(a.x, y.z, fmx(-a.y, y.w, re[2 * q + 1]));
-                im[2 * q + 1] = fmx(a.x, y.w, fmx(a.y, y.z, im[2 * q + 1]));
+            for (int u = 0; u < 8; u++) av[u] = l0 + u < Ns ? __ldg(Aj + (l0 + u) * Ns) : make_float2(0.f, 0.f);
+#pragma unroll
+            for (int u = 0; u < 8; u++) {
+                if (l0 + u >= Ns) break;
+                const float2 a = av[u];
+                const float4 *y4 = reinterpret_cast<const float4 *>(xj + (l0 + u) * CW_R);
+#pragma unroll
+                for (int q = 0; q < CW_R / 2; q++) {
+                    const float4 y = y4[q];
+                    re[2 * q] = fmx(a.x, y.x, fmx(-a.y, y.y, re[2 * q]));
+                    im[2 * q] = fmx(a.x, y.y, fmx(a.y, y.x, im[2 * q]));
+                    re[2 * q + 1] = fmx(a.x, y.z, fmx(-a.y, y.w, re[2 * q + 1]));
+                    im[2 * q + 1] = fmx(a.x, y.w, fmx(a.y, y.z, im[2 * q + 1]));
+                }
             }
         }
     }
@@ -1323,6 +1252,7 @@ struct DflState {
     int ncol[2] = {0, 0};
     int *blist = nullptr;   // device [ncol[0] colour-0 block ids, then ncol[1] colour-1 ids]
     int *bpos = nullptr;    // device [nblk]: index of a block within its colour's list
+    int *npos = nullptr;    // device [nblk][8]: for list entry i, the list index of its neighbour j + 1
 };
 
 void dfl_free(lqcd_ctx *c)
@@ -1338,6 +1268,7 @@ void dfl_free(lqcd_ctx *c)
     cudaFree(c->dfl->Dinv32);
     cudaFree(c->dfl->blist);
     cudaFree(c->dfl->bpos);
+    cudaFree(c->dfl->npos);
     delete c->dfl;
     c->dfl = nullptr;
 }
@@ -1660,7 +1591,7 @@ lqcd_status coarse_gcr(lqcd_ctx *c, const double2 *b, double2 *x, int nrhs, doub
                        int *iters)
 {
     DflState *d = c->dfl;
-    if (d->Aint32 && d->eo && d->params.coarse_eo) return coarse_gcr32_eo(c, b, x, nrhs, tol, nkv, nmx, iters);
+    if (d->AT32) return coarse_gcr32_eo(c, b, x, nrhs, tol, nkv, nmx, iters);
     if (d->Aint32) return coarse_gcr32(c, b, x, nrhs, tol, nkv, nmx, iters);
     const long N = (long)d->B.nblk * d->Ns;
     const long n2 = 2 * N;
@@ -1850,25 +1781,12 @@ lqcd_status coarse_gcr32_eo(lqcd_ctx *c, const double2 *b, double2 *x, int nrhs,
     double2 *partial2 = partial + 4096 * 32;   // second half of the reduction buffer (4096 * 64 double2)
     const int nb = std::max(1, std::min<int>(std::max(8, 4 * 152 / nrhs), (int)((Ne + 255) / 256)));
     const int ga = std::max(1, std::min<int>(4 * 152 / std::max(1, nrhs), (int)((Ne + 255) / 256)));
-    const int Pp = Ns | 1;
-    const int rc = std::max(1, std::min(nrhs, COARSE_SMEM / (int)(9 * Pp * sizeof(float2))));
-    const int hthreads = std::min(256, (Ns * rc + 31) / 32 * 32);
-    const size_t hsm = (size_t)9 * rc * Pp * sizeof(float2);
-    static bool attr = false;
-    if (!attr) {
-        LQCD_CUDA_CHECK(c, cudaFuncSetAttribute(k_coarse_hop_eo, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                COARSE_SMEM));
-        attr = true;
-    }
+    if (!d->AT32) return set_err(c, LQCD_ERR_STATE, "even-odd coarse solve without its FP32 matrix copies");
     const size_t wsm = (size_t)9 * Ns * CW_R * sizeof(float2);
     auto hop = [&](const int *rows, int nrows, long Nin, long Nout, const float2 *in, int dinv, const float2 *xadd,
                    float sign, float2 *out) -> lqcd_status {
-        if (d->AT32)
-            k_coarse_hop_eo_j<<<dim3(nrows, div_up(nrhs, CW_R)), 256, wsm, c->stream>>>(
-                Ns, Nin, Nout, nrhs, rows, d->nbr, d->bpos, d->AT32, d->DT32, dinv, in, xadd, sign, out);
-        else
-            k_coarse_hop_eo<<<dim3(nrows, div_up(nrhs, rc)), hthreads, hsm, c->stream>>>(
-                Ns, Nin, Nout, nrhs, rc, rows, d->nbr, d->bpos, d->Aint32, d->Dinv32, dinv, in, xadd, sign, out);
+        k_coarse_hop_eo_j<<<dim3(nrows, div_up(nrhs, CW_R)), 256, wsm, c->stream>>>(
+            Ns, Nin, Nout, nrhs, rows, d->npos + 8 * (rows - d->blist), d->AT32, d->DT32, dinv, in, xadd, sign, out);
         c->n_kernel_launches++;
         LQCD_LAUNCH_CHECK(c);
         return LQCD_OK;
@@ -2103,14 +2021,19 @@ lqcd_status lqcd_dfl_build(lqcd_ctx *c, const lqcd_dfl_params *p, const double *
         d->ncol[1] = (int)lst[1].size();
         std::vector<int> all(lst[0]);
         all.insert(all.end(), lst[1].begin(), lst[1].end());
+        std::vector<int> np(8 * (size_t)B.nblk);
+        for (int i = 0; i < B.nblk; i++)
+            for (int j = 0; j < 8; j++) np[8 * (size_t)i + j] = pos[d->nbr_host[9 * all[i] + 1 + j]];
         if (cudaMalloc(&d->blist, B.nblk * sizeof(int)) != cudaSuccess ||
-            cudaMalloc(&d->bpos, B.nblk * sizeof(int)) != cudaSuccess) {
+            cudaMalloc(&d->bpos, B.nblk * sizeof(int)) != cudaSuccess ||
+            cudaMalloc(&d->npos, 8 * (size_t)B.nblk * sizeof(int)) != cudaSuccess) {
             cudaGetLastError();
             dfl_free(c);
             return set_err(c, LQCD_ERR_NOMEM, "deflation colour lists");
         }
         LQCD_CUDA_CHECK(c, cudaMemcpy(d->blist, all.data(), B.nblk * sizeof(int), cudaMemcpyHostToDevice));
         LQCD_CUDA_CHECK(c, cudaMemcpy(d->bpos, pos.data(), B.nblk * sizeof(int), cudaMemcpyHostToDevice));
+        LQCD_CUDA_CHECK(c, cudaMemcpy(d->npos, np.data(), 8 * (size_t)B.nblk * sizeof(int), cudaMemcpyHostToDevice));
     }
     // start vectors: canonical FP64 -> native storage precision
     void *t64;

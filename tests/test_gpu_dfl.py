@@ -1,6 +1,6 @@
 """GPU deflation against the oracle: subspace build (inverse iteration with
 SAP + block Gram-Schmidt), Pi^dag, Pi, the little Dirac operator, the coarse
-solve and the deflated preconditioner; the deflated GCR solve judged by the
+solve and the deflated preconditioner; the deflated GCR solve checked against the
 FP64 true residual."""
 import numpy as np
 import pytest

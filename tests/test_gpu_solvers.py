@@ -1,5 +1,5 @@
 """GPU solvers: CGNR on Dhat (8^4 workload), SAP parity against the oracle,
-SAP-preconditioned flexible GCR; every solve is judged by the FP64 true
+SAP-preconditioned flexible GCR; every solve is checked by the FP64 true
 residual recomputed by the oracle from the GPU solution."""
 import numpy as np
 import pytest
