@@ -12,6 +12,7 @@
 // H_blk keeps only hops whose both ends lie in the block (Dirichlet); a block
 // that spans a whole lattice direction keeps the wrapped hop of that direction.
 #include <algorithm>
+#include <list>
 #include <type_traits>
 #include <vector>
 
@@ -489,7 +490,7 @@ __global__ void __launch_bounds__(128) k_sap_block(SapArgs<P> a)
     // The block's new residual r - D_blk chi is (rho, 0): on odd sites it vanishes
     // by construction of chi_o, on even sites it is the MinRes residual of
     // Dhat_blk chi_e = b_e.  Hops from chi into other blocks are applied by
-    // k_sap_face afterwards.
+    // k_sap_face_l afterwards.
     for (int t = threadIdx.x; t < nh; t += blockDim.x) {
         SiteInfo s;
         block_site(a.g, B, org, 1, t, s);
@@ -1084,10 +1085,50 @@ __device__ __forceinline__ void sap_face_body(const SapArgs<P> &a, int col, long
     gadd(a.r + foff + par * half, Vh, rk, acc);
 }
 
+// The update of sap_face_body driven by a precomputed list of the sites that receive hops
+// from blocks of colour col: entry (i, mask) with i the parity-major site index
+// and bit 2 mu + (d > 0) of mask set for each hop from x + d mu that enters
+// from such a block.  The list is sorted by mask, so the threads of a warp
+// take the same hops (the site-ordered form branches per site); the hops are
+// those of sap_face_body in the same order, so the result is bitwise the same.
 template <int P>
-__global__ void __launch_bounds__(128) k_sap_face(SapArgs<P> a, int col)
+__global__ void __launch_bounds__(128) k_sap_face_l(SapArgs<P> a, const int2 *__restrict__ list, int n)
 {
-    sap_face_body<P>(a, col, blockIdx.x * (long)blockDim.x + threadIdx.x, blockIdx.y);
+    using R = typename SapT<P>::R;
+    using SP = typename SapT<P>::SP;
+    const long e = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    const int rhs = blockIdx.y;
+    const int2 fs = list[e];
+    const long Vh = a.g.Vh;
+    const int par = fs.x >= Vh;
+    const long rk = par ? fs.x - Vh : fs.x;
+    const long half = SapT<P>::half(Vh);
+    const long foff = rhs * a.fstride;
+    int x[4];
+    rank_coords(a.g, par, (int)rk, x);
+    cx<R> acc[12], u[3][3], v[12];
+#pragma unroll
+    for (int c = 0; c < 12; c++) acc[c] = mk(R(0), R(0));
+    const SP *din = a.delta + foff + (1 - par) * half;
+    for (int mu = 0; mu < 4; mu++)
+        for (int d = -1; d <= 1; d += 2) {
+            if (!((fs.y >> (2 * mu + (d > 0))) & 1)) continue;
+            const long ry = nbr_rank(a.g, x, mu, d);
+            gload(din, Vh, ry, v);
+            if (d > 0) {
+                R sg = (mu == 0 && x[0] == a.g.L[0] - 1) ? R(a.g.bc_t) : R(1);
+                glink(a.U, Vh, par, mu, rk, u);
+                proj_apply<R>(mu, -1, v, u, false, sg, acc);
+            } else {
+                R sg = (mu == 0 && x[0] == 0) ? R(a.g.bc_t) : R(1);
+                glink(a.U, Vh, 1 - par, mu, ry, u);
+                proj_apply<R>(mu, +1, v, u, true, sg, acc);
+            }
+        }
+#pragma unroll
+    for (int c = 0; c < 12; c++) acc[c] = R(0.5) * acc[c];
+    gadd(a.r + foff + par * half, Vh, rk, acc);
 }
 
 // ------------------------------------------------------------------ batches
@@ -1140,6 +1181,8 @@ struct SapPlan {
     int *blocks_dev = nullptr;   // [colour 0 ids..., colour 1 ids...]
     int count[2] = {0, 0};
     BlkGeom B;
+    int2 *face_dev[2] = {nullptr, nullptr};   // sites updated after colour col (k_sap_face_l)
+    int nface[2] = {0, 0};
 };
 
 // one cached plan per context (keyed by block shape)
@@ -1147,7 +1190,7 @@ struct PlanCache {
     lqcd_ctx *ctx;
     SapPlan plan;
 };
-std::vector<PlanCache> g_plans;
+std::list<PlanCache> g_plans;   // a list: pointers to its plans stay valid as it grows
 
 lqcd_status get_plan(lqcd_ctx *c, const int bs[4], SapPlan **out)
 {
@@ -1185,6 +1228,47 @@ lqcd_status get_plan(lqcd_ctx *c, const int bs[4], SapPlan **out)
     all.insert(all.end(), ids[1].begin(), ids[1].end());
     LQCD_CUDA_CHECK(c, cudaMalloc(&P.blocks_dev, all.size() * sizeof(int)));
     LQCD_CUDA_CHECK(c, cudaMemcpy(P.blocks_dev, all.data(), all.size() * sizeof(int), cudaMemcpyHostToDevice));
+    // face lists: for each site, the hops that enter from a block of colour col
+    // (a different block; both parities, parity-major index), sorted by hop mask
+    {
+        const int *L = c->g.L;
+        const long Vh = c->g.Vh;
+        std::vector<std::pair<int, int>> fl[2];   // (mask, index)
+        int x[4];
+        for (x[0] = 0; x[0] < L[0]; x[0]++)
+            for (x[1] = 0; x[1] < L[1]; x[1]++)
+                for (x[2] = 0; x[2] < L[2]; x[2]++)
+                    for (x[3] = 0; x[3] < L[3]; x[3]++) {
+                        const long lex = x[3] + (long)L[3] * (x[2] + (long)L[2] * (x[1] + (long)L[1] * x[0]));
+                        const int par = (x[0] + x[1] + x[2] + x[3]) & 1;
+                        const int idx = (int)(par * Vh + (lex >> 1));
+                        int bx[4], bsum = 0;
+                        for (int m = 0; m < 4; m++) {
+                            bx[m] = x[m] / bs[m];
+                            bsum += bx[m];
+                        }
+                        int mask[2] = {0, 0};
+                        for (int mu = 0; mu < 4; mu++)
+                            for (int d = -1; d <= 1; d += 2) {
+                                int y = x[mu] + d;
+                                y = y < 0 ? y + L[mu] : (y >= L[mu] ? y - L[mu] : y);
+                                const int by = y / bs[mu];
+                                if (by == bx[mu]) continue;
+                                mask[(bsum - bx[mu] + by) & 1] |= 1 << (2 * mu + (d > 0));
+                            }
+                        for (int col = 0; col < 2; col++)
+                            if (mask[col]) fl[col].push_back({mask[col], idx});
+                    }
+        for (int col = 0; col < 2; col++) {
+            std::sort(fl[col].begin(), fl[col].end());
+            std::vector<int2> h(fl[col].size());
+            for (size_t k = 0; k < h.size(); k++) h[k] = make_int2(fl[col][k].second, fl[col][k].first);
+            P.nface[col] = (int)h.size();
+            if (h.empty()) continue;
+            LQCD_CUDA_CHECK(c, cudaMalloc(&P.face_dev[col], h.size() * sizeof(int2)));
+            LQCD_CUDA_CHECK(c, cudaMemcpy(P.face_dev[col], h.data(), h.size() * sizeof(int2), cudaMemcpyHostToDevice));
+        }
+    }
     g_plans.push_back({c, P});
     *out = &g_plans.back().plan;
     return LQCD_OK;
@@ -1310,7 +1394,9 @@ lqcd_status sap_run(lqcd_ctx *c, const SapPlan &P_, int ncy, int nmr, const void
             }
             sweep++;
             if (cyc == ncy - 1 && col == last_col) continue;
-            k_sap_face<P><<<dim3(div_up(2L * c->g.Vh, 128), nrhs), 128, 0, c->stream>>>(a, col);
+            if (Pl.nface[col] > 0)
+                k_sap_face_l<P><<<dim3(div_up(Pl.nface[col], 128), nrhs), 128, 0, c->stream>>>(
+                    a, Pl.face_dev[col], Pl.nface[col]);
             c->n_kernel_launches++;
             LQCD_LAUNCH_CHECK(c);
         }
@@ -1536,12 +1622,14 @@ lqcd_status sap_batch_apply(lqcd_ctx *hc, SapBatch *b, const void *eta, size_t b
 
 void sap_free_plans(lqcd_ctx *c)
 {
-    for (size_t i = 0; i < g_plans.size();) {
-        if (g_plans[i].ctx == c) {
-            cudaFree(g_plans[i].plan.blocks_dev);
-            g_plans.erase(g_plans.begin() + i);
+    for (auto it = g_plans.begin(); it != g_plans.end();) {
+        if (it->ctx == c) {
+            cudaFree(it->plan.blocks_dev);
+            cudaFree(it->plan.face_dev[0]);
+            cudaFree(it->plan.face_dev[1]);
+            it = g_plans.erase(it);
         } else
-            i++;
+            ++it;
     }
 }
 
