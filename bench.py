@@ -293,8 +293,8 @@ def time_to_solve(ctx, lqcd, eta, net=None):
     build = r["build_s"]
     out["chosen"] = {"form": "deflated SAP-GCR (Ns=20, 4^4 blocks), FP16 (per-site scale) SAP in the solve and the "
                              "subspace build, FP32 subspace, "
-                             "stencil, little-Dirac solve and GCR Krylov vectors; FP64 residual, solution and "
-                             "restarts; 12 RHS batched",
+                             "stencil, even-odd little-Dirac solve and GCR Krylov vectors; FP64 residual, "
+                             "solution and restarts; 12 RHS batched",
                      "seconds": r["total_s"], "build_s": build, "iters": max(r["iters"]), "net_fallbacks": 0,
                      "max_relres_dhat": r["max_relres_dhat"], "status": r["status"]}
     if net is not None:
