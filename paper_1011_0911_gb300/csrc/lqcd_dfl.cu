@@ -469,6 +469,9 @@ __global__ void k_little_build32(Geom g, DBlk B, const float4 *phi, int Ns, long
         for (int sp = 0; sp < 4; sp++)
 #pragma unroll
             for (int c = 0; c < 3; c++) acc.s[sp][c] = mk(0.f, 0.f);
+        // W_j (j >= 1) vanishes on the sites that its hop does not reach: they
+        // skip the subspace loads below (their products would all be zero)
+        bool nz = j == 0;
         for (int mu = 0; mu < 4; mu++)
             for (int d = -1; d <= 1; d += 2) {
                 const int jj = d > 0 ? 1 + 2 * mu : 2 + 2 * mu;
@@ -476,6 +479,7 @@ __global__ void k_little_build32(Geom g, DBlk B, const float4 *phi, int Ns, long
                 const bool inside = (lm >= 0 && lm < B.bs[mu]) || B.wrap[mu];
                 if ((j == 0) != inside) continue;
                 if (j != 0 && j != jj) continue;
+                nz = true;
                 int y[4] = {s.x[0], s.x[1], s.x[2], s.x[3]};
                 y[mu] = (y[mu] + d + g.L[mu]) % g.L[mu];
                 const int ry = coords_rank(g, y);
@@ -505,7 +509,7 @@ __global__ void k_little_build32(Geom g, DBlk B, const float4 *phi, int Ns, long
 #pragma unroll
             for (int i = 0; i < RCHUNK; i++) {
                 dd[2 * i] = dd[2 * i + 1] = 0.f;
-                if (i < kn) {
+                if (i < kn && nz) {
                     stencil::Spinor<float> q;
                     stencil::load_spinor(phi + (k0 + i) * fstride + s.p * hs, g.Vh, (int)s.r, q);
 #pragma unroll
